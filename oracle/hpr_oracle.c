@@ -1,0 +1,602 @@
+/*
+ * Plain FP64 CPU oracle: restarted HPR for LP (Sec. 3, Eq. 9 and Theorem 1),
+ * Pock-Chambolle scaling with normalisation (Sec. 3.A), the Round operator
+ * and Algorithm 1 (Sec. 4.1), and the bound propagation + reduction that
+ * stands in for MILP-/LP-Presolve in Algorithm 2 (Sec. 4.2).
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline).  It shares no
+ * source with the CUDA library.  Every loop is scalar, sequential and in the
+ * order the formulas are written; no blocking, fusion or reordering.
+ *
+ * Readings of points the paper leaves open (restart rule, sigma update,
+ * residual normalisation, propagation tolerances) are the ones listed in the
+ * design notes; each is named where it is used below.
+ */
+#include "hpr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static double clampd(double v, double l, double u) {
+  if (v < l) return l;
+  if (v > u) return u;
+  return v;
+}
+
+/* magnitude of the finite bounds of one row (0 when both are infinite) */
+static double bound_mag(double lo, double hi) {
+  double b = 0.0;
+  if (isfinite(lo) && fabs(lo) > b) b = fabs(lo);
+  if (isfinite(hi) && fabs(hi) > b) b = fabs(hi);
+  return b;
+}
+
+static double* dalloc(int64_t k) { return (double*)calloc((size_t)(k > 0 ? k : 1), sizeof(double)); }
+
+/* y = A x (CSR) */
+static void spmv(int32_t m, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* x, double* y) {
+  for (int32_t i = 0; i < m; i++) {
+    double s = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; k++) s += val[k] * x[col[k]];
+    y[i] = s;
+  }
+}
+
+/* y = A^T x (CSR of A, scatter in row order) */
+static void spmv_t(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
+                   const double* val, const double* x, double* y) {
+  for (int32_t j = 0; j < n; j++) y[j] = 0.0;
+  for (int32_t i = 0; i < m; i++)
+    for (int64_t k = rp[i]; k < rp[i + 1]; k++) y[col[k]] += val[k] * x[i];
+}
+
+static double dot(int64_t k, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < k; i++) s += a[i] * b[i];
+  return s;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.A: Pock-Chambolle scaling (alpha = 1) and normalisation          */
+/* ---------------------------------------------------------------------- */
+void orc_scale(const orc_lp* lp, int32_t use_scaling, double* Dr, double* Dc, double* beta,
+               double* gamma, double* val_s, double* c_s, double* xl_s, double* xu_s,
+               double* lo_s, double* hi_s) {
+  const int32_t m = lp->m, n = lp->n;
+  for (int32_t i = 0; i < m; i++) Dr[i] = 1.0;
+  for (int32_t j = 0; j < n; j++) Dc[j] = 1.0;
+  if (use_scaling) {
+    /* D_r,i = 1/sqrt(sum_j |a_ij|),  D_c,j = 1/sqrt(sum_i |a_ij|) */
+    double* cs = dalloc(n);
+    for (int32_t i = 0; i < m; i++) {
+      double s = 0.0;
+      for (int64_t k = lp->row_ptr[i]; k < lp->row_ptr[i + 1]; k++) {
+        s += fabs(lp->val[k]);
+        cs[lp->col[k]] += fabs(lp->val[k]);
+      }
+      Dr[i] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    }
+    for (int32_t j = 0; j < n; j++) Dc[j] = cs[j] > 0.0 ? 1.0 / sqrt(cs[j]) : 1.0;
+    free(cs);
+  }
+  /* A_hat = D_r A D_c; bounds and cost in the scaled variables x = D_c x_hat */
+  for (int32_t i = 0; i < m; i++)
+    for (int64_t k = lp->row_ptr[i]; k < lp->row_ptr[i + 1]; k++)
+      val_s[k] = (Dr[i] * lp->val[k]) * Dc[lp->col[k]];
+  for (int32_t j = 0; j < n; j++) {
+    c_s[j] = Dc[j] * lp->c[j];
+    xl_s[j] = lp->xl[j] / Dc[j];
+    xu_s[j] = lp->xu[j] / Dc[j];
+  }
+  for (int32_t i = 0; i < m; i++) {
+    lo_s[i] = Dr[i] * lp->lo[i];
+    hi_s[i] = Dr[i] * lp->hi[i];
+  }
+  /* normalisation of the bound vector by 1+||b|| and the cost by 1+||c|| */
+  double bn = 0.0, cn = 0.0;
+  for (int32_t i = 0; i < m; i++) {
+    double b = bound_mag(lo_s[i], hi_s[i]);
+    bn += b * b;
+  }
+  for (int32_t j = 0; j < n; j++) cn += c_s[j] * c_s[j];
+  *beta = use_scaling ? 1.0 + sqrt(bn) : 1.0;
+  *gamma = use_scaling ? 1.0 + sqrt(cn) : 1.0;
+  for (int32_t i = 0; i < m; i++) {
+    lo_s[i] /= *beta;
+    hi_s[i] /= *beta;
+  }
+  for (int32_t j = 0; j < n; j++) {
+    xl_s[j] /= *beta;
+    xu_s[j] /= *beta;
+    c_s[j] /= *gamma;
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Power method for lambda_max(A A^T) (Sec. 3)                             */
+/* ---------------------------------------------------------------------- */
+/* SplitMix64 (Steele, Lea, Flood 2014) evaluated at counter j */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t j) {
+  uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+double orc_power_lambda(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
+                        const double* val, int32_t max_iter, double tol, uint64_t seed,
+                        int32_t* iters_out) {
+  double* q = dalloc(n);
+  double* u = dalloc(m);
+  double* w = dalloc(n);
+  for (int32_t j = 0; j < n; j++) q[j] = 0.5 + (double)(splitmix64_at(seed, (uint64_t)j) >> 11) * 0x1.0p-53;
+  double nq = sqrt(dot(n, q, q));
+  for (int32_t j = 0; j < n; j++) q[j] /= nq;
+  double lam = 0.0, lam_prev = 0.0;
+  int32_t it = 0;
+  for (it = 1; it <= max_iter; it++) {
+    spmv(m, rp, col, val, q, u);           /* u = A q          */
+    spmv_t(m, n, rp, col, val, u, w);      /* w = A^T A q      */
+    lam = dot(m, u, u);                    /* q^T A^T A q      */
+    double nw = sqrt(dot(n, w, w));
+    if (nw == 0.0) break;
+    for (int32_t j = 0; j < n; j++) q[j] = w[j] / nw;
+    if (it > 1 && fabs(lam - lam_prev) <= tol * lam) break;
+    lam_prev = lam;
+  }
+  if (it > max_iter) it = max_iter;
+  if (iters_out) *iters_out = it;
+  free(q);
+  free(u);
+  free(w);
+  return lam;
+}
+
+/* ---------------------------------------------------------------------- */
+/* KKT residuals on the unscaled LP (Theorem 1 map, normalised)            */
+/* ---------------------------------------------------------------------- */
+void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z, double* out) {
+  const int32_t m = lp->m, n = lp->n;
+  double* ax = dalloc(m);
+  double* aty = dalloc(n);
+  spmv(m, lp->row_ptr, lp->col, lp->val, x, ax);
+  spmv_t(m, n, lp->row_ptr, lp->col, lp->val, y, aty);
+  /* primal: distance of A x to [lo, hi] */
+  double pr = 0.0, bn = 0.0;
+  for (int32_t i = 0; i < m; i++) {
+    double d = ax[i] - clampd(ax[i], lp->lo[i], lp->hi[i]);
+    pr += d * d;
+    double b = bound_mag(lp->lo[i], lp->hi[i]);
+    bn += b * b;
+  }
+  /* dual: c - A^T y - z */
+  double dr = 0.0, cn = 0.0;
+  for (int32_t j = 0; j < n; j++) {
+    double d = lp->c[j] - aty[j] - z[j];
+    dr += d * d;
+    cn += lp->c[j] * lp->c[j];
+  }
+  /* objectives: dual uses the bound each multiplier prices */
+  double pobj = 0.0, dobj = 0.0;
+  for (int32_t j = 0; j < n; j++) pobj += lp->c[j] * x[j];
+  for (int32_t i = 0; i < m; i++) {
+    if (y[i] > 0.0 && isfinite(lp->lo[i])) dobj += lp->lo[i] * y[i];
+    else if (y[i] < 0.0 && isfinite(lp->hi[i])) dobj += lp->hi[i] * y[i];
+  }
+  for (int32_t j = 0; j < n; j++) {
+    if (z[j] > 0.0 && isfinite(lp->xl[j])) dobj += lp->xl[j] * z[j];
+    else if (z[j] < 0.0 && isfinite(lp->xu[j])) dobj += lp->xu[j] * z[j];
+  }
+  out[0] = sqrt(pr) / (1.0 + sqrt(bn));
+  out[1] = sqrt(dr) / (1.0 + sqrt(cn));
+  out[2] = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+  out[3] = pobj;
+  out[4] = dobj;
+  out[5] = fmax(out[0], fmax(out[1], out[2]));
+  /* Theorem 1 map R(x,y,z) with the row box generalising R^m_+:
+   * R1 = y - P(y - A x), P(r) = r + Pi_[lo,hi](-r)  (= Pi_+(y - Ax + theta)
+   * for rows A x >= theta);  R2 = x - Pi_K(x - z);  R3 = c - A^T y - z   */
+  double rr = 0.0;
+  for (int32_t i = 0; i < m; i++) {
+    double r = y[i] - ax[i];
+    double p = r + clampd(-r, lp->lo[i], lp->hi[i]);
+    rr += (y[i] - p) * (y[i] - p);
+  }
+  for (int32_t j = 0; j < n; j++) {
+    double r2 = x[j] - clampd(x[j] - z[j], lp->xl[j], lp->xu[j]);
+    double r3 = lp->c[j] - aty[j] - z[j];
+    rr += r2 * r2 + r3 * r3;
+  }
+  out[6] = sqrt(rr);
+  free(ax);
+  free(aty);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Restarted HPR (Eq. 9)                                                   */
+/* ---------------------------------------------------------------------- */
+int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
+                  const double* y_init, double* x_out, double* y_out, double* z_out,
+                  orc_info* info, orc_log* log) {
+  const int32_t m = lp->m, n = lp->n;
+  const int64_t nnz = lp->row_ptr[m];
+  double *Dr = dalloc(m), *Dc = dalloc(n), *vs = dalloc(nnz), *cs = dalloc(n);
+  double *xls = dalloc(n), *xus = dalloc(n), *los = dalloc(m), *his = dalloc(m);
+  double beta = 1.0, gamma = 1.0;
+  orc_scale(lp, prm->use_scaling, Dr, Dc, &beta, &gamma, vs, cs, xls, xus, los, his);
+
+  double lambda = prm->lambda_in;
+  int32_t piters = 0;
+  if (!(lambda > 0.0)) {
+    lambda = prm->lambda_safety *
+             orc_power_lambda(m, n, lp->row_ptr, lp->col, vs, prm->power_max_iter, prm->power_tol,
+                              prm->power_seed, &piters);
+    if (!(lambda > 0.0)) lambda = 1.0; /* no constraints: any positive value */
+  }
+
+  double *x = dalloc(n), *x0 = dalloc(n), *xt = dalloc(n), *xb = dalloc(n), *zb = dalloc(n);
+  double *g = dalloc(n), *y = dalloc(m), *y0 = dalloc(m), *yb = dalloc(m), *q = dalloc(m);
+  double *xo = dalloc(n), *yo = dalloc(m), *zo = dalloc(n);
+
+  /* starting point, in scaled variables, projected onto K and the dual cone */
+  for (int32_t j = 0; j < n; j++) {
+    double v = x_init ? x_init[j] / (beta * Dc[j]) : 0.0;
+    x[j] = clampd(v, xls[j], xus[j]);
+  }
+  for (int32_t i = 0; i < m; i++) {
+    double v = y_init ? y_init[i] / (gamma * Dr[i]) : 0.0;
+    if (!isfinite(los[i]) && v > 0.0) v = 0.0;
+    if (!isfinite(his[i]) && v < 0.0) v = 0.0;
+    y[i] = v;
+  }
+  memcpy(x0, x, sizeof(double) * (size_t)n);
+  memcpy(y0, y, sizeof(double) * (size_t)m);
+
+  double sigma = prm->sigma0;
+  int64_t k = 0, t = 0;
+  int first_check = 1;
+  double rho0 = 0.0, rho_prev = 0.0;
+  int32_t restarts = 0, nlog = 0, status = 1;
+  double last[7] = {0, 0, 0, 0, 0, 0, 0};
+  int have_out = 0;
+
+  while (t < prm->max_iter) {
+    const int is_check = ((t + 1) % prm->check_every == 0) || (t + 1 == prm->max_iter);
+    const double s = 1.0 / (lambda * sigma);
+    const double wa = 1.0 / (double)(k + 2);        /* Halpern weights */
+    const double wb = (double)(k + 1) / (double)(k + 2);
+
+    /* x_bar = Pi_K(x + sigma (A^T y - c)); z_bar = (x_bar - v)/sigma */
+    spmv_t(m, n, lp->row_ptr, lp->col, vs, y, g);
+    double dxx = 0.0;
+    for (int32_t j = 0; j < n; j++) {
+      double v = x[j] + sigma * (g[j] - cs[j]);
+      double xbar = clampd(v, xls[j], xus[j]);
+      xt[j] = 2.0 * xbar - x[j];                   /* reflection */
+      if (is_check) {
+        xb[j] = xbar;
+        zb[j] = (xbar - v) / sigma;
+        dxx += (xbar - x[j]) * (xbar - x[j]);
+      }
+    }
+    /* y_bar = prox: r = y - s A x_tilde; y_bar = r + s * Pi_[lo,hi](-r/s) */
+    spmv(m, lp->row_ptr, lp->col, vs, xt, q);
+    double dyy = 0.0;
+    for (int32_t i = 0; i < m; i++) {
+      double r = y[i] - s * q[i];
+      double ybar = r + s * clampd(-r / s, los[i], his[i]);
+      if (is_check) {
+        yb[i] = ybar;
+        dyy += (ybar - y[i]) * (ybar - y[i]);
+      }
+      y[i] = wa * y0[i] + wb * (2.0 * ybar - y[i]);  /* Halpern step */
+    }
+    for (int32_t j = 0; j < n; j++) x[j] = wa * x0[j] + wb * xt[j];
+    k++;
+    t++;
+    if (!is_check) continue;
+
+    /* unscale the barred iterate and evaluate the KKT map on the original LP */
+    for (int32_t j = 0; j < n; j++) {
+      xo[j] = beta * Dc[j] * xb[j];
+      double zz = gamma * zb[j] / Dc[j];
+      if (zz > 0.0 && !isfinite(lp->xl[j])) zz = 0.0;
+      if (zz < 0.0 && !isfinite(lp->xu[j])) zz = 0.0;
+      zo[j] = zz;
+    }
+    for (int32_t i = 0; i < m; i++) yo[i] = gamma * Dr[i] * yb[i];
+    orc_kkt(lp, xo, yo, zo, last);
+    have_out = 1;
+    const double rho = sqrt(dxx / sigma + lambda * sigma * dyy);
+
+    int restart = 0;
+    const int was_first = first_check;
+    if (last[5] <= prm->tol) {
+      status = 0;
+    } else {
+      /* restart rule (reading): sufficient / necessary / long */
+      if (first_check) {
+        rho0 = rho;
+        first_check = 0;
+        if ((double)k >= prm->restart_long * (double)t) restart = 1;
+      } else {
+        if (rho <= prm->restart_suff * rho0) restart = 1;
+        else if (rho <= prm->restart_nec * rho0 && rho > rho_prev) restart = 1;
+        else if ((double)k >= prm->restart_long * (double)t) restart = 1;
+      }
+      rho_prev = rho;
+    }
+    if (log && nlog < prm->log_cap) {
+      orc_log* e = &log[nlog];
+      e->iter = t;
+      e->restart = restart;
+      e->first = was_first;
+      e->rp = last[0];
+      e->rd = last[1];
+      e->gap = last[2];
+      e->pobj = last[3];
+      e->dobj = last[4];
+      e->rho = rho;
+      e->sigma = sigma;
+      e->rmap = last[6];
+    }
+    nlog++;
+    if (status == 0) break;
+    if (restart) {
+      /* primal-weight update from the displacement since the last restart */
+      double ddx = 0.0, ddy = 0.0;
+      for (int32_t j = 0; j < n; j++) ddx += (x[j] - x0[j]) * (x[j] - x0[j]);
+      for (int32_t i = 0; i < m; i++) ddy += (y[i] - y0[i]) * (y[i] - y0[i]);
+      ddx = sqrt(ddx);
+      ddy = sqrt(ddy);
+      if (ddx > 1e-10 && ddy > 1e-10) {
+        double sig_new = ddx / (sqrt(lambda) * ddy);
+        sigma = sqrt(sig_new * sigma); /* equal-weight geometric smoothing */
+      }
+      memcpy(x0, x, sizeof(double) * (size_t)n);
+      memcpy(y0, y, sizeof(double) * (size_t)m);
+      k = 0;
+      first_check = 1;
+      restarts++;
+    }
+  }
+
+  if (have_out) {
+    memcpy(x_out, xo, sizeof(double) * (size_t)n);
+    memcpy(y_out, yo, sizeof(double) * (size_t)m);
+    memcpy(z_out, zo, sizeof(double) * (size_t)n);
+  }
+  if (info) {
+    info->iters = t;
+    info->status = status;
+    info->restarts = restarts;
+    info->nlog = nlog;
+    info->power_iters = piters;
+    info->rp = last[0];
+    info->rd = last[1];
+    info->gap = last[2];
+    info->pobj = last[3];
+    info->dobj = last[4];
+    info->kkt = last[5];
+    info->lambda = lambda;
+    info->sigma = sigma;
+    info->beta = beta;
+    info->gamma = gamma;
+  }
+  free(Dr); free(Dc); free(vs); free(cs); free(xls); free(xus); free(los); free(his);
+  free(x); free(x0); free(xt); free(xb); free(zb); free(g); free(y); free(y0); free(yb);
+  free(q); free(xo); free(yo); free(zo);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 4.1: Round and Algorithm 1                                         */
+/* ---------------------------------------------------------------------- */
+int32_t orc_round(double s, double tau) {
+  if (s >= 1.0 - tau) return 1;
+  if (s >= 0.0 && s <= tau) return 0;
+  return -1;
+}
+
+int64_t orc_fix(int32_t G, int32_t T, const double* u, const double* v, const double* w,
+                const int8_t* u_init, double tau, int32_t t_first, int8_t* fix_out) {
+  int64_t nfixed = 0;
+  int32_t* ru = (int32_t*)malloc(sizeof(int32_t) * (size_t)(T + 1));
+  int32_t* rv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(T + 1));
+  int32_t* rw = (int32_t*)malloc(sizeof(int32_t) * (size_t)(T + 1));
+  for (int64_t e = 0; e < 3LL * G * T; e++) fix_out[e] = -1;
+  for (int32_t g = 0; g < G; g++) {
+    for (int32_t t = 0; t < T; t++) {
+      ru[t] = orc_round(u[(int64_t)g * T + t], tau);
+      rv[t] = orc_round(v[(int64_t)g * T + t], tau);
+      rw[t] = orc_round(w[(int64_t)g * T + t], tau);
+    }
+    for (int32_t t = t_first; t < T; t++) {
+      int32_t uprev = t > 0 ? ru[t - 1] : (int32_t)u_init[g];
+      if (ru[t] == -1 || uprev == -1 || rv[t] == -1 || rw[t] == -1) break;
+      if (ru[t] - uprev == rv[t] - rw[t] && rv[t] + rw[t] <= 1) {
+        int64_t e = 3 * ((int64_t)g * T + t);
+        fix_out[e + 0] = (int8_t)ru[t];
+        fix_out[e + 1] = (int8_t)rv[t];
+        fix_out[e + 2] = (int8_t)rw[t];
+        nfixed++;
+      } else {
+        break;
+      }
+    }
+  }
+  free(ru);
+  free(rv);
+  free(rw);
+  return nfixed;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bound propagation (stands in for MILP-/LP-Presolve of Algorithm 2)      */
+/* ---------------------------------------------------------------------- */
+/* Activity range of one row over the bounds: finite parts and the number of
+ * infinite contributions, summed in entry order.                          */
+static void row_activity(int64_t k0, int64_t k1, const int32_t* col, const double* val,
+                         const double* xl, const double* xu, double* mn, double* mx,
+                         int32_t* cmn, int32_t* cmx) {
+  double a_mn = 0.0, a_mx = 0.0;
+  int32_t c_mn = 0, c_mx = 0;
+  for (int64_t k = k0; k < k1; k++) {
+    double a = val[k];
+    double lmin = a > 0.0 ? xl[col[k]] : xu[col[k]];
+    double lmax = a > 0.0 ? xu[col[k]] : xl[col[k]];
+    if (isinf(lmin)) c_mn++;
+    else a_mn += a * lmin;
+    if (isinf(lmax)) c_mx++;
+    else a_mx += a * lmax;
+  }
+  *mn = a_mn;
+  *mx = a_mx;
+  *cmn = c_mn;
+  *cmx = c_mx;
+}
+
+int32_t orc_propagate(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
+                      const double* val, const double* lo, const double* hi, double* xl,
+                      double* xu, const uint8_t* is_int, int32_t max_passes) {
+  double* nlo = dalloc(n);
+  double* nhi = dalloc(n);
+  int32_t pass;
+  int32_t result = 0;
+  for (pass = 0; pass < max_passes; pass++) {
+    memcpy(nlo, xl, sizeof(double) * (size_t)n);
+    memcpy(nhi, xu, sizeof(double) * (size_t)n);
+    /* Jacobi: every row uses the bounds of the previous pass */
+    for (int32_t i = 0; i < m; i++) {
+      double mn, mx;
+      int32_t cmn, cmx;
+      row_activity(rp[i], rp[i + 1], col, val, xl, xu, &mn, &mx, &cmn, &cmx);
+      for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+        const int32_t j = col[k];
+        const double a = val[k];
+        const double lmin = a > 0.0 ? xl[j] : xu[j];
+        const double lmax = a > 0.0 ? xu[j] : xl[j];
+        /* from the row's upper bound: a x_j <= hi - (min activity of the rest) */
+        if (isfinite(hi[i])) {
+          int ok = isinf(lmin) ? (cmn == 1) : (cmn == 0);
+          if (ok) {
+            double rest = isinf(lmin) ? mn : mn - a * lmin;
+            double b = (hi[i] - rest) / a;
+            if (a > 0.0) { if (b < nhi[j]) nhi[j] = b; }
+            else { if (b > nlo[j]) nlo[j] = b; }
+          }
+        }
+        /* from the row's lower bound: a x_j >= lo - (max activity of the rest) */
+        if (isfinite(lo[i])) {
+          int ok = isinf(lmax) ? (cmx == 1) : (cmx == 0);
+          if (ok) {
+            double rest = isinf(lmax) ? mx : mx - a * lmax;
+            double b = (lo[i] - rest) / a;
+            if (a > 0.0) { if (b > nlo[j]) nlo[j] = b; }
+            else { if (b < nhi[j]) nhi[j] = b; }
+          }
+        }
+      }
+    }
+    int changed = 0;
+    for (int32_t j = 0; j < n; j++) {
+      double l = nlo[j], u = nhi[j];
+      if (is_int[j]) {
+        if (isfinite(u)) u = floor(u + 1e-6);
+        if (isfinite(l)) l = ceil(l - 1e-6);
+        if (l > xl[j]) { xl[j] = l; changed = 1; }
+        if (u < xu[j]) { xu[j] = u; changed = 1; }
+      } else {
+        double tl = 1e-9 * fmax(1.0, isfinite(xl[j]) ? fabs(xl[j]) : 1.0);
+        double tu = 1e-9 * fmax(1.0, isfinite(xu[j]) ? fabs(xu[j]) : 1.0);
+        if (l > xl[j] + tl) { xl[j] = l; changed = 1; }
+        if (u < xu[j] - tu) { xu[j] = u; changed = 1; }
+      }
+      if (xl[j] > xu[j] + 1e-6) result = -1 - pass;
+    }
+    if (result < 0) break;
+    if (!changed) break;
+  }
+  free(nlo);
+  free(nhi);
+  if (result < 0) return result;
+  return pass < max_passes ? pass + 1 : max_passes;
+}
+
+int orc_reduce(int32_t m, int32_t n, const int64_t* rp, const int32_t* col, const double* val,
+               const double* c, const double* lo, const double* hi, const double* xl,
+               const double* xu, int64_t* dims, int64_t* rp_r, int32_t* col_r, double* val_r,
+               double* c_r, double* lo_r, double* hi_r, double* xl_r, double* xu_r,
+               int32_t* row_map, int32_t* col_map, double* obj_const) {
+  int32_t* newcol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t nr = 0;
+  double oc = 0.0;
+  for (int32_t j = 0; j < n; j++) {
+    if (xl[j] == xu[j]) {
+      newcol[j] = -1;
+      oc += c[j] * xl[j];
+    } else {
+      newcol[j] = nr;
+      col_map[nr] = j;
+      c_r[nr] = c[j];
+      xl_r[nr] = xl[j];
+      xu_r[nr] = xu[j];
+      nr++;
+    }
+  }
+  int32_t mr = 0;
+  int64_t kk = 0;
+  int bad = 0;
+  rp_r[0] = 0;
+  for (int32_t i = 0; i < m; i++) {
+    /* fold the fixed columns into the row bounds */
+    double shift = 0.0;
+    int64_t kept = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+      if (newcol[col[k]] < 0) shift += val[k] * xl[col[k]];
+      else kept++;
+    }
+    double l = lo[i] - shift, u = hi[i] - shift;
+    if (kept == 0) {
+      if (l > 1e-6 * fmax(1.0, fabs(l)) || u < -1e-6 * fmax(1.0, fabs(u))) bad = 1;
+      continue;
+    }
+    /* activity range over the free columns */
+    double mn = 0.0, mx = 0.0;
+    int32_t cmn = 0, cmx = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+      const int32_t j = col[k];
+      if (newcol[j] < 0) continue;
+      const double a = val[k];
+      const double lmin = a > 0.0 ? xl[j] : xu[j];
+      const double lmax = a > 0.0 ? xu[j] : xl[j];
+      if (isinf(lmin)) cmn++;
+      else mn += a * lmin;
+      if (isinf(lmax)) cmx++;
+      else mx += a * lmax;
+    }
+    int lo_red = !isfinite(l) || (cmn == 0 && mn >= l);
+    int hi_red = !isfinite(u) || (cmx == 0 && mx <= u);
+    if (lo_red && hi_red) continue;
+    row_map[mr] = i;
+    lo_r[mr] = l;
+    hi_r[mr] = u;
+    for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+      int32_t nc = newcol[col[k]];
+      if (nc < 0) continue;
+      col_r[kk] = nc;
+      val_r[kk] = val[k];
+      kk++;
+    }
+    mr++;
+    rp_r[mr] = kk;
+  }
+  dims[0] = mr;
+  dims[1] = nr;
+  dims[2] = kk;
+  *obj_const = oc;
+  free(newcol);
+  return bad;
+}
