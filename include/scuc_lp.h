@@ -1,0 +1,207 @@
+/*
+ * scuc_lp.h -- C ABI of the B300 (sm_103a) library that solves SCUC LP
+ * relaxations with the restarted Halpern Peaceman-Rachford (HPR) iteration
+ * and runs the logic-driven fixing + bound propagation between relaxations.
+ *
+ * Paper: "Successive Fixing for Large-Scale SCUC Using First-Order Methods".
+ *   LP form ............ Sec. 3, Eq. 8:  min mu^T x  s.t.  A x >= theta,
+ *                        x in K = [x^L, x^U].  Here the row set is a box
+ *                        lo <= A x <= hi given by a sense per row.
+ *   Iteration .......... Sec. 3, Eq. 9 (x-, y-, z-steps, reflection,
+ *                        Halpern anchoring); lambda = lambda_max(A A^T) by
+ *                        the power method (Sec. 3, text after Eq. 9).
+ *   Stopping ........... KKT residual map of Theorem 1 (normalised).
+ *   Scaling ............ Sec. 3.A: Pock-Chambolle diagonal scaling and
+ *                        normalisation of bounds and costs (Ruiz off).
+ *   FP32 matvecs ....... Sec. 3.B: low-precision arithmetic for the core
+ *                        steps; here the matvecs only, with FP64 iterates,
+ *                        reductions and a final FP64 phase.
+ *   Round / fixing ..... Sec. 4.1, Round operator and Algorithm 1.
+ *   Presolve ........... Sec. 4.2, Algorithm 2 (MILP-/LP-Presolve): bound
+ *                        propagation and removal of fixed columns and
+ *                        redundant rows.
+ *
+ * Conventions (all entry points):
+ *   - Return value is an scuc_err code; SCUC_OK on success.  On failure
+ *     scuc_last_error() gives a message (thread-local, valid until the next
+ *     call on the same thread).  Solver outcomes go to info->status.
+ *   - Every pointer argument is caller-owned and never retained.  Host
+ *     arrays are read (or written) during the call only.  Device pointers
+ *     are used only where a parameter says so.
+ *   - A handle owns its device copies; it is not thread-safe; all its work is
+ *     ordered on the CUDA stream given at creation (NULL = legacy default
+ *     stream) on the device that was current at creation.
+ *   - Invalid input (sizes, unsorted or out-of-range column indices, NaN,
+ *     lo > hi, xl > xu) returns SCUC_E_INVALID before any launch.
+ *   - Sizes: m, n < 2^31 and nnz < 2^31 (32-bit indices on the device).
+ *   - No entry point allocates pinned host memory per call or synchronises
+ *     the whole device; each solve synchronises its stream before returning.
+ */
+#ifndef SCUC_LP_H
+#define SCUC_LP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scuc_lp scuc_lp;
+
+enum scuc_err {
+  SCUC_OK = 0,
+  SCUC_E_INVALID = 1,        /* bad argument or malformed input             */
+  SCUC_E_CUDA = 2,           /* a CUDA runtime call failed                  */
+  SCUC_E_OOM = 3,            /* device allocation failed                    */
+  SCUC_E_DEVICE_TIMEOUT = 4, /* a bounded device-side wait ran out          */
+  SCUC_E_INFEASIBLE = 5      /* propagation proved the fixed model infeasible */
+};
+
+enum scuc_status {
+  SCUC_ST_OPTIMAL = 0,       /* max(r_p, r_d, gap) <= tol                   */
+  SCUC_ST_ITER_LIMIT = 1,
+  SCUC_ST_TIME_LIMIT = 2,
+  SCUC_ST_NUMERICAL = 3,     /* NaN/Inf appeared in a residual              */
+  SCUC_ST_FALLBACK_COLD = 4  /* warm start rejected, solved from cold start */
+};
+
+enum scuc_precision {
+  SCUC_FP64 = 0,             /* FP64 matvecs                                */
+  SCUC_MIXED = 1             /* FP32 matvecs + FP32 accumulation, FP64
+                                iterates/reductions/restarts, FP64 final
+                                phase (Sec. 3.B)                             */
+};
+
+/* Solver parameters.  scuc_default_params() fills the defaults given in the
+ * comments; the restart and sigma rules are the readings of "adaptive sigma
+ * updates and restart schemes" (Sec. 3, after Theorem 1) described with
+ * scuc_lp_solve.                                                         */
+typedef struct {
+  double tol;             /* 1e-4: stop when max(r_p, r_d, gap) <= tol      */
+  int64_t max_iter;       /* 1e6 (rounded up to a multiple of check_every)  */
+  double time_limit_s;    /* 3600 (wall time, checked at KKT checks)        */
+  int32_t check_every;    /* 64: iterations between KKT/restart checks      */
+  int32_t precision;      /* SCUC_FP64                                      */
+  int32_t use_scaling;    /* 1: Pock-Chambolle + normalisation (Sec. 3.A)   */
+  double sigma0;          /* 1.0: initial primal step sigma                 */
+  double lambda_in;       /* 0: run the power method; > 0: use this value   */
+  double lambda_safety;   /* 1.01: lambda = safety * power estimate         */
+  int32_t power_max_iter; /* 500                                            */
+  double power_tol;       /* 1e-4 relative change of the estimate           */
+  uint64_t power_seed;    /* 0x5EED: start q_j = 0.5 + U01(SplitMix64(seed +
+                             (j+1) * 0x9E3779B97F4A7C15))                   */
+  double restart_suff;    /* 0.2 */
+  double restart_nec;     /* 0.8 */
+  double restart_long;    /* 0.2 */
+  double polish_factor;   /* 10: MIXED switches to FP64 at kkt <= factor*tol */
+  int32_t polish_stall;   /* 20: ... or after this many checks without a
+                             10 % improvement of the best KKT in FP32       */
+  int32_t use_graph;      /* 1: replay each check period as a CUDA graph    */
+  int32_t profile;        /* 1: time the two SpMV kernels with CUDA events  */
+  int32_t device_ptrs;    /* 1: x0/y0 and x/y/z_out of scuc_lp_solve are
+                             device pointers on the handle's device         */
+} scuc_solve_params;
+
+typedef struct {
+  int32_t status;         /* scuc_status                                    */
+  int32_t restarts;
+  int64_t iters;          /* total HPR iterations                           */
+  int64_t iters_fp32;     /* of which with FP32 matvecs                     */
+  int32_t power_iters;
+  int32_t nlog;           /* entries in the check log (scuc_lp_get_log)     */
+  double kkt, rp, rd, gap;/* at the returned point (unscaled LP)            */
+  double pobj, dobj;      /* primal and dual objective (unscaled LP)        */
+  double lambda, sigma;   /* lambda used, final sigma                       */
+  double beta, gamma;     /* normalisation factors of Sec. 3.A              */
+  double setup_ms;        /* scaling + power method                         */
+  double solve_ms;        /* iterations (wall, stream-synchronised)         */
+  /* profile = 1: summed CUDA-event time and launch counts of the SpMV
+   * kernels (dual step = A x_tilde, primal step = A^T y)                  */
+  double ms_dual_spmv, ms_primal_spmv;
+  int64_t n_dual_spmv, n_primal_spmv;
+} scuc_solve_info;
+
+typedef struct {
+  int64_t iter;           /* total iterations at this check                 */
+  int32_t restart;        /* 1 if the check restarted the Halpern cycle     */
+  int32_t first;          /* 1 if first check of its cycle                  */
+  double rp, rd, gap, pobj, dobj;
+  double rho;             /* restart metric (scaled space)                  */
+  double sigma;           /* sigma in force during the checked period       */
+  int32_t fp64;           /* 1 if the period used FP64 matvecs              */
+  int32_t pad;
+} scuc_check_log;
+
+/* Defaults listed in scuc_solve_params. */
+void scuc_default_params(scuc_solve_params* p);
+
+/* Create an LP  min c^T x  s.t.  row_i(A x) in [lo_i, hi_i], xl <= x <= xu
+ * (Eq. 8).  Host CSR: row_ptr[m+1] (int64, row_ptr[0] = 0, nondecreasing),
+ * col[nnz] (int32, strictly increasing within a row, in [0, n)), val[nnz]
+ * (finite FP64).  c[n] finite; xl[n], xu[n] may be -INF / +INF.
+ * sense[m]: 'G' (lo = rhs, hi = +INF), 'L' (lo = -INF, hi = rhs),
+ * 'E' (lo = hi = rhs), 'R' (lo = rhs, hi = rhs + range, range >= 0).
+ * range may be NULL when no row is 'R'.  cuda_stream: cudaStream_t or NULL.
+ * All data are copied to the device of the current CUDA context; the
+ * transposed matrix is built on the device.  *out receives the handle.   */
+int scuc_lp_create(scuc_lp** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                   const int32_t* col, const double* val, const double* c, const double* xl,
+                   const double* xu, const char* sense, const double* rhs, const double* range,
+                   void* cuda_stream);
+
+/* Same with the row box given directly: lo[m], hi[m] (lo <= hi, +-INF). */
+int scuc_lp_create_box(scuc_lp** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                       const int32_t* col, const double* val, const double* c, const double* xl,
+                       const double* xu, const double* lo, const double* hi, void* cuda_stream);
+
+/* Dimensions of a handle. */
+int scuc_lp_dims(const scuc_lp* lp, int32_t* m, int32_t* n, int64_t* nnz);
+
+/* Solve with restarted HPR (Eq. 9).
+ *  x0[n], y0[m]: optional warm start (NULL = cold start from x = Pi_K(0),
+ *    y = 0); projected onto K and onto the sign pattern of the rows.
+ *  x_out[n], y_out[m], z_out[n]: caller buffers (NULL allowed) receiving
+ *    the last checked point (x_bar, y_bar, z_bar) in the unscaled LP.
+ *  Host or device pointers according to p->device_ptrs.
+ *  Per iteration k (k counts iterations since the last restart, scaled
+ *  problem, s = 1/(lambda sigma)):
+ *    x_bar = Pi_K(x + sigma (A^T y - c));   z_bar = (x_bar - v)/sigma
+ *    x_t   = 2 x_bar - x;                   y_bar = P_s(y - s A x_t)
+ *    with P_s(r) = r + s Pi_[lo,hi](-r/s), i.e. Pi_+(y + s(theta - A x_t))
+ *    for rows A x >= theta;  then x, y <- (anchor + (k+1)(2 bar - old))/(k+2).
+ *  Every check_every iterations the KKT residuals r_p = ||Ax - Pi(Ax)|| /
+ *  (1+||b||), r_d = ||c - A^T y - z|| / (1+||c||), gap = |p-d|/(1+|p|+|d|)
+ *  are evaluated at (x_bar, y_bar, z_bar) of the unscaled LP, and the cycle
+ *  restarts (anchor <- current point, k <- 0) on the first check with
+ *  k >= restart_long * total, or on a later check with
+ *  rho <= restart_suff*rho0, or rho <= restart_nec*rho0 and rho > rho_prev,
+ *  or k >= restart_long*total; rho = sqrt(||x_bar-x||^2/sigma +
+ *  lambda sigma ||y_bar-y||^2).  At a restart sigma <- sqrt(sigma *
+ *  ||dx||/(sqrt(lambda) ||dy||)) with d the displacement since the last
+ *  restart (skipped when either norm < 1e-10).
+ *  info (may be NULL) receives the outcome; the check log is kept in the
+ *  handle (scuc_lp_get_log).  Synchronises the handle's stream.         */
+int scuc_lp_solve(scuc_lp* lp, const scuc_solve_params* p, const double* x0, const double* y0,
+                  double* x_out, double* y_out, double* z_out, scuc_solve_info* info);
+
+/* Copy up to cap entries of the last solve's check log into out (host);
+ * *count receives the number copied.                                    */
+int scuc_lp_get_log(const scuc_lp* lp, scuc_check_log* out, int32_t cap, int32_t* count);
+
+/* Unscaled products on device buffers of the handle's device:
+ * transpose = 0: out[m] = A in[n];  transpose = 1: out[n] = A^T in[m].
+ * Uses the same SpMV kernels as the solver (FP64).                      */
+int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double* out_dev);
+
+/* Solve several LPs (each with its own handle; they may live on different
+ * streams of the same device) with the same parameters.  infos[count]. */
+int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_params* p,
+                        scuc_solve_info* infos);
+
+void scuc_lp_destroy(scuc_lp* lp);
+
+const char* scuc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

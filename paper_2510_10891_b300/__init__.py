@@ -1,0 +1,6 @@
+"""B300 (sm_103a) library for the LP relaxations of the successive-fixing
+SCUC method: restarted HPR solve (Sec. 3), logic-driven fixing (Sec. 4.1)
+and bound-propagation presolve (Sec. 4.2), behind the C ABI of
+include/scuc_lp.h.  This package only marshals arguments to that library;
+importing it does not load the library until it is first used."""
+from .lp import LP, default_params, info_dict  # noqa: F401

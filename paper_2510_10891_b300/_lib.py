@@ -1,0 +1,93 @@
+"""ctypes declarations of the C ABI in include/scuc_lp.h (marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "libscuclp.so")
+
+SCUC_OK, SCUC_E_INVALID, SCUC_E_CUDA, SCUC_E_OOM, SCUC_E_DEVICE_TIMEOUT, SCUC_E_INFEASIBLE = range(6)
+STATUS = {0: "optimal", 1: "iter_limit", 2: "time_limit", 3: "numerical", 4: "fallback_cold"}
+FP64, MIXED = 0, 1
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("time_limit_s", C.c_double),
+                ("check_every", C.c_int32), ("precision", C.c_int32), ("use_scaling", C.c_int32),
+                ("sigma0", C.c_double), ("lambda_in", C.c_double), ("lambda_safety", C.c_double),
+                ("power_max_iter", C.c_int32), ("power_tol", C.c_double), ("power_seed", C.c_uint64),
+                ("restart_suff", C.c_double), ("restart_nec", C.c_double),
+                ("restart_long", C.c_double), ("polish_factor", C.c_double),
+                ("polish_stall", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
+                ("device_ptrs", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("restarts", C.c_int32), ("iters", C.c_int64),
+                ("iters_fp32", C.c_int64), ("power_iters", C.c_int32), ("nlog", C.c_int32),
+                ("kkt", C.c_double), ("rp", C.c_double), ("rd", C.c_double), ("gap", C.c_double),
+                ("pobj", C.c_double), ("dobj", C.c_double), ("lambda_", C.c_double),
+                ("sigma", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("ms_dual_spmv", C.c_double),
+                ("ms_primal_spmv", C.c_double), ("n_dual_spmv", C.c_int64),
+                ("n_primal_spmv", C.c_int64)]
+
+
+class CheckLog(C.Structure):
+    _fields_ = [("iter", C.c_int64), ("restart", C.c_int32), ("first", C.c_int32),
+                ("rp", C.c_double), ("rd", C.c_double), ("gap", C.c_double), ("pobj", C.c_double),
+                ("dobj", C.c_double), ("rho", C.c_double), ("sigma", C.c_double),
+                ("fp64", C.c_int32), ("pad", C.c_int32)]
+
+
+_lib = None
+
+# exported symbols and their signatures
+_SIGS = {
+    "scuc_default_params": (None, [C.POINTER(SolveParams)]),
+    "scuc_lp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_int64, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_lp_create_box": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_int64,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_lp_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int64)]),
+    "scuc_lp_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
+    "scuc_lp_get_log": (C.c_int, [C.c_void_p, C.POINTER(CheckLog), C.c_int32, C.POINTER(C.c_int32)]),
+    "scuc_lp_matvec": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "scuc_lp_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(SolveParams),
+                                      C.POINTER(SolveInfo)]),
+    "scuc_lp_destroy": (None, [C.c_void_p]),
+    "scuc_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load the in-tree library; raise if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO):
+            raise RuntimeError("libscuclp.so is missing: build it with "
+                               "`python -m paper_2510_10891_b300.build` (nvcc, sm_103a)")
+        L = C.CDLL(SO)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class ScucError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("scuc error %d: %s" % (code, msg))
+        self.code = code
+
+
+def check(rc):
+    if rc != SCUC_OK:
+        raise ScucError(rc, lib().scuc_last_error().decode(errors="replace"))
+    return rc

@@ -1,0 +1,61 @@
+// Shared definitions of the sm_103a SCUC LP library (device + host).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "scuc_lp.h"
+
+namespace scuc {
+
+void set_error(const char* fmt, ...);
+
+#define SCUC_CUDA(expr)                                                                  \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      ::scuc::set_error("%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+      return _e == cudaErrorMemoryAllocation ? SCUC_E_OOM : SCUC_E_CUDA;                 \
+    }                                                                                    \
+  } while (0)
+
+#define SCUC_TRY(expr)              \
+  do {                              \
+    int _r = (expr);                \
+    if (_r != SCUC_OK) return _r;   \
+  } while (0)
+
+constexpr int kBlock = 256;     // threads per SpMV block
+constexpr int kNnzCap = 2048;   // nonzeros staged in shared memory per multi-row block
+constexpr int kMaxRows = 256;   // rows per multi-row block
+constexpr int kLongRow = 256;   // rows longer than this get a whole block
+constexpr int kDecideThreads = 1024;
+
+// Row-block partition of a CSR matrix for the SpMV kernels: block b covers
+// rows [row[b], row[b+1]); gsz[b] = threads per row (1..32), or 0 when the
+// block is a single long row reduced by the whole block.
+struct Partition {
+  int nblk = 0;
+  int* row = nullptr;
+  int8_t* gsz = nullptr;
+};
+
+// Device-resident solver state.  Parameters are written by the host before a
+// solve; the state is advanced only by the decide kernel.
+struct Ctrl {
+  double tol, sigma, lambda, beta, gamma, bnorm, cnorm;
+  double restart_suff, restart_nec, restart_long, polish_factor;
+  int64_t max_iter;
+  int32_t check_every, polish_stall, log_cap, precision;
+  int64_t k, t, iters_fp32;
+  double rho0, rho_prev, best_kkt;
+  int32_t first_check, done, status, restart_pending;
+  int32_t restarts, nlog, fp64_phase, stall;
+  double kkt, rp, rd, gap, pobj, dobj;
+};
+
+struct PowerCtrl {
+  double lam, lam_prev, nw, tol;
+  int32_t it, max_iter, done, pad;
+};
+
+}  // namespace scuc

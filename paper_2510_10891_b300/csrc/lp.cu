@@ -1,0 +1,764 @@
+// Host side of the SCUC LP library: handle lifetime, device setup, the
+// restarted HPR solve loop (Eq. 9) and the C ABI of include/scuc_lp.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "lp.h"
+#include "setup_kernels.cuh"
+
+namespace scuc {
+
+static thread_local std::string g_err;
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  SCUC_CUDA(cudaMalloc((void**)p, count * sizeof(T) + 16));
+  return SCUC_OK;
+}
+
+static int grid_for(int64_t work, int block = kBlock) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 148 * 16) g = 148 * 16;
+  return (int)g;
+}
+
+// Row-block partition (host): rows longer than kLongRow get a block each;
+// other rows are packed in order into blocks of <= kMaxRows rows and
+// <= kNnzCap nonzeros; threads per row = largest power of two <= 256/rows.
+int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int>* rows_out,
+                    std::vector<int8_t>* gsz_out) {
+  std::vector<int> rows;
+  std::vector<int8_t> gsz;
+  rows.reserve(m / 64 + 16);
+  int r = 0;
+  rows.push_back(0);
+  while (r < m) {
+    const int len = rp[r + 1] - rp[r];
+    if (len > kLongRow) {
+      gsz.push_back(0);
+      r++;
+      rows.push_back(r);
+      continue;
+    }
+    const int start = r;
+    int nz = 0;
+    while (r < m && r - start < kMaxRows) {
+      const int l = rp[r + 1] - rp[r];
+      if (l > kLongRow || nz + l > kNnzCap) break;
+      nz += l;
+      r++;
+    }
+    const int nr = r - start;
+    int g = 1;
+    while (g < 32 && g * 2 * nr <= kBlock) g *= 2;
+    gsz.push_back((int8_t)g);
+    rows.push_back(r);
+  }
+  P->nblk = (int)gsz.size();
+  SCUC_TRY(dalloc(&P->row, rows.size()));
+  SCUC_TRY(dalloc(&P->gsz, gsz.size()));
+  SCUC_CUDA(cudaMemcpy(P->row, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!gsz.empty())
+    SCUC_CUDA(cudaMemcpy(P->gsz, gsz.data(), gsz.size() * sizeof(int8_t), cudaMemcpyHostToDevice));
+  if (rows_out) *rows_out = rows;
+  if (gsz_out) *gsz_out = gsz;
+  return SCUC_OK;
+}
+
+// exclusive scan of n ints into out[0..n] (out[n] = total), recursive
+int exclusive_scan(const int* in, int n, int* out, cudaStream_t s) {
+  const int nb = (n + kScan - 1) / kScan;
+  int *bsum = nullptr, *boff = nullptr;
+  SCUC_TRY(dalloc(&bsum, nb));
+  SCUC_TRY(dalloc(&boff, nb + 1));
+  if (n > 0) k_scan_block<<<nb, kScan, 0, s>>>(in, n, out, bsum);
+  SCUC_CUDA(cudaGetLastError());
+  if (nb > 1) {
+    SCUC_TRY(exclusive_scan(bsum, nb, boff, s));
+    k_scan_add<<<nb, kScan, 0, s>>>(out, n, boff);
+    SCUC_CUDA(cudaGetLastError());
+  }
+  // total
+  int total = 0;
+  if (n > 0) {
+    int last_in = 0, last_out = 0;
+    SCUC_CUDA(cudaMemcpyAsync(&last_in, in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    total = last_in + last_out;
+  }
+  SCUC_CUDA(cudaMemcpyAsync(out + n, &total, sizeof(int), cudaMemcpyHostToDevice, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  cudaFree(bsum);
+  cudaFree(boff);
+  return SCUC_OK;
+}
+
+Handle::~Handle() {
+  for (void* p : allocs) cudaFree(p);
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  for (auto& e : prof_ev) cudaEventDestroy(e);
+  if (ctrl_h) cudaFreeHost(ctrl_h);
+  if (ev_user) cudaEventDestroy(ev_user);
+  if (ev_work) cudaEventDestroy(ev_work);
+  for (auto& e : ev_slot)
+    if (e) cudaEventDestroy(e);
+  if (work) cudaStreamDestroy(work);
+}
+
+template <typename T>
+int Handle::alloc(T** p, size_t count) {
+  SCUC_TRY(dalloc(p, count));
+  allocs.push_back((void*)*p);
+  return SCUC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// validation (host, before any launch)
+// ---------------------------------------------------------------------------
+static int validate(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                    const double* val, const double* c, const double* xl, const double* xu,
+                    const double* lo, const double* hi) {
+  if (m < 0 || n < 0 || nnz < 0 || nnz >= (int64_t)INT32_MAX) {
+    set_error("invalid sizes m=%d n=%d nnz=%lld", m, n, (long long)nnz);
+    return SCUC_E_INVALID;
+  }
+  if (!row_ptr || (nnz > 0 && (!col || !val)) || (n > 0 && (!c || !xl || !xu)) ||
+      (m > 0 && (!lo || !hi))) {
+    set_error("null input array");
+    return SCUC_E_INVALID;
+  }
+  if (row_ptr[0] != 0 || row_ptr[m] != nnz) {
+    set_error("row_ptr[0] must be 0 and row_ptr[m] must equal nnz");
+    return SCUC_E_INVALID;
+  }
+  for (int32_t i = 0; i < m; i++) {
+    if (row_ptr[i + 1] < row_ptr[i]) {
+      set_error("row_ptr decreases at row %d", i);
+      return SCUC_E_INVALID;
+    }
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+      if (col[e] < 0 || col[e] >= n || (e > row_ptr[i] && col[e] <= col[e - 1])) {
+        set_error("column index out of range or not increasing in row %d", i);
+        return SCUC_E_INVALID;
+      }
+      if (!std::isfinite(val[e])) {
+        set_error("non-finite matrix value in row %d", i);
+        return SCUC_E_INVALID;
+      }
+    }
+    if (std::isnan(lo[i]) || std::isnan(hi[i]) || lo[i] > hi[i] || lo[i] == INFINITY ||
+        hi[i] == -INFINITY) {
+      set_error("invalid row bounds at row %d", i);
+      return SCUC_E_INVALID;
+    }
+  }
+  for (int32_t j = 0; j < n; j++) {
+    if (!std::isfinite(c[j]) || std::isnan(xl[j]) || std::isnan(xu[j]) || xl[j] > xu[j] ||
+        xl[j] == INFINITY || xu[j] == -INFINITY) {
+      set_error("invalid cost or bounds at column %d", j);
+      return SCUC_E_INVALID;
+    }
+  }
+  return SCUC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// creation: copies, transpose on the device, partitions
+// ---------------------------------------------------------------------------
+int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                  const int32_t* col, const double* val, const double* c, const double* xl,
+                  const double* xu, const double* lo, const double* hi, void* stream) {
+  SCUC_TRY(validate(m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi));
+  Handle* H = new Handle();
+  int rc = H->init(m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi, (cudaStream_t)stream);
+  if (rc != SCUC_OK) {
+    delete H;
+    return rc;
+  }
+  *out = H;
+  return SCUC_OK;
+}
+
+int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, const int32_t* col_,
+                 const double* val_, const double* c_, const double* xl_, const double* xu_,
+                 const double* lo_, const double* hi_, cudaStream_t user_) {
+  m = m_;
+  n = n_;
+  nnz = nnz_;
+  user = user_;
+  SCUC_CUDA(cudaGetDevice(&device));
+  SCUC_CUDA(cudaStreamCreateWithFlags(&work, cudaStreamNonBlocking));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_user, cudaEventDisableTiming));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_work, cudaEventDisableTiming));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_slot[0], cudaEventDisableTiming));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_slot[1], cudaEventDisableTiming));
+  SCUC_CUDA(cudaMallocHost((void**)&ctrl_h, 2 * sizeof(Ctrl)));
+  SCUC_TRY(enter());
+  cudaStream_t s = work;
+
+  std::vector<int> rp32(m + 1);
+  for (int i = 0; i <= m; i++) rp32[i] = (int)row_ptr[i];
+  SCUC_TRY(alloc(&rp, m + 1));
+  SCUC_TRY(alloc(&col, nnz));
+  SCUC_TRY(alloc(&val, nnz));
+  SCUC_TRY(alloc(&c, n));
+  SCUC_TRY(alloc(&xl, n));
+  SCUC_TRY(alloc(&xu, n));
+  SCUC_TRY(alloc(&lo, m));
+  SCUC_TRY(alloc(&hi, m));
+  SCUC_CUDA(cudaMemcpyAsync(rp, rp32.data(), (m + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nnz) {
+    SCUC_CUDA(cudaMemcpyAsync(col, col_, nnz * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaMemcpyAsync(val, val_, nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  if (n) {
+    SCUC_CUDA(cudaMemcpyAsync(c, c_, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaMemcpyAsync(xl, xl_, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaMemcpyAsync(xu, xu_, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  if (m) {
+    SCUC_CUDA(cudaMemcpyAsync(lo, lo_, m * sizeof(double), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaMemcpyAsync(hi, hi_, m * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+
+  // transpose: count, scan, scatter, per-column sort by row, gather values
+  SCUC_TRY(alloc(&rpt, n + 1));
+  SCUC_TRY(alloc(&colt, nnz));
+  SCUC_TRY(alloc(&permt, nnz));
+  SCUC_TRY(alloc(&valt, nnz));
+  int* cnt = nullptr;
+  SCUC_TRY(alloc(&cnt, n + 1));
+  SCUC_CUDA(cudaMemsetAsync(cnt, 0, (n + 1) * sizeof(int), s));
+  if (nnz) k_count_cols<<<grid_for(nnz), kBlock, 0, s>>>(col, nnz, cnt);
+  SCUC_CUDA(cudaGetLastError());
+  SCUC_TRY(exclusive_scan(cnt, n, rpt, s));
+  SCUC_CUDA(cudaMemcpyAsync(cnt, rpt, n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if (m) k_scatter_t<<<grid_for((int64_t)m * 32), kBlock, 0, s>>>(rp, col, m, cnt, colt, permt);
+  SCUC_CUDA(cudaGetLastError());
+  std::vector<int> rpt_h(n + 1);
+  SCUC_CUDA(cudaMemcpyAsync(rpt_h.data(), rpt, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> longcols;
+  for (int j = 0; j < n; j++) {
+    const int L = rpt_h[j + 1] - rpt_h[j];
+    if (L > kSortCap) {
+      set_error("column %d has %d nonzeros; at most %d per column are supported", j, L, kSortCap);
+      return SCUC_E_INVALID;
+    }
+    if (L > 32) longcols.push_back(j);
+  }
+  if (n) k_sort_small<<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(rpt, n, colt, permt);
+  SCUC_CUDA(cudaGetLastError());
+  if (!longcols.empty()) {
+    int* lc = nullptr;
+    SCUC_TRY(alloc(&lc, longcols.size()));
+    SCUC_CUDA(cudaMemcpyAsync(lc, longcols.data(), longcols.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kSortCap * 8));
+    k_sort_block<<<(int)longcols.size(), 1024, kSortCap * 8, s>>>(rpt, lc, colt, permt);
+    SCUC_CUDA(cudaGetLastError());
+  }
+  if (nnz) k_gather_t<<<grid_for(nnz), kBlock, 0, s>>>(permt, nnz, val, valt);
+  SCUC_CUDA(cudaGetLastError());
+
+  SCUC_TRY(build_partition(rp32, m, &pA, nullptr, nullptr));
+  SCUC_TRY(build_partition(rpt_h, n, &pT, nullptr, nullptr));
+  allocs.push_back(pA.row);
+  allocs.push_back(pA.gsz);
+  allocs.push_back(pT.row);
+  allocs.push_back(pT.gsz);
+
+  // scaled data and iterates
+  SCUC_TRY(alloc(&vs, nnz));
+  SCUC_TRY(alloc(&vst, nnz));
+  SCUC_TRY(alloc(&Dr, m));
+  SCUC_TRY(alloc(&Dc, n));
+  SCUC_TRY(alloc(&cs, n));
+  SCUC_TRY(alloc(&xls, n));
+  SCUC_TRY(alloc(&xus, n));
+  SCUC_TRY(alloc(&los, m));
+  SCUC_TRY(alloc(&his, m));
+  SCUC_TRY(alloc(&x, n));
+  SCUC_TRY(alloc(&x0, n));
+  SCUC_TRY(alloc(&xt, n));
+  SCUC_TRY(alloc(&xbar, n));
+  SCUC_TRY(alloc(&zbar, n));
+  SCUC_TRY(alloc(&y, m));
+  SCUC_TRY(alloc(&y0, m));
+  SCUC_TRY(alloc(&ybar, m));
+  SCUC_TRY(alloc(&xt32, n));
+  SCUC_TRY(alloc(&y32, m));
+  SCUC_TRY(alloc(&partP, 4 * (size_t)pT.nblk));
+  SCUC_TRY(alloc(&partD, 2 * (size_t)pA.nblk));
+  SCUC_TRY(alloc(&partRA, 2 * (size_t)std::max(pA.nblk, kNormBlocks)));
+  SCUC_TRY(alloc(&partRT, 4 * (size_t)std::max(pT.nblk, kNormBlocks)));
+  SCUC_TRY(alloc(&ctrl, 1));
+  SCUC_TRY(alloc(&pctrl, 1));
+  SCUC_TRY(alloc(&qv, n));
+  SCUC_TRY(alloc(&uv, m));
+  SCUC_TRY(alloc(&wv, n));
+  SCUC_CUDA(cudaMemsetAsync(xbar, 0, n * sizeof(double) + 16, s));
+  SCUC_CUDA(cudaMemsetAsync(zbar, 0, n * sizeof(double) + 16, s));
+  SCUC_CUDA(cudaMemsetAsync(ybar, 0, m * sizeof(double) + 16, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  return leave();
+}
+
+// the handle's private stream follows the caller's stream and vice versa
+int Handle::enter() {
+  SCUC_CUDA(cudaSetDevice(device));
+  SCUC_CUDA(cudaEventRecord(ev_user, user));
+  SCUC_CUDA(cudaStreamWaitEvent(work, ev_user, 0));
+  return SCUC_OK;
+}
+
+int Handle::leave() {
+  SCUC_CUDA(cudaEventRecord(ev_work, work));
+  SCUC_CUDA(cudaStreamWaitEvent(user, ev_work, 0));
+  return SCUC_OK;
+}
+
+DevLP Handle::dev() const {
+  DevLP L;
+  L.m = m; L.n = n;
+  L.rp = rp; L.col = col; L.rpt = rpt; L.colt = colt;
+  L.vs = vs; L.vst = vst; L.vs32 = vs32; L.vst32 = vst32; L.val = val; L.valt = valt;
+  L.c = cs; L.xl = xls; L.xu = xus; L.lo = los; L.hi = his; L.Dr = Dr; L.Dc = Dc;
+  L.x = x; L.x0 = x0; L.xt = xt; L.xbar = xbar; L.zbar = zbar; L.y = y; L.y0 = y0; L.ybar = ybar;
+  L.xt32 = xt32; L.y32 = y32;
+  L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
+  L.pA = pA; L.pT = pT;
+  L.ctrl = ctrl; L.log = log_d;
+  return L;
+}
+
+// Pock-Chambolle scaling + normalisation (Sec. 3.A), then the unscaled norms
+int Handle::setup_scaling(int use_scaling, bool need_f32) {
+  cudaStream_t s = work;
+  if (m) k_abs_sum_inv_sqrt<<<(m + kBlock - 1) / kBlock, kBlock, 0, s>>>(rp, val, m, use_scaling, Dr);
+  if (n) k_abs_sum_inv_sqrt<<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(rpt, valt, n, use_scaling, Dc);
+  if (m) k_scale_vals<<<grid_for((int64_t)m * 32), kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, vs);
+  if (nnz) k_gather_t<<<grid_for(nnz), kBlock, 0, s>>>(permt, nnz, vs, vst);
+  k_scale_vecs<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(m, n, Dr, Dc, c, xl, xu, lo, hi, cs, xls, xus,
+                                                          los, his);
+  k_norms_partial<<<kNormBlocks, kBlock, 0, s>>>(m, n, los, his, cs, lo, hi, c, partRT);
+  k_norms_final<<<1, kDecideThreads, 0, s>>>(partRT, kNormBlocks, use_scaling, ctrl);
+  k_normalize<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(m, n, ctrl, cs, xls, xus, los, his);
+  SCUC_CUDA(cudaGetLastError());
+  if (need_f32) {
+    if (!vs32) {
+      SCUC_TRY(alloc(&vs32, nnz));
+      SCUC_TRY(alloc(&vst32, nnz));
+    }
+    if (nnz) {
+      k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vs, nnz, vs32);
+      k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vst, nnz, vst32);
+    }
+    SCUC_CUDA(cudaGetLastError());
+  }
+  return SCUC_OK;
+}
+
+// power method on A_hat (Sec. 3): lambda estimate of lambda_max(A A^T)
+int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters_out) {
+  cudaStream_t s = work;
+  PowerCtrl P0{};
+  P0.tol = p.power_tol;
+  P0.max_iter = p.power_max_iter;
+  SCUC_CUDA(cudaMemcpyAsync(pctrl, &P0, sizeof(PowerCtrl), cudaMemcpyHostToDevice, s));
+  k_power_seed<<<kNormBlocks, kBlock, 0, s>>>(n, p.power_seed, qv, partRT);
+  k_power_seed_norm<<<1, kDecideThreads, 0, s>>>(partRT, kNormBlocks, pctrl);
+  k_power_norm_seed<<<grid_for(n), kBlock, 0, s>>>(n, qv, pctrl);
+  SCUC_CUDA(cudaGetLastError());
+  PowerCtrl P{};
+  for (int it = 0; it < p.power_max_iter; it += 16) {
+    for (int j = 0; j < 16; j++) {
+      if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, 0, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
+      if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, 0, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
+      k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);
+      k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, pctrl);
+    }
+    SCUC_CUDA(cudaGetLastError());
+    SCUC_CUDA(cudaMemcpyAsync(&P, pctrl, sizeof(PowerCtrl), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    if (P.done) break;
+  }
+  *lam_out = P.lam;
+  *iters_out = P.it;
+  return SCUC_OK;
+}
+
+int Handle::ensure_log(int cap) {
+  if (cap > log_cap) {
+    scuc_check_log* nl = nullptr;
+    SCUC_TRY(alloc(&nl, cap));
+    log_d = nl;
+    log_cap = cap;
+  }
+  return SCUC_OK;
+}
+
+// One check period: anchor, check_every-1 plain iterations, a check iteration,
+// the two FP64 residual SpMVs and the decide kernel.
+int Handle::launch_period(int check_every, bool profile) {
+  cudaStream_t s = work;
+  const DevLP L = dev();
+  k_anchor<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L);
+  for (int j = 0; j < check_every; j++) {
+    const bool chk = (j == check_every - 1);
+    if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 0], s));
+    if (pT.nblk) {
+      if (chk) k_primal<true><<<pT.nblk, kBlock, 0, s>>>(L, j);
+      else k_primal<false><<<pT.nblk, kBlock, 0, s>>>(L, j);
+    }
+    if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 1], s));
+    if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 2], s));
+    if (pA.nblk) {
+      if (chk) k_dual<true><<<pA.nblk, kBlock, 0, s>>>(L, j);
+      else k_dual<false><<<pA.nblk, kBlock, 0, s>>>(L, j);
+    }
+    if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 3], s));
+  }
+  if (pA.nblk) k_res_primal<<<pA.nblk, kBlock, 0, s>>>(L);
+  if (pT.nblk) k_res_dual<<<pT.nblk, kBlock, 0, s>>>(L);
+  k_decide<<<1, kDecideThreads, 0, s>>>(L, check_every);
+  SCUC_CUDA(cudaGetLastError());
+  return SCUC_OK;
+}
+
+int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double* y0_in, double* xo,
+                  double* yo, double* zo, scuc_solve_info* info) {
+  using clk = std::chrono::steady_clock;
+  if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
+      (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1) {
+    set_error("invalid solve parameters");
+    return SCUC_E_INVALID;
+  }
+  SCUC_TRY(enter());
+  cudaStream_t s = work;
+  const auto t0 = clk::now();
+  const bool mixed = p.precision == SCUC_MIXED;
+  SCUC_TRY(ensure_log(4096));
+
+  // warm start in device memory
+  const double *xin = nullptr, *yin = nullptr;
+  if (x0_in) {
+    if (p.device_ptrs) xin = x0_in;
+    else {
+      SCUC_CUDA(cudaMemcpyAsync(wv, x0_in, n * sizeof(double), cudaMemcpyHostToDevice, s));
+      xin = wv;
+    }
+  }
+  if (y0_in) {
+    if (p.device_ptrs) yin = y0_in;
+    else {
+      SCUC_CUDA(cudaMemcpyAsync(uv, y0_in, m * sizeof(double), cudaMemcpyHostToDevice, s));
+      yin = uv;
+    }
+  }
+
+  SCUC_TRY(setup_scaling(p.use_scaling, mixed));
+  double lambda = p.lambda_in;
+  int piters = 0;
+  if (!(lambda > 0.0)) {
+    // the warm-start buffers double as power-method scratch: move them aside
+    if (xin == wv) { SCUC_CUDA(cudaMemcpyAsync(xt, wv, n * sizeof(double), cudaMemcpyDeviceToDevice, s)); xin = xt; }
+    if (yin == uv) { SCUC_CUDA(cudaMemcpyAsync(ybar, uv, m * sizeof(double), cudaMemcpyDeviceToDevice, s)); yin = ybar; }
+    double est = 0.0;
+    SCUC_TRY(power_method(p, &est, &piters));
+    lambda = p.lambda_safety * est;
+    if (!(lambda > 0.0)) lambda = 1.0;
+  }
+
+  // control block: parameters and initial state
+  Ctrl C{};
+  SCUC_CUDA(cudaMemcpyAsync(&C, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));  // beta, gamma, bnorm, cnorm from the device
+  const int64_t ce = p.check_every;
+  C.tol = p.tol;
+  C.sigma = p.sigma0;
+  C.lambda = lambda;
+  C.restart_suff = p.restart_suff;
+  C.restart_nec = p.restart_nec;
+  C.restart_long = p.restart_long;
+  C.polish_factor = p.polish_factor;
+  C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
+  C.check_every = p.check_every;
+  C.polish_stall = p.polish_stall;
+  C.log_cap = log_cap;
+  C.precision = p.precision;
+  C.k = 0; C.t = 0; C.iters_fp32 = 0;
+  C.rho0 = 0; C.rho_prev = 0; C.best_kkt = INFINITY;
+  C.first_check = 1; C.done = 0; C.status = -1; C.restart_pending = 0;
+  C.restarts = 0; C.nlog = 0; C.fp64_phase = mixed ? 0 : 1; C.stall = 0;
+  SCUC_CUDA(cudaMemcpyAsync(ctrl, &C, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  const DevLP L = dev();
+  k_init_iterates<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L, xin, yin);
+  SCUC_CUDA(cudaGetLastError());
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  const auto t1 = clk::now();
+
+  // iteration: periods of check_every iterations, two in flight
+  const int64_t nper = C.max_iter / ce;
+  bool use_graph = p.use_graph && !p.profile;
+  if (p.profile && (int)prof_ev.size() < 4 * p.check_every) {
+    while ((int)prof_ev.size() < 4 * p.check_every) {
+      cudaEvent_t e;
+      SCUC_CUDA(cudaEventCreate(&e));
+      prof_ev.push_back(e);
+    }
+  }
+  const void* key[3] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d};
+  if (use_graph && (!graph_exec || memcmp(key, graph_key, sizeof(key)) != 0)) {
+    if (graph_exec) { cudaGraphExecDestroy(graph_exec); graph_exec = nullptr; }
+    cudaGraph_t g;
+    SCUC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_period(p.check_every, false);
+    cudaError_t ce2 = cudaStreamEndCapture(s, &g);
+    if (rc != SCUC_OK) return rc;
+    SCUC_CUDA(ce2);
+    SCUC_CUDA(cudaGraphInstantiate(&graph_exec, g, 0));
+    cudaGraphDestroy(g);
+    memcpy(graph_key, key, sizeof(key));
+  }
+  double ms_p = 0.0, ms_d = 0.0;
+  int64_t n_p = 0, n_d = 0;
+  int timed_out = 0;
+  int64_t launched = 0, seen = 0;
+  const int inflight = p.profile ? 1 : 2;
+  while (seen < nper) {
+    while (launched < nper && launched - seen < inflight) {
+      if (use_graph) SCUC_CUDA(cudaGraphLaunch(graph_exec, s));
+      else SCUC_TRY(launch_period(p.check_every, p.profile != 0));
+      SCUC_CUDA(cudaMemcpyAsync(ctrl_h + (launched & 1), ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+      SCUC_CUDA(cudaEventRecord(ev_slot[launched & 1], s));
+      launched++;
+    }
+    // wait for the oldest period in flight (its state copy has landed)
+    SCUC_CUDA(cudaEventSynchronize(ev_slot[seen & 1]));
+    if (p.profile) {
+      for (int j = 0; j < p.check_every; j++) {
+        float a = 0.f, b = 0.f;
+        SCUC_CUDA(cudaEventElapsedTime(&a, prof_ev[4 * j + 0], prof_ev[4 * j + 1]));
+        SCUC_CUDA(cudaEventElapsedTime(&b, prof_ev[4 * j + 2], prof_ev[4 * j + 3]));
+        ms_p += a; ms_d += b;
+      }
+      n_p += p.check_every; n_d += p.check_every;
+    }
+    const Ctrl& h = ctrl_h[seen & 1];
+    seen++;
+    if (h.done) break;
+    const double el = std::chrono::duration<double>(clk::now() - t0).count();
+    if (el > p.time_limit_s) { timed_out = 1; break; }
+  }
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  SCUC_CUDA(cudaMemcpyAsync(&C, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  const auto t2 = clk::now();
+
+  // outputs (unscaled)
+  double *dxo = xo, *dyo = yo, *dzo = zo;
+  if (!p.device_ptrs) {
+    dxo = xo ? xt : nullptr;    // scratch: xt, wv (n), uv (m)
+    dzo = zo ? wv : nullptr;
+    dyo = yo ? uv : nullptr;
+  }
+  k_finalize<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L, dxo, dyo, dzo);
+  SCUC_CUDA(cudaGetLastError());
+  if (!p.device_ptrs) {
+    if (xo) SCUC_CUDA(cudaMemcpyAsync(xo, dxo, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (yo) SCUC_CUDA(cudaMemcpyAsync(yo, dyo, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (zo) SCUC_CUDA(cudaMemcpyAsync(zo, dzo, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  last_nlog = std::min(C.nlog, log_cap);
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = timed_out && !C.done ? SCUC_ST_TIME_LIMIT : (C.status < 0 ? SCUC_ST_ITER_LIMIT : C.status);
+    info->restarts = C.restarts;
+    info->iters = C.t;
+    info->iters_fp32 = C.iters_fp32;
+    info->power_iters = piters;
+    info->nlog = last_nlog;
+    info->kkt = C.kkt; info->rp = C.rp; info->rd = C.rd; info->gap = C.gap;
+    info->pobj = C.pobj; info->dobj = C.dobj;
+    info->lambda = C.lambda; info->sigma = C.sigma; info->beta = C.beta; info->gamma = C.gamma;
+    info->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->solve_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    info->ms_dual_spmv = ms_d; info->ms_primal_spmv = ms_p;
+    info->n_dual_spmv = n_d; info->n_primal_spmv = n_p;
+  }
+  return leave();
+}
+
+int Handle::matvec(int transpose, const double* in, double* out) {
+  SCUC_TRY(enter());
+  cudaStream_t s = work;
+  if (!transpose) {
+    if (pA.nblk) k_spmv_plain<<<pA.nblk, kBlock, 0, s>>>(rp, col, val, in, pA, out);
+  } else {
+    if (pT.nblk) k_spmv_plain<<<pT.nblk, kBlock, 0, s>>>(rpt, colt, valt, in, pT, out);
+  }
+  SCUC_CUDA(cudaGetLastError());
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  return leave();
+}
+
+}  // namespace scuc
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using scuc::Handle;
+
+struct scuc_lp {
+  Handle* h;
+};
+
+extern "C" {
+
+void scuc_default_params(scuc_solve_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->tol = 1e-4;
+  p->max_iter = 1000000;
+  p->time_limit_s = 3600.0;
+  p->check_every = 64;
+  p->precision = SCUC_FP64;
+  p->use_scaling = 1;
+  p->sigma0 = 1.0;
+  p->lambda_in = 0.0;
+  p->lambda_safety = 1.01;
+  p->power_max_iter = 500;
+  p->power_tol = 1e-4;
+  p->power_seed = 0x5EED;
+  p->restart_suff = 0.2;
+  p->restart_nec = 0.8;
+  p->restart_long = 0.2;
+  p->polish_factor = 10.0;
+  p->polish_stall = 20;
+  p->use_graph = 1;
+  p->profile = 0;
+  p->device_ptrs = 0;
+}
+
+static int sense_to_box(int32_t m, const char* sense, const double* rhs, const double* range,
+                        std::vector<double>& lo, std::vector<double>& hi) {
+  lo.assign(m, -INFINITY);
+  hi.assign(m, INFINITY);
+  if (m > 0 && (!sense || !rhs)) {
+    scuc::set_error("sense and rhs are required");
+    return SCUC_E_INVALID;
+  }
+  for (int32_t i = 0; i < m; i++) {
+    switch (sense[i]) {
+      case 'G': lo[i] = rhs[i]; break;
+      case 'L': hi[i] = rhs[i]; break;
+      case 'E': lo[i] = rhs[i]; hi[i] = rhs[i]; break;
+      case 'R':
+        if (!range || !(range[i] >= 0.0)) {
+          scuc::set_error("row %d: 'R' needs range >= 0", i);
+          return SCUC_E_INVALID;
+        }
+        lo[i] = rhs[i];
+        hi[i] = rhs[i] + range[i];
+        break;
+      default:
+        scuc::set_error("row %d: unknown sense", i);
+        return SCUC_E_INVALID;
+    }
+  }
+  return SCUC_OK;
+}
+
+int scuc_lp_create(scuc_lp** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                   const int32_t* col, const double* val, const double* c, const double* xl,
+                   const double* xu, const char* sense, const double* rhs, const double* range,
+                   void* cuda_stream) {
+  if (!out) { scuc::set_error("out is NULL"); return SCUC_E_INVALID; }
+  if (m < 0) { scuc::set_error("m < 0"); return SCUC_E_INVALID; }
+  std::vector<double> lo, hi;
+  SCUC_TRY(sense_to_box(m, sense, rhs, range, lo, hi));
+  return scuc_lp_create_box(out, m, n, nnz, row_ptr, col, val, c, xl, xu, lo.data(), hi.data(),
+                            cuda_stream);
+}
+
+int scuc_lp_create_box(scuc_lp** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                       const int32_t* col, const double* val, const double* c, const double* xl,
+                       const double* xu, const double* lo, const double* hi, void* cuda_stream) {
+  if (!out) { scuc::set_error("out is NULL"); return SCUC_E_INVALID; }
+  *out = nullptr;
+  Handle* h = nullptr;
+  SCUC_TRY(scuc::create_handle(&h, m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi, cuda_stream));
+  *out = new scuc_lp{h};
+  return SCUC_OK;
+}
+
+int scuc_lp_dims(const scuc_lp* lp, int32_t* m, int32_t* n, int64_t* nnz) {
+  if (!lp) { scuc::set_error("null handle"); return SCUC_E_INVALID; }
+  if (m) *m = lp->h->m;
+  if (n) *n = lp->h->n;
+  if (nnz) *nnz = lp->h->nnz;
+  return SCUC_OK;
+}
+
+int scuc_lp_solve(scuc_lp* lp, const scuc_solve_params* p, const double* x0, const double* y0,
+                  double* x_out, double* y_out, double* z_out, scuc_solve_info* info) {
+  if (!lp) { scuc::set_error("null handle"); return SCUC_E_INVALID; }
+  scuc_solve_params d;
+  if (!p) { scuc_default_params(&d); p = &d; }
+  return lp->h->solve(*p, x0, y0, x_out, y_out, z_out, info);
+}
+
+int scuc_lp_get_log(const scuc_lp* lp, scuc_check_log* out, int32_t cap, int32_t* count) {
+  if (!lp || (!out && cap > 0)) { scuc::set_error("null argument"); return SCUC_E_INVALID; }
+  const Handle* h = lp->h;
+  int k = std::min(cap, h->last_nlog);
+  if (k > 0) SCUC_CUDA(cudaMemcpy(out, h->log_d, k * sizeof(scuc_check_log), cudaMemcpyDeviceToHost));
+  if (count) *count = k;
+  return SCUC_OK;
+}
+
+int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double* out_dev) {
+  if (!lp || !in_dev || !out_dev) { scuc::set_error("null argument"); return SCUC_E_INVALID; }
+  return lp->h->matvec(transpose, in_dev, out_dev);
+}
+
+int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_params* p,
+                        scuc_solve_info* infos) {
+  if (!lps || count < 0 || (count > 0 && !infos)) { scuc::set_error("null argument"); return SCUC_E_INVALID; }
+  for (int32_t i = 0; i < count; i++) {
+    scuc_solve_params q;
+    if (p) q = *p; else scuc_default_params(&q);
+    q.device_ptrs = 0;
+    SCUC_TRY(scuc_lp_solve(lps[i], &q, nullptr, nullptr, nullptr, nullptr, nullptr, &infos[i]));
+  }
+  return SCUC_OK;
+}
+
+void scuc_lp_destroy(scuc_lp* lp) {
+  if (!lp) return;
+  delete lp->h;
+  delete lp;
+}
+
+const char* scuc_last_error(void) { return scuc::g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Internal declarations of the SCUC LP library (host side).
+#pragma once
+#include <vector>
+
+#include "lp_kernels.cuh"
+
+namespace scuc {
+
+int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int>* rows_out,
+                    std::vector<int8_t>* gsz_out);
+int exclusive_scan(const int* in, int n, int* out, cudaStream_t s);
+
+struct Handle {
+  int32_t m = 0, n = 0;
+  int64_t nnz = 0;
+  int device = 0;
+  cudaStream_t user = nullptr, work = nullptr;
+  cudaEvent_t ev_user = nullptr, ev_work = nullptr, ev_slot[2] = {nullptr, nullptr};
+  std::vector<void*> allocs;
+  // matrix
+  int *rp = nullptr, *col = nullptr, *rpt = nullptr, *colt = nullptr, *permt = nullptr;
+  double *val = nullptr, *valt = nullptr, *vs = nullptr, *vst = nullptr;
+  float *vs32 = nullptr, *vst32 = nullptr;
+  Partition pA, pT;
+  // problem data (unscaled and scaled)
+  double *c = nullptr, *xl = nullptr, *xu = nullptr, *lo = nullptr, *hi = nullptr;
+  double *Dr = nullptr, *Dc = nullptr, *cs = nullptr, *xls = nullptr, *xus = nullptr,
+         *los = nullptr, *his = nullptr;
+  // iterates and scratch
+  double *x = nullptr, *x0 = nullptr, *xt = nullptr, *xbar = nullptr, *zbar = nullptr;
+  double *y = nullptr, *y0 = nullptr, *ybar = nullptr;
+  float *xt32 = nullptr, *y32 = nullptr;
+  double *qv = nullptr, *uv = nullptr, *wv = nullptr;
+  double *partP = nullptr, *partD = nullptr, *partRA = nullptr, *partRT = nullptr;
+  Ctrl* ctrl = nullptr;
+  Ctrl* ctrl_h = nullptr;
+  PowerCtrl* pctrl = nullptr;
+  scuc_check_log* log_d = nullptr;
+  int log_cap = 0, last_nlog = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* graph_key[3] = {nullptr, nullptr, nullptr};  // check_every, FP32 values, log
+  std::vector<cudaEvent_t> prof_ev;
+
+  ~Handle();
+  template <typename T>
+  int alloc(T** p, size_t count);
+  int init(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+           const double* val, const double* c, const double* xl, const double* xu,
+           const double* lo, const double* hi, cudaStream_t user);
+  int enter();
+  int leave();
+  DevLP dev() const;
+  int setup_scaling(int use_scaling, bool need_f32);
+  int power_method(const scuc_solve_params& p, double* lam, int* iters);
+  int ensure_log(int cap);
+  int launch_period(int check_every, bool profile);
+  int solve(const scuc_solve_params& p, const double* x0, const double* y0, double* xo,
+            double* yo, double* zo, scuc_solve_info* info);
+  int matvec(int transpose, const double* in, double* out);
+};
+
+int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                  const int32_t* col, const double* val, const double* c, const double* xl,
+                  const double* xu, const double* lo, const double* hi, void* stream);
+
+}  // namespace scuc

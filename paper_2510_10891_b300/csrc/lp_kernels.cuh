@@ -1,0 +1,278 @@
+// HPR iteration kernels (Eq. 9) with the dual/primal epilogues fused into the
+// SpMVs, the KKT-check SpMVs, and the single-block decide kernel.
+#pragma once
+#include "spmv.cuh"
+
+namespace scuc {
+
+struct DevLP {
+  int m, n;
+  // A (rows) and A^T (columns) in CSR, 32-bit indices
+  const int *rp, *col, *rpt, *colt;
+  const double *vs, *vst;      // scaled values  A_hat = D_r A D_c
+  const float *vs32, *vst32;   // FP32 copies (mixed precision)
+  const double *val, *valt;    // unscaled values
+  // scaled problem data
+  const double *c, *xl, *xu, *lo, *hi, *Dr, *Dc;
+  // iterates
+  double *x, *x0, *xt, *xbar, *zbar, *y, *y0, *ybar;
+  float *xt32, *y32;
+  // partial sums
+  double *partP, *partD, *partRA, *partRT;
+  Partition pA, pT;
+  Ctrl* ctrl;
+  scuc_check_log* log;
+};
+
+__device__ __forceinline__ double clampd(double v, double l, double u) {
+  return v < l ? l : (v > u ? u : v);
+}
+
+// ---------------------------------------------------------------------------
+// primal step over A^T y: x_bar = Pi_K(x + sigma (g - c)), reflection, Halpern
+// ---------------------------------------------------------------------------
+template <bool CHECK>
+struct PrimalEpi {
+  const DevLP& L;
+  double sigma, wa, wb;
+  bool fp64;
+  double acc[4];
+  __device__ void row(int j, double g) {
+    const double xj = L.x[j];
+    const double v = xj + sigma * (g - L.c[j]);
+    const double xb = clampd(v, L.xl[j], L.xu[j]);
+    const double xt = 2.0 * xb - xj;
+    const double x0j = L.x0[j];
+    const double xn = wa * x0j + wb * xt;
+    L.x[j] = xn;
+    if (fp64) L.xt[j] = xt;
+    else L.xt32[j] = (float)xt;
+    if (CHECK) {
+      double zb = (xb - v) / sigma;
+      if (zb > 0.0 && !isfinite(L.xl[j])) zb = 0.0;
+      if (zb < 0.0 && !isfinite(L.xu[j])) zb = 0.0;
+      L.xbar[j] = xb;
+      L.zbar[j] = zb;
+      acc[0] += (xb - xj) * (xb - xj);
+      acc[1] += (xn - x0j) * (xn - x0j);
+      acc[2] += L.c[j] * xb;
+      if (zb > 0.0) acc[3] += L.xl[j] * zb;
+      else if (zb < 0.0) acc[3] += L.xu[j] * zb;
+    }
+  }
+};
+
+template <bool CHECK>
+__global__ void __launch_bounds__(kBlock) k_primal(DevLP L, int j) {
+  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  const Ctrl* ctrl = L.ctrl;
+  if (ctrl->done) return;
+  const int64_t k = ctrl->k + j;
+  PrimalEpi<CHECK> epi{L, ctrl->sigma, 1.0 / (double)(k + 2), (double)(k + 1) / (double)(k + 2),
+                       ctrl->fp64_phase != 0, {0.0, 0.0, 0.0, 0.0}};
+  if (epi.fp64) {
+    spmv_block<double>(L.rpt, L.colt, L.vst, L.y, L.pT, smem, epi);
+  } else {
+    // FP32 matvec, FP32 accumulation; epilogue in FP64
+    struct Wrap {
+      PrimalEpi<CHECK>& e;
+      __device__ void row(int r, float a) { e.row(r, (double)a); }
+    } w{epi};
+    spmv_block<float>(L.rpt, L.colt, L.vst32, L.y32, L.pT, smem, w);
+  }
+  if (CHECK) block_store<4>(epi.acc, L.partP, L.pT.nblk);
+}
+
+// ---------------------------------------------------------------------------
+// dual step over A x_t: y_bar = P_s(y - s A x_t), Halpern
+// P_s(r) = r + s Pi_[lo,hi](-r/s) = max(r + s lo, 0) + min(r + s hi, 0)
+// ---------------------------------------------------------------------------
+template <bool CHECK>
+struct DualEpi {
+  const DevLP& L;
+  double s, wa, wb;
+  bool fp64;
+  double acc[2];
+  __device__ void row(int i, double q) {
+    const double yi = L.y[i];
+    const double r = yi - s * q;
+    const double yb = fmax(r + s * L.lo[i], 0.0) + fmin(r + s * L.hi[i], 0.0);
+    const double y0i = L.y0[i];
+    const double yn = wa * y0i + wb * (2.0 * yb - yi);
+    L.y[i] = yn;
+    if (!fp64) L.y32[i] = (float)yn;
+    if (CHECK) {
+      L.ybar[i] = yb;
+      acc[0] += (yb - yi) * (yb - yi);
+      acc[1] += (yn - y0i) * (yn - y0i);
+    }
+  }
+};
+
+template <bool CHECK>
+__global__ void __launch_bounds__(kBlock) k_dual(DevLP L, int j) {
+  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  const Ctrl* ctrl = L.ctrl;
+  if (ctrl->done) return;
+  const int64_t k = ctrl->k + j;
+  DualEpi<CHECK> epi{L, 1.0 / (ctrl->lambda * ctrl->sigma), 1.0 / (double)(k + 2),
+                     (double)(k + 1) / (double)(k + 2), ctrl->fp64_phase != 0, {0.0, 0.0}};
+  if (epi.fp64) {
+    spmv_block<double>(L.rp, L.col, L.vs, L.xt, L.pA, smem, epi);
+  } else {
+    struct Wrap {
+      DualEpi<CHECK>& e;
+      __device__ void row(int r, float a) { e.row(r, (double)a); }
+    } w{epi};
+    spmv_block<float>(L.rp, L.col, L.vs32, L.xt32, L.pA, smem, w);
+  }
+  if (CHECK) block_store<2>(epi.acc, L.partD, L.pA.nblk);
+}
+
+// ---------------------------------------------------------------------------
+// KKT check SpMVs (always FP64)
+// ---------------------------------------------------------------------------
+struct ResPrimalEpi {  // A x_bar: primal violation (unscaled) and y-part of dobj
+  const DevLP& L;
+  double beta;
+  double acc[2];
+  __device__ void row(int i, double a) {
+    const double lo = L.lo[i], hi = L.hi[i];
+    const double viol = (a - clampd(a, lo, hi)) * beta / L.Dr[i];
+    acc[0] += viol * viol;
+    const double yb = L.ybar[i];
+    if (yb > 0.0 && isfinite(lo)) acc[1] += lo * yb;
+    else if (yb < 0.0 && isfinite(hi)) acc[1] += hi * yb;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_res_primal(DevLP L) {
+  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  if (L.ctrl->done) return;
+  ResPrimalEpi epi{L, L.ctrl->beta, {0.0, 0.0}};
+  spmv_block<double>(L.rp, L.col, L.vs, L.xbar, L.pA, smem, epi);
+  block_store<2>(epi.acc, L.partRA, L.pA.nblk);
+}
+
+struct ResDualEpi {  // A^T y_bar: dual residual (unscaled)
+  const DevLP& L;
+  double gamma;
+  double acc[1];
+  __device__ void row(int j, double g) {
+    const double d = gamma * (L.c[j] - g - L.zbar[j]) / L.Dc[j];
+    acc[0] += d * d;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_res_dual(DevLP L) {
+  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  if (L.ctrl->done) return;
+  ResDualEpi epi{L, L.ctrl->gamma, {0.0}};
+  spmv_block<double>(L.rpt, L.colt, L.vst, L.ybar, L.pT, smem, epi);
+  block_store<1>(epi.acc, L.partRT, L.pT.nblk);
+}
+
+// fixed-order sum of one partial array by a single block
+__device__ double decide_sum(const double* p, int cnt) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += kDecideThreads) s += p[i];
+  __shared__ double sm[kDecideThreads / 32];
+  s = warp_sum(s);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kDecideThreads / 32; w++) r += sm[w];
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// decide: residuals, restart rule, sigma update, stop (one block)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
+  Ctrl* C = L.ctrl;
+  if (C->done) return;
+  const int nA = L.pA.nblk, nT = L.pT.nblk;
+  const double Sx = decide_sum(L.partP + 0 * nT, nT);
+  const double Sxa = decide_sum(L.partP + 1 * nT, nT);
+  const double pobj_s = decide_sum(L.partP + 2 * nT, nT);
+  const double dz = decide_sum(L.partP + 3 * nT, nT);
+  const double Sy = decide_sum(L.partD + 0 * nA, nA);
+  const double Sya = decide_sum(L.partD + 1 * nA, nA);
+  const double viol2 = decide_sum(L.partRA + 0 * nA, nA);
+  const double dy = decide_sum(L.partRA + 1 * nA, nA);
+  const double dres2 = decide_sum(L.partRT, nT);
+  if (threadIdx.x != 0) return;
+
+  const double sigma = C->sigma, lambda = C->lambda, bg = C->beta * C->gamma;
+  const double rp = sqrt(viol2) / (1.0 + C->bnorm);
+  const double rd = sqrt(dres2) / (1.0 + C->cnorm);
+  const double pobj = bg * pobj_s, dobj = bg * (dy + dz);
+  const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+  const double kkt = fmax(rp, fmax(rd, gap));
+  const int64_t k = C->k + chunk, t = C->t + chunk;
+  const double rho = sqrt(Sx / sigma + lambda * sigma * Sy);
+  C->rp = rp; C->rd = rd; C->gap = gap; C->pobj = pobj; C->dobj = dobj; C->kkt = kkt;
+  if (!C->fp64_phase) C->iters_fp32 += chunk;
+
+  int restart = 0, status = -1;
+  const int was_first = C->first_check;
+  if (!(kkt == kkt) || isinf(kkt)) {
+    status = SCUC_ST_NUMERICAL;
+  } else if (kkt <= C->tol) {
+    status = SCUC_ST_OPTIMAL;
+  } else {
+    if (C->first_check) {
+      C->rho0 = rho;
+      C->first_check = 0;
+      if ((double)k >= C->restart_long * (double)t) restart = 1;
+    } else {
+      if (rho <= C->restart_suff * C->rho0) restart = 1;
+      else if (rho <= C->restart_nec * C->rho0 && rho > C->rho_prev) restart = 1;
+      else if ((double)k >= C->restart_long * (double)t) restart = 1;
+    }
+    C->rho_prev = rho;
+  }
+  if (C->nlog < C->log_cap) {
+    scuc_check_log& e = L.log[C->nlog];
+    e.iter = t; e.restart = restart; e.first = was_first;
+    e.rp = rp; e.rd = rd; e.gap = gap; e.pobj = pobj; e.dobj = dobj; e.rho = rho;
+    e.sigma = sigma; e.fp64 = C->fp64_phase; e.pad = 0;
+  }
+  C->nlog++;
+  C->restart_pending = 0;
+  if (status < 0 && restart) {
+    const double ddx = sqrt(Sxa), ddy = sqrt(Sya);
+    if (ddx > 1e-10 && ddy > 1e-10) {
+      const double sig_new = ddx / (sqrt(lambda) * ddy);
+      C->sigma = sqrt(sig_new * sigma);
+    }
+    C->restart_pending = 1;
+    C->first_check = 1;
+    C->restarts++;
+  }
+  // mixed precision: move to FP64 matvecs near the tolerance or on a stall
+  if (status < 0 && C->precision == SCUC_MIXED && !C->fp64_phase) {
+    if (kkt < 0.9 * C->best_kkt) { C->best_kkt = kkt; C->stall = 0; }
+    else C->stall++;
+    if (kkt <= C->polish_factor * C->tol || C->stall >= C->polish_stall) C->fp64_phase = 1;
+  }
+  C->k = restart ? 0 : k;
+  C->t = t;
+  if (status < 0 && t >= C->max_iter) status = SCUC_ST_ITER_LIMIT;
+  if (status >= 0) {
+    C->status = status;
+    C->done = 1;
+  }
+}
+
+// restart: anchor <- current point (runs at the start of each period)
+__global__ void k_anchor(DevLP L) {
+  if (L.ctrl->done || !L.ctrl->restart_pending) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) L.x0[i] = L.x[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.m; i += stride) L.y0[i] = L.y[i];
+}
+
+}  // namespace scuc

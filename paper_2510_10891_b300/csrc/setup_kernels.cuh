@@ -1,0 +1,355 @@
+// Setup kernels: transpose, Pock-Chambolle scaling (Sec. 3.A), norms, power
+// method for lambda_max(A A^T) (Sec. 3), iterate initialisation and output.
+#pragma once
+#include "lp_kernels.cuh"
+
+namespace scuc {
+
+// ----------------------------- transpose ---------------------------------
+__global__ void k_count_cols(const int* __restrict__ col, int64_t nnz, int* __restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+    atomicAdd(cnt + col[e], 1);
+}
+
+// one warp per row: entries of row i go to their column's next free slot
+__global__ void k_scatter_t(const int* __restrict__ rp, const int* __restrict__ col, int m,
+                            int* __restrict__ cursor, int* __restrict__ colt, int* __restrict__ permt) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < m; i += nw)
+    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+      const int pos = atomicAdd(cursor + col[e], 1);
+      colt[pos] = i;
+      permt[pos] = e;
+    }
+}
+
+// sort the entries of short columns by row (thread per column, insertion)
+__global__ void k_sort_small(const int* __restrict__ rpt, int n, int* __restrict__ colt,
+                             int* __restrict__ permt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int a = rpt[j], b = rpt[j + 1];
+  if (b - a > 32) return;
+  for (int p = a + 1; p < b; p++) {
+    const int kr = colt[p], kp = permt[p];
+    int q = p - 1;
+    while (q >= a && colt[q] > kr) {
+      colt[q + 1] = colt[q];
+      permt[q + 1] = permt[q];
+      q--;
+    }
+    colt[q + 1] = kr;
+    permt[q + 1] = kp;
+  }
+}
+
+// sort the entries of one longer column (<= kSortCap) by row: bitonic in smem
+constexpr int kSortCap = 8192;
+__global__ void __launch_bounds__(1024) k_sort_block(const int* __restrict__ rpt, const int* __restrict__ cols,
+                                                     int* __restrict__ colt, int* __restrict__ permt) {
+  extern __shared__ unsigned long long keys[];
+  const int j = cols[blockIdx.x];
+  const int a = rpt[j], L = rpt[j + 1] - a;
+  int P = 1;
+  while (P < L) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x)
+    keys[i] = i < L ? (((unsigned long long)(unsigned)colt[a + i]) << 32) | (unsigned)permt[a + i]
+                    : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const unsigned long long u = keys[i], v = keys[ixj];
+          if ((u > v) == up) { keys[i] = v; keys[ixj] = u; }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    colt[a + i] = (int)(keys[i] >> 32);
+    permt[a + i] = (int)(keys[i] & 0xffffffffu);
+  }
+}
+
+__global__ void k_gather_t(const int* __restrict__ permt, int64_t nnz, const double* __restrict__ val,
+                           double* __restrict__ valt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+    valt[e] = val[permt[e]];
+}
+
+// ------------------------- scan (exclusive) ------------------------------
+constexpr int kScan = 1024;
+__global__ void __launch_bounds__(kScan) k_scan_block(const int* __restrict__ in, int n, int* __restrict__ out,
+                                                      int* __restrict__ bsum) {
+  __shared__ int ws[kScan / 32];
+  const int i = blockIdx.x * kScan + threadIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int v = i < n ? in[i] : 0;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  const int incl = x + (w > 0 ? ws[w - 1] : 0);
+  if (i < n) out[i] = incl - v;
+  if (threadIdx.x == kScan - 1) bsum[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ boff) {
+  const int i = blockIdx.x * kScan + threadIdx.x;
+  if (i < n) out[i] += boff[blockIdx.x];
+}
+
+// --------------------------- scaling -------------------------------------
+// row sums in entry order, column sums in row order (sequential, one thread
+// per row/column), then D = 1/sqrt(sum) (1 for empty rows/columns)
+__global__ void k_abs_sum_inv_sqrt(const int* __restrict__ rp, const double* __restrict__ val, int m,
+                                   int use_scaling, double* __restrict__ D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  if (!use_scaling) { D[i] = 1.0; return; }
+  double s = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; e++) s += fabs(val[e]);
+  D[i] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+}
+
+// vs[e] = (Dr[i] * val[e]) * Dc[col[e]]   (warp per row)
+__global__ void k_scale_vals(const int* __restrict__ rp, const int* __restrict__ col,
+                             const double* __restrict__ val, int m, const double* __restrict__ Dr,
+                             const double* __restrict__ Dc, double* __restrict__ vs) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < m; i += nw) {
+    const double d = Dr[i];
+    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) vs[e] = (d * val[e]) * Dc[col[e]];
+  }
+}
+
+__global__ void k_scale_vecs(int m, int n, const double* __restrict__ Dr, const double* __restrict__ Dc,
+                             const double* __restrict__ c, const double* __restrict__ xl,
+                             const double* __restrict__ xu, const double* __restrict__ lo,
+                             const double* __restrict__ hi, double* __restrict__ cs,
+                             double* __restrict__ xls, double* __restrict__ xus,
+                             double* __restrict__ los, double* __restrict__ his) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    cs[j] = Dc[j] * c[j];
+    xls[j] = xl[j] / Dc[j];
+    xus[j] = xu[j] / Dc[j];
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    los[i] = Dr[i] * lo[i];
+    his[i] = Dr[i] * hi[i];
+  }
+}
+
+__device__ __forceinline__ double bound_mag(double lo, double hi) {
+  double b = 0.0;
+  if (isfinite(lo) && fabs(lo) > b) b = fabs(lo);
+  if (isfinite(hi) && fabs(hi) > b) b = fabs(hi);
+  return b;
+}
+
+// stage 1 of the four norms: {sum bmag(los,his)^2, sum cs^2, sum bmag(lo,hi)^2, sum c^2}
+constexpr int kNormBlocks = 592;  // 4 x 148 SMs
+__global__ void __launch_bounds__(kBlock) k_norms_partial(int m, int n, const double* __restrict__ los,
+                                                          const double* __restrict__ his,
+                                                          const double* __restrict__ cs,
+                                                          const double* __restrict__ lo,
+                                                          const double* __restrict__ hi,
+                                                          const double* __restrict__ c,
+                                                          double* __restrict__ part) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const double a = bound_mag(los[i], his[i]);
+    const double b = bound_mag(lo[i], hi[i]);
+    v[0] += a * a;
+    v[2] += b * b;
+  }
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    v[1] += cs[j] * cs[j];
+    v[3] += c[j] * c[j];
+  }
+  block_store<4>(v, part, gridDim.x);
+}
+
+// stage 2: beta = 1 + ||b_hat||, gamma = 1 + ||c_hat|| (1 when unscaled),
+// bnorm = ||b||, cnorm = ||c|| of the unscaled LP
+__global__ void __launch_bounds__(kDecideThreads) k_norms_final(const double* __restrict__ part, int nb,
+                                                                int use_scaling, Ctrl* C) {
+  const double b2 = decide_sum(part + 0 * nb, nb);
+  const double c2 = decide_sum(part + 1 * nb, nb);
+  const double ub2 = decide_sum(part + 2 * nb, nb);
+  const double uc2 = decide_sum(part + 3 * nb, nb);
+  if (threadIdx.x == 0) {
+    C->beta = use_scaling ? 1.0 + sqrt(b2) : 1.0;
+    C->gamma = use_scaling ? 1.0 + sqrt(c2) : 1.0;
+    C->bnorm = sqrt(ub2);
+    C->cnorm = sqrt(uc2);
+  }
+}
+
+__global__ void k_normalize(int m, int n, const Ctrl* __restrict__ C, double* __restrict__ cs,
+                            double* __restrict__ xls, double* __restrict__ xus,
+                            double* __restrict__ los, double* __restrict__ his) {
+  const double beta = C->beta, gamma = C->gamma;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    xls[j] /= beta;
+    xus[j] /= beta;
+    cs[j] /= gamma;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    los[i] /= beta;
+    his[i] /= beta;
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, int64_t k, float* __restrict__ b) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k; e += stride) b[e] = (float)a[e];
+}
+
+// --------------------------- power method ---------------------------------
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j) {
+  uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(kBlock) k_power_seed(int n, uint64_t seed, double* __restrict__ q,
+                                                       double* __restrict__ part) {
+  double v[1] = {0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const double a = 0.5 + (double)(splitmix64_at(seed, (uint64_t)j) >> 11) * 0x1.0p-53;
+    q[j] = a;
+    v[0] += a * a;
+  }
+  block_store<1>(v, part, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kDecideThreads) k_power_seed_norm(const double* part, int nb, PowerCtrl* P) {
+  const double s = decide_sum(part, nb);
+  if (threadIdx.x == 0) P->nw = sqrt(s);
+}
+
+struct StoreEpi {  // out[r] = acc, and sum of squares
+  double* out;
+  double acc[1];
+  __device__ void row(int r, double a) {
+    out[r] = a;
+    acc[0] += a * a;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_power_spmv(const int* __restrict__ rp, const int* __restrict__ col,
+                                                       const double* __restrict__ val,
+                                                       const double* __restrict__ in, Partition part,
+                                                       double* __restrict__ out, double* __restrict__ psum,
+                                                       const PowerCtrl* __restrict__ P) {
+  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  if (P->done) return;
+  StoreEpi epi{out, {0.0}};
+  spmv_block<double>(rp, col, val, in, part, smem, epi);
+  block_store<1>(epi.acc, psum, part.nblk);
+}
+
+__global__ void __launch_bounds__(kDecideThreads) k_power_decide(const double* pu, int nA, const double* pw,
+                                                                 int nT, PowerCtrl* P) {
+  if (P->done) return;
+  const double lam = decide_sum(pu, nA);
+  const double w2 = decide_sum(pw, nT);
+  if (threadIdx.x != 0) return;
+  P->it++;
+  P->lam = lam;
+  P->nw = sqrt(w2);
+  // stop on a zero product, on a relative change <= tol, or at the limit
+  if (P->nw == 0.0) P->done = 1;
+  else if (P->it > 1 && fabs(lam - P->lam_prev) <= P->tol * lam) P->done = 1;
+  else if (P->it >= P->max_iter) P->done = 1;
+  P->lam_prev = lam;
+}
+
+// q = w / ||w||  (not needed once the estimate is final)
+__global__ void k_power_norm(int n, const double* __restrict__ w, double* __restrict__ q, const PowerCtrl* P) {
+  if (P->done) return;
+  const double nw = P->nw;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) q[j] = w[j] / nw;
+}
+
+__global__ void k_power_norm_seed(int n, double* __restrict__ q, const PowerCtrl* P) {
+  const double nq = P->nw;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) q[j] /= nq;
+}
+
+// ------------------------ iterate init / output ---------------------------
+__global__ void k_init_iterates(DevLP L, const double* __restrict__ xin, const double* __restrict__ yin) {
+  const double beta = L.ctrl->beta, gamma = L.ctrl->gamma;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L.n; j += stride) {
+    const double v = xin ? xin[j] / (beta * L.Dc[j]) : 0.0;
+    const double x = clampd(v, L.xl[j], L.xu[j]);
+    L.x[j] = x;
+    L.x0[j] = x;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.m; i += stride) {
+    double v = yin ? yin[i] / (gamma * L.Dr[i]) : 0.0;
+    if (!isfinite(L.lo[i]) && v > 0.0) v = 0.0;
+    if (!isfinite(L.hi[i]) && v < 0.0) v = 0.0;
+    L.y[i] = v;
+    L.y0[i] = v;
+    L.y32[i] = (float)v;
+  }
+}
+
+__global__ void k_finalize(DevLP L, double* __restrict__ xo, double* __restrict__ yo, double* __restrict__ zo) {
+  const double beta = L.ctrl->beta, gamma = L.ctrl->gamma;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L.n; j += stride) {
+    if (xo) xo[j] = beta * L.Dc[j] * L.xbar[j];
+    if (zo) zo[j] = gamma * L.zbar[j] / L.Dc[j];
+  }
+  if (yo)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.m; i += stride)
+      yo[i] = gamma * L.Dr[i] * L.ybar[i];
+}
+
+// unscaled product (matvec entry point)
+struct PlainEpi {
+  double* out;
+  __device__ void row(int r, double a) { out[r] = a; }
+};
+
+__global__ void __launch_bounds__(kBlock) k_spmv_plain(const int* __restrict__ rp, const int* __restrict__ col,
+                                                       const double* __restrict__ val,
+                                                       const double* __restrict__ in, Partition part,
+                                                       double* __restrict__ out) {
+  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  PlainEpi epi{out};
+  spmv_block<double>(rp, col, val, in, part, smem, epi);
+}
+
+}  // namespace scuc

@@ -1,0 +1,114 @@
+"""Python face of the C ABI (argument marshalling only; every step of the
+solve runs in the CUDA library)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_params(**kw) -> L.SolveParams:
+    p = L.SolveParams()
+    L.lib().scuc_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": L.FP64, "mixed": L.MIXED}[v]
+        if not hasattr(p, k):
+            raise TypeError("unknown solve parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def info_dict(info: L.SolveInfo) -> dict:
+    d = {f[0].rstrip("_"): getattr(info, f[0]) for f in L.SolveInfo._fields_}
+    d["status_name"] = L.STATUS.get(d["status"], "?")
+    return d
+
+
+class LP:
+    """An LP  min c^T x, lo <= A x <= hi, xl <= x <= xu  resident on the GPU.
+
+    ``src`` is a SCUCInstance or a dict with m, n, row_ptr, col, val, c, xl, xu
+    and either (sense, rhs, rng_) or (lo, hi).  ``stream`` is a raw
+    cudaStream_t value (e.g. ``torch.cuda.current_stream().cuda_stream``)."""
+
+    def __init__(self, src, stream: int | None = None):
+        if not isinstance(src, dict):
+            src = dict(m=src.m, n=src.n, row_ptr=src.row_ptr, col=src.col, val=src.val, c=src.c,
+                       xl=src.xl, xu=src.xu, sense=src.sense, rhs=src.rhs, rng_=src.rng_)
+        self.m, self.n = int(src["m"]), int(src["n"])
+        rp = np.ascontiguousarray(src["row_ptr"], dtype=np.int64)
+        col = np.ascontiguousarray(src["col"], dtype=np.int32)
+        val = _f64(src["val"])
+        c, xl, xu = _f64(src["c"]), _f64(src["xl"]), _f64(src["xu"])
+        self.nnz = int(rp[-1])
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        if "lo" in src:
+            lo, hi = _f64(src["lo"]), _f64(src["hi"])
+            L.check(L.lib().scuc_lp_create_box(C.byref(h), self.m, self.n, self.nnz, _ptr(rp),
+                                               _ptr(col), _ptr(val), _ptr(c), _ptr(xl), _ptr(xu),
+                                               _ptr(lo), _ptr(hi), st))
+        else:
+            sense = np.ascontiguousarray(src["sense"], dtype=np.uint8)
+            rhs, rng = _f64(src["rhs"]), _f64(src["rng_"])
+            L.check(L.lib().scuc_lp_create(C.byref(h), self.m, self.n, self.nnz, _ptr(rp), _ptr(col),
+                                           _ptr(val), _ptr(c), _ptr(xl), _ptr(xu), _ptr(sense),
+                                           _ptr(rhs), _ptr(rng), st))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib().scuc_lp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def solve(self, x0=None, y0=None, want=("x", "y", "z"), **params) -> dict:
+        """Host-buffer solve: returns x, y, z (numpy), info and the check log."""
+        p = default_params(**params)
+        p.device_ptrs = 0
+        out = {k: np.zeros(self.n if k in ("x", "z") else self.m) for k in want}
+        info = L.SolveInfo()
+        L.check(L.lib().scuc_lp_solve(self.h, C.byref(p),
+                                      _ptr(_f64(x0)) if x0 is not None else None,
+                                      _ptr(_f64(y0)) if y0 is not None else None,
+                                      _ptr(out.get("x")), _ptr(out.get("y")), _ptr(out.get("z")),
+                                      C.byref(info)))
+        out["info"] = info_dict(info)
+        out["log"] = self.log(info.nlog)
+        return out
+
+    def solve_device(self, x_out=None, y_out=None, z_out=None, x0=None, y0=None, **params) -> dict:
+        """Device-buffer solve: arguments are torch CUDA float64 tensors (or None)."""
+        p = default_params(**params)
+        p.device_ptrs = 1
+        dp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        info = L.SolveInfo()
+        L.check(L.lib().scuc_lp_solve(self.h, C.byref(p), dp(x0), dp(y0), dp(x_out), dp(y_out),
+                                      dp(z_out), C.byref(info)))
+        return info_dict(info)
+
+    def log(self, cap=None) -> list:
+        cap = 4096 if cap is None else max(0, int(cap))
+        buf = (L.CheckLog * max(cap, 1))()
+        cnt = C.c_int32()
+        L.check(L.lib().scuc_lp_get_log(self.h, buf, cap, C.byref(cnt)))
+        return [{f[0]: getattr(buf[i], f[0]) for f in L.CheckLog._fields_ if f[0] != "pad"}
+                for i in range(cnt.value)]
+
+    def matvec(self, inp, out, transpose=False):
+        """out = A inp (or A^T inp) on torch CUDA float64 tensors."""
+        L.check(L.lib().scuc_lp_matvec(self.h, 1 if transpose else 0, C.c_void_p(inp.data_ptr()),
+                                       C.c_void_p(out.data_ptr())))
+        return out
