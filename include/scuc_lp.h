@@ -99,6 +99,9 @@ typedef struct {
   int32_t profile;        /* 1: time the two SpMV kernels with CUDA events  */
   int32_t device_ptrs;    /* 1: x0/y0 and x/y/z_out of scuc_lp_solve are
                              device pointers on the handle's device         */
+  int32_t restart_ref;    /* reference rho0 of the restart tests: 0 = rho at
+                             the first check of the cycle; 1 = rho at the
+                             check that made the last restart               */
 } scuc_solve_params;
 
 typedef struct {

@@ -358,7 +358,8 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       memcpy(x0, x, sizeof(double) * (size_t)n);
       memcpy(y0, y, sizeof(double) * (size_t)m);
       k = 0;
-      first_check = 1;
+      if (prm->restart_ref == 1) rho0 = rho; /* decrease is measured from here */
+      else first_check = 1;
       restarts++;
     }
   }

@@ -45,6 +45,9 @@ typedef struct {
   double restart_nec;    /* 0.8 */
   double restart_long;   /* 0.2 */
   int32_t log_cap;       /* capacity of the check log                     */
+  int32_t restart_ref;   /* reference rho0 of the restart tests: 0 = metric
+                            at the first check of the cycle, 1 = metric at
+                            the check that made the last restart           */
 } orc_params;
 
 typedef struct {

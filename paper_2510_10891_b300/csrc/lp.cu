@@ -498,6 +498,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.restart_suff = p.restart_suff;
   C.restart_nec = p.restart_nec;
   C.restart_long = p.restart_long;
+  C.restart_ref = p.restart_ref;
   C.polish_factor = p.polish_factor;
   C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
   C.check_every = p.check_every;
@@ -657,6 +658,7 @@ void scuc_default_params(scuc_solve_params* p) {
   p->use_graph = 1;
   p->profile = 0;
   p->device_ptrs = 0;
+  p->restart_ref = 0;
 }
 
 static int sense_to_box(int32_t m, const char* sense, const double* rhs, const double* range,

@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
       C->sigma = sqrt(sig_new * sigma);
     }
     C->restart_pending = 1;
-    C->first_check = 1;
+    if (C->restart_ref == 1) C->rho0 = rho;  // decrease is measured from here
+    else C->first_check = 1;
     C->restarts++;
   }
   // mixed precision: move to FP64 matvecs near the tolerance or on a stall
