@@ -102,6 +102,11 @@ typedef struct {
   int32_t restart_ref;    /* reference rho0 of the restart tests: 0 = rho at
                              the first check of the cycle; 1 = rho at the
                              check that made the last restart               */
+  int32_t restart_metric; /* rho of the restart tests: 0 = sqrt(||dx||^2/sigma
+                             + lambda sigma ||dy||^2) with dx = x_bar - x,
+                             dy = y_bar - y; 1 = the same plus 2<A dx, dy>
+                             (the norm in which the iteration is
+                             nonexpansive); 2 = KKT error                   */
 } scuc_solve_params;
 
 typedef struct {

@@ -239,6 +239,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   double *x = dalloc(n), *x0 = dalloc(n), *xt = dalloc(n), *xb = dalloc(n), *zb = dalloc(n);
   double *g = dalloc(n), *y = dalloc(m), *y0 = dalloc(m), *yb = dalloc(m), *q = dalloc(m);
   double *xo = dalloc(n), *yo = dalloc(m), *zo = dalloc(n);
+  double *dyv = dalloc(m), *pv = dalloc(m);
 
   /* starting point, in scaled variables, projected onto K and the dual cone */
   for (int32_t j = 0; j < n; j++) {
@@ -289,6 +290,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       double ybar = r + s * clampd(-r / s, los[i], his[i]);
       if (is_check) {
         yb[i] = ybar;
+        dyv[i] = ybar - y[i];
         dyy += (ybar - y[i]) * (ybar - y[i]);
       }
       y[i] = wa * y0[i] + wb * (2.0 * ybar - y[i]);  /* Halpern step */
@@ -309,7 +311,20 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
     for (int32_t i = 0; i < m; i++) yo[i] = gamma * Dr[i] * yb[i];
     orc_kkt(lp, xo, yo, zo, last);
     have_out = 1;
-    const double rho = sqrt(dxx / sigma + lambda * sigma * dyy);
+    /* restart metric: fixed-point residual of the step, optionally in the
+     * metric of the iteration (cross term with A(x_bar - x) = A x_t - A x_bar),
+     * or the KKT error */
+    double rho;
+    if (prm->restart_metric == 2) {
+      rho = last[5];
+    } else {
+      double cross = 0.0;
+      if (prm->restart_metric == 1) {
+        spmv(m, lp->row_ptr, lp->col, vs, xb, pv);
+        for (int32_t i = 0; i < m; i++) cross += (q[i] - pv[i]) * dyv[i];
+      }
+      rho = sqrt(fmax(0.0, dxx / sigma + lambda * sigma * dyy + 2.0 * cross));
+    }
 
     int restart = 0;
     const int was_first = first_check;
@@ -388,7 +403,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   }
   free(Dr); free(Dc); free(vs); free(cs); free(xls); free(xus); free(los); free(his);
   free(x); free(x0); free(xt); free(xb); free(zb); free(g); free(y); free(y0); free(yb);
-  free(q); free(xo); free(yo); free(zo);
+  free(q); free(xo); free(yo); free(zo); free(dyv); free(pv);
   return 0;
 }
 

@@ -48,6 +48,10 @@ typedef struct {
   int32_t restart_ref;   /* reference rho0 of the restart tests: 0 = metric
                             at the first check of the cycle, 1 = metric at
                             the check that made the last restart           */
+  int32_t restart_metric;/* 0: rho^2 = ||dx||^2/sigma + lambda sigma ||dy||^2;
+                            1: the same plus the cross term 2<A dx, dy> (the
+                            norm in which the iteration is nonexpansive);
+                            2: the KKT error max(r_p, r_d, gap)            */
 } orc_params;
 
 typedef struct {

@@ -20,7 +20,8 @@ class SolveParams(C.Structure):
                 ("restart_suff", C.c_double), ("restart_nec", C.c_double),
                 ("restart_long", C.c_double), ("polish_factor", C.c_double),
                 ("polish_stall", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
-                ("device_ptrs", C.c_int32), ("restart_ref", C.c_int32)]
+                ("device_ptrs", C.c_int32), ("restart_ref", C.c_int32),
+                ("restart_metric", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -45,7 +45,7 @@ struct Ctrl {
   double tol, sigma, lambda, beta, gamma, bnorm, cnorm;
   double restart_suff, restart_nec, restart_long, polish_factor;
   int64_t max_iter;
-  int32_t check_every, polish_stall, log_cap, precision, restart_ref, pad0;
+  int32_t check_every, polish_stall, log_cap, precision, restart_ref, restart_metric;
   int64_t k, t, iters_fp32;
   double rho0, rho_prev, best_kkt;
   int32_t first_check, done, status, restart_pending;

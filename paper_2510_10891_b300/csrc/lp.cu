@@ -307,7 +307,8 @@ int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, c
   SCUC_TRY(alloc(&y32, m));
   SCUC_TRY(alloc(&partP, 4 * (size_t)pT.nblk));
   SCUC_TRY(alloc(&partD, 2 * (size_t)pA.nblk));
-  SCUC_TRY(alloc(&partRA, 2 * (size_t)std::max(pA.nblk, kNormBlocks)));
+  SCUC_TRY(alloc(&partRA, 3 * (size_t)std::max(pA.nblk, kNormBlocks)));
+  SCUC_TRY(alloc(&dychk, m));
   SCUC_TRY(alloc(&partRT, 4 * (size_t)std::max(pT.nblk, kNormBlocks)));
   SCUC_TRY(alloc(&ctrl, 1));
   SCUC_TRY(alloc(&pctrl, 1));
@@ -343,6 +344,7 @@ DevLP Handle::dev() const {
   L.c = cs; L.xl = xls; L.xu = xus; L.lo = los; L.hi = his; L.Dr = Dr; L.Dc = Dc;
   L.x = x; L.x0 = x0; L.xt = xt; L.xbar = xbar; L.zbar = zbar; L.y = y; L.y0 = y0; L.ybar = ybar;
   L.xt32 = xt32; L.y32 = y32;
+  L.qchk = uv; L.dychk = dychk;  // uv: power-method scratch, free during iterations
   L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
   L.pA = pA; L.pT = pT;
   L.ctrl = ctrl; L.log = log_d;
@@ -499,6 +501,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.restart_nec = p.restart_nec;
   C.restart_long = p.restart_long;
   C.restart_ref = p.restart_ref;
+  C.restart_metric = p.restart_metric;
   C.polish_factor = p.polish_factor;
   C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
   C.check_every = p.check_every;
@@ -659,6 +662,7 @@ void scuc_default_params(scuc_solve_params* p) {
   p->profile = 0;
   p->device_ptrs = 0;
   p->restart_ref = 0;
+  p->restart_metric = 0;
 }
 
 static int sense_to_box(int32_t m, const char* sense, const double* rhs, const double* range,

@@ -30,6 +30,7 @@ struct Handle {
   double *x = nullptr, *x0 = nullptr, *xt = nullptr, *xbar = nullptr, *zbar = nullptr;
   double *y = nullptr, *y0 = nullptr, *ybar = nullptr;
   float *xt32 = nullptr, *y32 = nullptr;
+  double* dychk = nullptr;
   double *qv = nullptr, *uv = nullptr, *wv = nullptr;
   double *partP = nullptr, *partD = nullptr, *partRA = nullptr, *partRT = nullptr;
   Ctrl* ctrl = nullptr;

@@ -17,6 +17,7 @@ struct DevLP {
   // iterates
   double *x, *x0, *xt, *xbar, *zbar, *y, *y0, *ybar;
   float *xt32, *y32;
+  double *qchk, *dychk;        // A x_t and y_bar - y at a check iteration
   // partial sums
   double *partP, *partD, *partRA, *partRT;
   Partition pA, pT;
@@ -103,6 +104,8 @@ struct DualEpi {
     if (!fp64) L.y32[i] = (float)yn;
     if (CHECK) {
       L.ybar[i] = yb;
+      L.qchk[i] = q;
+      L.dychk[i] = yb - yi;
       acc[0] += (yb - yi) * (yb - yi);
       acc[1] += (yn - y0i) * (yn - y0i);
     }
@@ -132,10 +135,10 @@ __global__ void __launch_bounds__(kBlock) k_dual(DevLP L, int j) {
 // ---------------------------------------------------------------------------
 // KKT check SpMVs (always FP64)
 // ---------------------------------------------------------------------------
-struct ResPrimalEpi {  // A x_bar: primal violation (unscaled) and y-part of dobj
+struct ResPrimalEpi {  // A x_bar: primal violation (unscaled), y-part of dobj, <A dx, dy>
   const DevLP& L;
   double beta;
-  double acc[2];
+  double acc[3];
   __device__ void row(int i, double a) {
     const double lo = L.lo[i], hi = L.hi[i];
     const double viol = (a - clampd(a, lo, hi)) * beta / L.Dr[i];
@@ -143,15 +146,16 @@ struct ResPrimalEpi {  // A x_bar: primal violation (unscaled) and y-part of dob
     const double yb = L.ybar[i];
     if (yb > 0.0 && isfinite(lo)) acc[1] += lo * yb;
     else if (yb < 0.0 && isfinite(hi)) acc[1] += hi * yb;
+    acc[2] += (L.qchk[i] - a) * L.dychk[i];   // A(x_bar - x) = A x_t - A x_bar
   }
 };
 
 __global__ void __launch_bounds__(kBlock) k_res_primal(DevLP L) {
   __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
   if (L.ctrl->done) return;
-  ResPrimalEpi epi{L, L.ctrl->beta, {0.0, 0.0}};
+  ResPrimalEpi epi{L, L.ctrl->beta, {0.0, 0.0, 0.0}};
   spmv_block<double>(L.rp, L.col, L.vs, L.xbar, L.pA, smem, epi);
-  block_store<2>(epi.acc, L.partRA, L.pA.nblk);
+  block_store<3>(epi.acc, L.partRA, L.pA.nblk);
 }
 
 struct ResDualEpi {  // A^T y_bar: dual residual (unscaled)
@@ -203,6 +207,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   const double viol2 = decide_sum(L.partRA + 0 * nA, nA);
   const double dy = decide_sum(L.partRA + 1 * nA, nA);
   const double dres2 = decide_sum(L.partRT, nT);
+  const double cross = decide_sum(L.partRA + 2 * nA, nA);
   if (threadIdx.x != 0) return;
 
   const double sigma = C->sigma, lambda = C->lambda, bg = C->beta * C->gamma;
@@ -212,7 +217,10 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
   const double kkt = fmax(rp, fmax(rd, gap));
   const int64_t k = C->k + chunk, t = C->t + chunk;
-  const double rho = sqrt(Sx / sigma + lambda * sigma * Sy);
+  const double rho = C->restart_metric == 2
+                         ? kkt
+                         : sqrt(fmax(0.0, Sx / sigma + lambda * sigma * Sy +
+                                              (C->restart_metric == 1 ? 2.0 * cross : 0.0)));
   C->rp = rp; C->rd = rd; C->gap = gap; C->pobj = pobj; C->dobj = dobj; C->kkt = kkt;
   if (!C->fp64_phase) C->iters_fp32 += chunk;
 
