@@ -81,7 +81,9 @@ typedef struct {
   double time_limit_s;    /* 3600 (wall time, checked at KKT checks)        */
   int32_t check_every;    /* 64: iterations between KKT/restart checks      */
   int32_t precision;      /* SCUC_FP64                                      */
-  int32_t use_scaling;    /* 1: Pock-Chambolle + normalisation (Sec. 3.A)   */
+  int32_t use_scaling;    /* 1: Pock-Chambolle + normalisation (Sec. 3.A);
+                             2: 10 Ruiz passes first (the HPR-LP default
+                             that Sec. 3.A replaces); 0: none               */
   double sigma0;          /* 1.0: initial primal step sigma                 */
   double lambda_in;       /* 0: run the power method; > 0: use this value   */
   double lambda_safety;   /* 1.01: lambda = safety * power estimate         */
@@ -107,6 +109,7 @@ typedef struct {
                              dy = y_bar - y; 1 = the same plus 2<A dx, dy>
                              (the norm in which the iteration is
                              nonexpansive); 2 = KKT error                   */
+  int32_t sigma_update;   /* 1: sigma update at restarts; 0: keep sigma0    */
 } scuc_solve_params;
 
 typedef struct {

@@ -67,20 +67,42 @@ void orc_scale(const orc_lp* lp, int32_t use_scaling, double* Dr, double* Dc, do
   const int32_t m = lp->m, n = lp->n;
   for (int32_t i = 0; i < m; i++) Dr[i] = 1.0;
   for (int32_t j = 0; j < n; j++) Dc[j] = 1.0;
-  if (use_scaling) {
-    /* D_r,i = 1/sqrt(sum_j |a_ij|),  D_c,j = 1/sqrt(sum_i |a_ij|) */
-    double* cs = dalloc(n);
+  double* rs = dalloc(m);
+  double* cs = dalloc(n);
+  if (use_scaling == 2) {
+    /* Ruiz: 10 passes; each divides every row and column of the current
+     * D_r A D_c by the square root of its largest magnitude */
+    for (int pass = 0; pass < 10; pass++) {
+      for (int32_t i = 0; i < m; i++) rs[i] = 0.0;
+      for (int32_t j = 0; j < n; j++) cs[j] = 0.0;
+      for (int32_t i = 0; i < m; i++)
+        for (int64_t k = lp->row_ptr[i]; k < lp->row_ptr[i + 1]; k++) {
+          const double a = fabs((Dr[i] * lp->val[k]) * Dc[lp->col[k]]);
+          if (a > rs[i]) rs[i] = a;
+          if (a > cs[lp->col[k]]) cs[lp->col[k]] = a;
+        }
+      for (int32_t i = 0; i < m; i++) Dr[i] *= rs[i] > 0.0 ? 1.0 / sqrt(rs[i]) : 1.0;
+      for (int32_t j = 0; j < n; j++) Dc[j] *= cs[j] > 0.0 ? 1.0 / sqrt(cs[j]) : 1.0;
+    }
+  }
+  if (use_scaling >= 1) {
+    /* Pock-Chambolle (alpha = 1) on the current matrix:
+     * D_r,i *= 1/sqrt(sum_j |a_ij|),  D_c,j *= 1/sqrt(sum_i |a_ij|) */
+    for (int32_t j = 0; j < n; j++) cs[j] = 0.0;
     for (int32_t i = 0; i < m; i++) {
       double s = 0.0;
       for (int64_t k = lp->row_ptr[i]; k < lp->row_ptr[i + 1]; k++) {
-        s += fabs(lp->val[k]);
-        cs[lp->col[k]] += fabs(lp->val[k]);
+        const double a = fabs((Dr[i] * lp->val[k]) * Dc[lp->col[k]]);
+        s += a;
+        cs[lp->col[k]] += a;
       }
-      Dr[i] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+      rs[i] = s;
     }
-    for (int32_t j = 0; j < n; j++) Dc[j] = cs[j] > 0.0 ? 1.0 / sqrt(cs[j]) : 1.0;
-    free(cs);
+    for (int32_t i = 0; i < m; i++) Dr[i] *= rs[i] > 0.0 ? 1.0 / sqrt(rs[i]) : 1.0;
+    for (int32_t j = 0; j < n; j++) Dc[j] *= cs[j] > 0.0 ? 1.0 / sqrt(cs[j]) : 1.0;
   }
+  free(rs);
+  free(cs);
   /* A_hat = D_r A D_c; bounds and cost in the scaled variables x = D_c x_hat */
   for (int32_t i = 0; i < m; i++)
     for (int64_t k = lp->row_ptr[i]; k < lp->row_ptr[i + 1]; k++)
@@ -366,7 +388,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       for (int32_t i = 0; i < m; i++) ddy += (y[i] - y0[i]) * (y[i] - y0[i]);
       ddx = sqrt(ddx);
       ddy = sqrt(ddy);
-      if (ddx > 1e-10 && ddy > 1e-10) {
+      if (prm->sigma_update && ddx > 1e-10 && ddy > 1e-10) {
         double sig_new = ddx / (sqrt(lambda) * ddy);
         sigma = sqrt(sig_new * sigma); /* equal-weight geometric smoothing */
       }

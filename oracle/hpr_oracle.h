@@ -34,7 +34,8 @@ typedef struct {
   double tol;            /* stop when max(r_p, r_d, gap) <= tol            */
   int64_t max_iter;
   int32_t check_every;   /* KKT / restart evaluation period               */
-  int32_t use_scaling;   /* Pock-Chambolle + normalisation (Sec. 3.A)     */
+  int32_t use_scaling;   /* 1: Pock-Chambolle + normalisation (Sec. 3.A);
+                            2: Ruiz (10 passes) first, then as 1; 0: none */
   double sigma0;         /* initial primal step                           */
   double lambda_in;      /* > 0: use this lambda instead of power method  */
   double lambda_safety;  /* lambda = safety * power-method estimate       */
@@ -52,6 +53,7 @@ typedef struct {
                             1: the same plus the cross term 2<A dx, dy> (the
                             norm in which the iteration is nonexpansive);
                             2: the KKT error max(r_p, r_d, gap)            */
+  int32_t sigma_update;  /* 1: sigma update at restarts; 0: keep sigma0    */
 } orc_params;
 
 typedef struct {

@@ -21,7 +21,7 @@ class SolveParams(C.Structure):
                 ("restart_long", C.c_double), ("polish_factor", C.c_double),
                 ("polish_stall", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("device_ptrs", C.c_int32), ("restart_ref", C.c_int32),
-                ("restart_metric", C.c_int32)]
+                ("restart_metric", C.c_int32), ("sigma_update", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -47,7 +47,8 @@ struct Ctrl {
   int64_t max_iter;
   int32_t check_every, polish_stall, log_cap, precision, restart_ref, restart_metric;
   int64_t k, t, iters_fp32;
-  double rho0, rho_prev, best_kkt;
+  double rho0, rho_prev, best_kkt, s_step;
+  int32_t sigma_update, pad1;
   int32_t first_check, done, status, restart_pending;
   int32_t restarts, nlog, fp64_phase, stall;
   double kkt, rp, rd, gap, pobj, dobj;

@@ -345,6 +345,7 @@ DevLP Handle::dev() const {
   L.x = x; L.x0 = x0; L.xt = xt; L.xbar = xbar; L.zbar = zbar; L.y = y; L.y0 = y0; L.ybar = ybar;
   L.xt32 = xt32; L.y32 = y32;
   L.qchk = uv; L.dychk = dychk;  // uv: power-method scratch, free during iterations
+  L.coef = coef; L.coef_w = coef;
   L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
   L.pA = pA; L.pT = pT;
   L.ctrl = ctrl; L.log = log_d;
@@ -354,8 +355,17 @@ DevLP Handle::dev() const {
 // Pock-Chambolle scaling + normalisation (Sec. 3.A), then the unscaled norms
 int Handle::setup_scaling(int use_scaling, bool need_f32) {
   cudaStream_t s = work;
-  if (m) k_abs_sum_inv_sqrt<<<(m + kBlock - 1) / kBlock, kBlock, 0, s>>>(rp, val, m, use_scaling, Dr);
-  if (n) k_abs_sum_inv_sqrt<<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(rpt, valt, n, use_scaling, Dc);
+  // D_r = D_c = 1; Ruiz passes (use_scaling = 2); Pock-Chambolle (>= 1).
+  // Factors of a pass are computed from the same D, then applied.
+  k_fill<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(Dr, m, Dc, n, 1.0);
+  const int mb = (m + kBlock - 1) / kBlock, nb = (n + kBlock - 1) / kBlock;
+  const int npass = use_scaling == 2 ? 11 : (use_scaling == 1 ? 1 : 0);
+  for (int pass = 0; pass < npass; pass++) {
+    const int use_max = pass < npass - 1 ? 1 : 0;  // Ruiz passes, then the sum pass
+    if (m) k_scale_factor<<<mb, kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, 0, use_max, uv);
+    if (n) k_scale_factor<<<nb, kBlock, 0, s>>>(rpt, colt, valt, n, Dr, Dc, 1, use_max, wv);
+    k_mul2<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(Dr, uv, m, Dc, wv, n);
+  }
   if (m) k_scale_vals<<<grid_for((int64_t)m * 32), kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, vs);
   if (nnz) k_gather_t<<<grid_for(nnz), kBlock, 0, s>>>(permt, nnz, vs, vst);
   k_scale_vecs<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(m, n, Dr, Dc, c, xl, xu, lo, hi, cs, xls, xus,
@@ -464,15 +474,15 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   if (x0_in) {
     if (p.device_ptrs) xin = x0_in;
     else {
-      SCUC_CUDA(cudaMemcpyAsync(wv, x0_in, n * sizeof(double), cudaMemcpyHostToDevice, s));
-      xin = wv;
+      SCUC_CUDA(cudaMemcpyAsync(xt, x0_in, n * sizeof(double), cudaMemcpyHostToDevice, s));
+      xin = xt;  // x_t and y_bar are unused until the first iteration
     }
   }
   if (y0_in) {
     if (p.device_ptrs) yin = y0_in;
     else {
-      SCUC_CUDA(cudaMemcpyAsync(uv, y0_in, m * sizeof(double), cudaMemcpyHostToDevice, s));
-      yin = uv;
+      SCUC_CUDA(cudaMemcpyAsync(ybar, y0_in, m * sizeof(double), cudaMemcpyHostToDevice, s));
+      yin = ybar;
     }
   }
 
@@ -480,9 +490,6 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   double lambda = p.lambda_in;
   int piters = 0;
   if (!(lambda > 0.0)) {
-    // the warm-start buffers double as power-method scratch: move them aside
-    if (xin == wv) { SCUC_CUDA(cudaMemcpyAsync(xt, wv, n * sizeof(double), cudaMemcpyDeviceToDevice, s)); xin = xt; }
-    if (yin == uv) { SCUC_CUDA(cudaMemcpyAsync(ybar, uv, m * sizeof(double), cudaMemcpyDeviceToDevice, s)); yin = ybar; }
     double est = 0.0;
     SCUC_TRY(power_method(p, &est, &piters));
     lambda = p.lambda_safety * est;
@@ -502,6 +509,8 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.restart_long = p.restart_long;
   C.restart_ref = p.restart_ref;
   C.restart_metric = p.restart_metric;
+  C.sigma_update = p.sigma_update;
+  C.s_step = 1.0 / (lambda * p.sigma0);
   C.polish_factor = p.polish_factor;
   C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
   C.check_every = p.check_every;
@@ -513,6 +522,16 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.first_check = 1; C.done = 0; C.status = -1; C.restart_pending = 0;
   C.restarts = 0; C.nlog = 0; C.fp64_phase = mixed ? 0 : 1; C.stall = 0;
   SCUC_CUDA(cudaMemcpyAsync(ctrl, &C, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  if (p.check_every > coef_cap) {
+    SCUC_TRY(alloc(&coef, 2 * (size_t)p.check_every));
+    coef_cap = p.check_every;
+  }
+  coef_h.resize(2 * (size_t)p.check_every);
+  for (int j = 0; j < p.check_every; j++) {  // Halpern weights of the first period (k = j)
+    coef_h[2 * j] = 1.0 / (double)(j + 2);
+    coef_h[2 * j + 1] = (double)(j + 1) / (double)(j + 2);
+  }
+  SCUC_CUDA(cudaMemcpyAsync(coef, coef_h.data(), coef_h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   const DevLP L = dev();
   k_init_iterates<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L, xin, yin);
   SCUC_CUDA(cudaGetLastError());
@@ -529,7 +548,8 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
       prof_ev.push_back(e);
     }
   }
-  const void* key[3] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d};
+  const void* key[4] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
+                        (const void*)coef};
   if (use_graph && (!graph_exec || memcmp(key, graph_key, sizeof(key)) != 0)) {
     if (graph_exec) { cudaGraphExecDestroy(graph_exec); graph_exec = nullptr; }
     cudaGraph_t g;
@@ -663,6 +683,7 @@ void scuc_default_params(scuc_solve_params* p) {
   p->device_ptrs = 0;
   p->restart_ref = 0;
   p->restart_metric = 0;
+  p->sigma_update = 1;
 }
 
 static int sense_to_box(int32_t m, const char* sense, const double* rhs, const double* range,

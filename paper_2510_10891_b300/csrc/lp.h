@@ -39,7 +39,10 @@ struct Handle {
   scuc_check_log* log_d = nullptr;
   int log_cap = 0, last_nlog = 0;
   cudaGraphExec_t graph_exec = nullptr;
-  const void* graph_key[3] = {nullptr, nullptr, nullptr};  // check_every, FP32 values, log
+  const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // check_every, FP32 values, log, coef
+  double* coef = nullptr;
+  int coef_cap = 0;
+  std::vector<double> coef_h;
   std::vector<cudaEvent_t> prof_ev;
 
   ~Handle();

@@ -18,6 +18,8 @@ struct DevLP {
   double *x, *x0, *xt, *xbar, *zbar, *y, *y0, *ybar;
   float *xt32, *y32;
   double *qchk, *dychk;        // A x_t and y_bar - y at a check iteration
+  const double* coef;          // Halpern weights {1/(k+2), (k+1)/(k+2)} per period slot
+  double* coef_w;              // same buffer, written by the decide kernel
   // partial sums
   double *partP, *partD, *partRA, *partRT;
   Partition pA, pT;
@@ -68,9 +70,8 @@ __global__ void __launch_bounds__(kBlock) k_primal(DevLP L, int j) {
   __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
-  const int64_t k = ctrl->k + j;
-  PrimalEpi<CHECK> epi{L, ctrl->sigma, 1.0 / (double)(k + 2), (double)(k + 1) / (double)(k + 2),
-                       ctrl->fp64_phase != 0, {0.0, 0.0, 0.0, 0.0}};
+  PrimalEpi<CHECK> epi{L, ctrl->sigma, L.coef[2 * j], L.coef[2 * j + 1], ctrl->fp64_phase != 0,
+                       {0.0, 0.0, 0.0, 0.0}};
   if (epi.fp64) {
     spmv_block<double>(L.rpt, L.colt, L.vst, L.y, L.pT, smem, epi);
   } else {
@@ -117,9 +118,8 @@ __global__ void __launch_bounds__(kBlock) k_dual(DevLP L, int j) {
   __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
-  const int64_t k = ctrl->k + j;
-  DualEpi<CHECK> epi{L, 1.0 / (ctrl->lambda * ctrl->sigma), 1.0 / (double)(k + 2),
-                     (double)(k + 1) / (double)(k + 2), ctrl->fp64_phase != 0, {0.0, 0.0}};
+  DualEpi<CHECK> epi{L, ctrl->s_step, L.coef[2 * j], L.coef[2 * j + 1], ctrl->fp64_phase != 0,
+                     {0.0, 0.0}};
   if (epi.fp64) {
     spmv_block<double>(L.rp, L.col, L.vs, L.xt, L.pA, smem, epi);
   } else {
@@ -194,6 +194,10 @@ __device__ double decide_sum(const double* p, int cnt) {
 // ---------------------------------------------------------------------------
 // decide: residuals, restart rule, sigma update, stop (one block)
 // ---------------------------------------------------------------------------
+__device__ long long decide_logic(const DevLP& L, Ctrl* C, int chunk, double Sx, double Sxa,
+                                  double pobj_s, double dz, double Sy, double Sya, double viol2,
+                                  double dy, double dres2, double cross);
+
 __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   Ctrl* C = L.ctrl;
   if (C->done) return;
@@ -208,7 +212,21 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   const double dy = decide_sum(L.partRA + 1 * nA, nA);
   const double dres2 = decide_sum(L.partRT, nT);
   const double cross = decide_sum(L.partRA + 2 * nA, nA);
-  if (threadIdx.x != 0) return;
+  __shared__ long long s_knew;
+  if (threadIdx.x == 0) s_knew = decide_logic(L, C, chunk, Sx, Sxa, pobj_s, dz, Sy, Sya, viol2, dy, dres2, cross);
+  __syncthreads();
+  // Halpern weights of the next period, computed once (FP64 division is slow on
+  // this part; every iterate update would otherwise divide per thread)
+  const long long kn = s_knew;
+  for (int j = threadIdx.x; j < chunk; j += kDecideThreads) {
+    L.coef_w[2 * j] = 1.0 / (double)(kn + j + 2);
+    L.coef_w[2 * j + 1] = (double)(kn + j + 1) / (double)(kn + j + 2);
+  }
+}
+
+__device__ long long decide_logic(const DevLP& L, Ctrl* C, int chunk, double Sx, double Sxa,
+                                  double pobj_s, double dz, double Sy, double Sya, double viol2,
+                                  double dy, double dres2, double cross) {
 
   const double sigma = C->sigma, lambda = C->lambda, bg = C->beta * C->gamma;
   const double rp = sqrt(viol2) / (1.0 + C->bnorm);
@@ -252,7 +270,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   C->restart_pending = 0;
   if (status < 0 && restart) {
     const double ddx = sqrt(Sxa), ddy = sqrt(Sya);
-    if (ddx > 1e-10 && ddy > 1e-10) {
+    if (C->sigma_update && ddx > 1e-10 && ddy > 1e-10) {
       const double sig_new = ddx / (sqrt(lambda) * ddy);
       C->sigma = sqrt(sig_new * sigma);
     }
@@ -269,11 +287,13 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   }
   C->k = restart ? 0 : k;
   C->t = t;
+  C->s_step = 1.0 / (C->lambda * C->sigma);
   if (status < 0 && t >= C->max_iter) status = SCUC_ST_ITER_LIMIT;
   if (status >= 0) {
     C->status = status;
     C->done = 1;
   }
+  return C->k;
 }
 
 // restart: anchor <- current point (runs at the start of each period)

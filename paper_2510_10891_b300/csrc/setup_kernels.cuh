@@ -119,6 +119,38 @@ __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__
 }
 
 // --------------------------- scaling -------------------------------------
+__global__ void k_fill(double* __restrict__ a, int na, double* __restrict__ b, int nb, double v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += stride) a[i] = v;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) b[i] = v;
+}
+
+// Factor of one scaling pass for each row of a CSR (thread per row,
+// sequential in entry order): 1/sqrt(max) (Ruiz) or 1/sqrt(sum) (Pock-
+// Chambolle) of |(Dr[row] * a) * Dc[col]| over the row, 1 for empty rows.
+// transposed = 1: the CSR is A^T (rows are columns of A).
+__global__ void k_scale_factor(const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ val, int m, const double* __restrict__ Dr,
+                               const double* __restrict__ Dc, int transposed, int use_max,
+                               double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; e++) {
+    const double a = transposed ? fabs((Dr[col[e]] * val[e]) * Dc[i]) : fabs((Dr[i] * val[e]) * Dc[col[e]]);
+    if (use_max) s = a > s ? a : s;
+    else s += a;
+  }
+  out[i] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+}
+
+__global__ void k_mul2(double* __restrict__ a, const double* __restrict__ fa, int na, double* __restrict__ b,
+                       const double* __restrict__ fb, int nb) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += stride) a[i] *= fa[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) b[i] *= fb[i];
+}
+
 // row sums in entry order, column sums in row order (sequential, one thread
 // per row/column), then D = 1/sqrt(sum) (1 for empty rows/columns)
 __global__ void k_abs_sum_inv_sqrt(const int* __restrict__ rp, const double* __restrict__ val, int m,

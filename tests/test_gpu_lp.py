@@ -146,6 +146,19 @@ def test_fixed_lambda_no_scaling_parity(P):
     assert g["info"]["lambda"] == lam
 
 
+@pytest.mark.parametrize("opts", [dict(use_scaling=2), dict(sigma_update=0, sigma0=0.5),
+                                  dict(restart_ref=1, restart_metric=1),
+                                  dict(restart_ref=1, restart_metric=2)])
+def test_option_parity(P, opts):
+    """Scaling, sigma and restart options take the same decisions on both sides."""
+    d = random_lp(300, 200, density=0.02, seed=1, long_rows=3, long_cols=2)
+    kw = dict(tol=1e-6, max_iter=20480, **opts)
+    o = oracle.hpr_solve(d, **kw)
+    g = P.LP(d).solve(**kw)
+    _compare_logs(g["log"], o["log"])
+    assert _rel(g["x"], o["x"]) < 1e-8
+
+
 def test_bounds_only_and_empty_rows(P):
     rng = np.random.default_rng(0)
     n = 37

@@ -226,8 +226,10 @@ def test_pock_chambolle_scaling_equivalence(scuc14):
     lp = oracle.as_lp(scuc14)
     a = oracle.hpr_solve(lp, tol=1e-7, max_iter=400000, use_scaling=1)
     b = oracle.hpr_solve(lp, tol=1e-7, max_iter=2000000, use_scaling=0)
-    assert a["info"]["status"] == 0 and b["info"]["status"] == 0
+    c = oracle.hpr_solve(lp, tol=1e-7, max_iter=400000, use_scaling=2)   # Ruiz + PC
+    assert a["info"]["status"] == 0 and b["info"]["status"] == 0 and c["info"]["status"] == 0
     assert a["info"]["pobj"] == pytest.approx(b["info"]["pobj"], rel=2e-6)
+    assert c["info"]["pobj"] == pytest.approx(b["info"]["pobj"], rel=2e-6)
 
 
 def test_scale_function_definition():
@@ -248,6 +250,25 @@ def test_scale_function_definition():
     assert s["beta"] == pytest.approx(beta, rel=1e-14)
     gamma = 1 + np.linalg.norm(Dc * lp["c"])
     assert s["gamma"] == pytest.approx(gamma, rel=1e-14)
+
+
+def test_ruiz_definition():
+    """use_scaling = 2: ten passes dividing rows and columns by sqrt of their
+    largest magnitude, then one Pock-Chambolle pass, all on the current matrix."""
+    lp = oracle.as_lp(random_lp(25, 15, density=0.3, seed=9))
+    s = oracle.scale(lp, use_scaling=2)
+    A = sp.csr_matrix((lp["val"], lp["col"], lp["row_ptr"]), shape=(lp["m"], lp["n"])).toarray()
+    Dr, Dc = np.ones(lp["m"]), np.ones(lp["n"])
+    for _ in range(10):
+        B = np.abs(Dr[:, None] * A * Dc[None, :])
+        Dr, Dc = Dr / np.sqrt(B.max(1)), Dc / np.sqrt(B.max(0))
+    B = np.abs(Dr[:, None] * A * Dc[None, :])
+    Dr, Dc = Dr / np.sqrt(B.sum(1)), Dc / np.sqrt(B.sum(0))
+    np.testing.assert_allclose(s["Dr"], Dr, rtol=1e-12)
+    np.testing.assert_allclose(s["Dc"], Dc, rtol=1e-12)
+    # after Ruiz the largest magnitude in every row/column is close to 1
+    Bh = np.abs(sp.csr_matrix((s["val"], lp["col"], lp["row_ptr"]), shape=A.shape).toarray())
+    assert Bh.max() <= 1.0 + 1e-12
 
 
 def test_eta_scaling_equivalence():
