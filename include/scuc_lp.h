@@ -129,6 +129,10 @@ typedef struct {
    * kernels (dual step = A x_tilde, primal step = A^T y)                  */
   double ms_dual_spmv, ms_primal_spmv;
   int64_t n_dual_spmv, n_primal_spmv;
+  /* the part of the above that ran with FP32 matvecs (MIXED)              */
+  double ms_dual_spmv_f32, ms_primal_spmv_f32;
+  int64_t n_dual_spmv_f32, n_primal_spmv_f32;
+  int64_t launches;       /* kernels launched by this solve                 */
 } scuc_solve_info;
 
 typedef struct {

@@ -32,7 +32,9 @@ class SolveInfo(C.Structure):
                 ("sigma", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("ms_dual_spmv", C.c_double),
                 ("ms_primal_spmv", C.c_double), ("n_dual_spmv", C.c_int64),
-                ("n_primal_spmv", C.c_int64)]
+                ("n_primal_spmv", C.c_int64), ("ms_dual_spmv_f32", C.c_double),
+                ("ms_primal_spmv_f32", C.c_double), ("n_dual_spmv_f32", C.c_int64),
+                ("n_primal_spmv_f32", C.c_int64), ("launches", C.c_int64)]
 
 
 class CheckLog(C.Structure):

@@ -365,7 +365,9 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
     if (m) k_scale_factor<<<mb, kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, 0, use_max, uv);
     if (n) k_scale_factor<<<nb, kBlock, 0, s>>>(rpt, colt, valt, n, Dr, Dc, 1, use_max, wv);
     k_mul2<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(Dr, uv, m, Dc, wv, n);
+    nlaunch += (m ? 1 : 0) + (n ? 1 : 0) + 1;
   }
+  nlaunch += 1 + (m ? 1 : 0) + (nnz ? 1 : 0) + 4;
   if (m) k_scale_vals<<<grid_for((int64_t)m * 32), kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, vs);
   if (nnz) k_gather_t<<<grid_for(nnz), kBlock, 0, s>>>(permt, nnz, vs, vst);
   k_scale_vecs<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(m, n, Dr, Dc, c, xl, xu, lo, hi, cs, xls, xus,
@@ -382,6 +384,7 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
     if (nnz) {
       k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vs, nnz, vs32);
       k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vst, nnz, vst32);
+      nlaunch += 2;
     }
     SCUC_CUDA(cudaGetLastError());
   }
@@ -398,6 +401,7 @@ int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters
   k_power_seed<<<kNormBlocks, kBlock, 0, s>>>(n, p.power_seed, qv, partRT);
   k_power_seed_norm<<<1, kDecideThreads, 0, s>>>(partRT, kNormBlocks, pctrl);
   k_power_norm_seed<<<grid_for(n), kBlock, 0, s>>>(n, qv, pctrl);
+  nlaunch += 3;
   SCUC_CUDA(cudaGetLastError());
   PowerCtrl P{};
   for (int it = 0; it < p.power_max_iter; it += 16) {
@@ -406,6 +410,7 @@ int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters
       if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, 0, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
       k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);
       k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, pctrl);
+      nlaunch += 2 + (pA.nblk ? 1 : 0) + (pT.nblk ? 1 : 0);
     }
     SCUC_CUDA(cudaGetLastError());
     SCUC_CUDA(cudaMemcpyAsync(&P, pctrl, sizeof(PowerCtrl), cudaMemcpyDeviceToHost, s));
@@ -452,6 +457,8 @@ int Handle::launch_period(int check_every, bool profile) {
   if (pT.nblk) k_res_dual<<<pT.nblk, kBlock, 0, s>>>(L);
   k_decide<<<1, kDecideThreads, 0, s>>>(L, check_every);
   SCUC_CUDA(cudaGetLastError());
+  nlaunch += 2 + (int64_t)check_every * ((pT.nblk ? 1 : 0) + (pA.nblk ? 1 : 0)) + (pA.nblk ? 1 : 0) +
+             (pT.nblk ? 1 : 0);
   return SCUC_OK;
 }
 
@@ -467,6 +474,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   cudaStream_t s = work;
   const auto t0 = clk::now();
   const bool mixed = p.precision == SCUC_MIXED;
+  const int64_t launch0 = nlaunch;
   SCUC_TRY(ensure_log(4096));
 
   // warm start in device memory
@@ -534,6 +542,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   SCUC_CUDA(cudaMemcpyAsync(coef, coef_h.data(), coef_h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   const DevLP L = dev();
   k_init_iterates<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L, xin, yin);
+  nlaunch += 1;
   SCUC_CUDA(cudaGetLastError());
   SCUC_CUDA(cudaStreamSynchronize(s));
   const auto t1 = clk::now();
@@ -554,23 +563,33 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
     if (graph_exec) { cudaGraphExecDestroy(graph_exec); graph_exec = nullptr; }
     cudaGraph_t g;
     SCUC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = nlaunch;
     int rc = launch_period(p.check_every, false);
+    nlaunch = before;  // captured, not launched
     cudaError_t ce2 = cudaStreamEndCapture(s, &g);
     if (rc != SCUC_OK) return rc;
     SCUC_CUDA(ce2);
+    size_t nodes = 0;
+    SCUC_CUDA(cudaGraphGetNodes(g, nullptr, &nodes));
+    graph_nodes = (int64_t)nodes;
     SCUC_CUDA(cudaGraphInstantiate(&graph_exec, g, 0));
     cudaGraphDestroy(g);
     memcpy(graph_key, key, sizeof(key));
   }
-  double ms_p = 0.0, ms_d = 0.0;
-  int64_t n_p = 0, n_d = 0;
+  double ms_p = 0.0, ms_d = 0.0, ms_p32 = 0.0, ms_d32 = 0.0;
+  int64_t n_p = 0, n_d = 0, n_p32 = 0, n_d32 = 0;
+  int phase64 = mixed ? 0 : 1;  // phase the next launched period runs in (profile mode)
   int timed_out = 0;
   int64_t launched = 0, seen = 0;
   const int inflight = p.profile ? 1 : 2;
   while (seen < nper) {
     while (launched < nper && launched - seen < inflight) {
-      if (use_graph) SCUC_CUDA(cudaGraphLaunch(graph_exec, s));
-      else SCUC_TRY(launch_period(p.check_every, p.profile != 0));
+      if (use_graph) {
+        SCUC_CUDA(cudaGraphLaunch(graph_exec, s));
+        nlaunch += graph_nodes;
+      } else {
+        SCUC_TRY(launch_period(p.check_every, p.profile != 0));
+      }
       SCUC_CUDA(cudaMemcpyAsync(ctrl_h + (launched & 1), ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
       SCUC_CUDA(cudaEventRecord(ev_slot[launched & 1], s));
       launched++;
@@ -583,10 +602,13 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
         SCUC_CUDA(cudaEventElapsedTime(&a, prof_ev[4 * j + 0], prof_ev[4 * j + 1]));
         SCUC_CUDA(cudaEventElapsedTime(&b, prof_ev[4 * j + 2], prof_ev[4 * j + 3]));
         ms_p += a; ms_d += b;
+        if (!phase64) { ms_p32 += a; ms_d32 += b; }
       }
       n_p += p.check_every; n_d += p.check_every;
+      if (!phase64) { n_p32 += p.check_every; n_d32 += p.check_every; }
     }
     const Ctrl& h = ctrl_h[seen & 1];
+    phase64 = h.fp64_phase;
     seen++;
     if (h.done) break;
     const double el = std::chrono::duration<double>(clk::now() - t0).count();
@@ -605,6 +627,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
     dyo = yo ? uv : nullptr;
   }
   k_finalize<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L, dxo, dyo, dzo);
+  nlaunch += 1;
   SCUC_CUDA(cudaGetLastError());
   if (!p.device_ptrs) {
     if (xo) SCUC_CUDA(cudaMemcpyAsync(xo, dxo, n * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -628,6 +651,9 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
     info->solve_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
     info->ms_dual_spmv = ms_d; info->ms_primal_spmv = ms_p;
     info->n_dual_spmv = n_d; info->n_primal_spmv = n_p;
+    info->ms_dual_spmv_f32 = ms_d32; info->ms_primal_spmv_f32 = ms_p32;
+    info->n_dual_spmv_f32 = n_d32; info->n_primal_spmv_f32 = n_p32;
+    info->launches = nlaunch - launch0;
   }
   return leave();
 }

@@ -41,6 +41,7 @@ struct Handle {
   cudaGraphExec_t graph_exec = nullptr;
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // check_every, FP32 values, log, coef
   double* coef = nullptr;
+  int64_t nlaunch = 0, graph_nodes = 0;  // kernels launched by this handle; nodes of the period graph
   int coef_cap = 0;
   std::vector<double> coef_h;
   std::vector<cudaEvent_t> prof_ev;

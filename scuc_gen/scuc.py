@@ -72,11 +72,19 @@ class SCUCConfig:
     penalty: float = 1000.0
     ctg_rating: float = 1.0
     lodf_candidates: int = 20
+    # "ptdf": Eq. 6 as written -- one system-wide balance row per hour and
+    # PTDF flow rows for the monitored lines (no angle variables);
+    # "btheta": nodal balance rows with bus angles and a row per line.
+    network: str = "ptdf"
+    # base-case monitored lines for "ptdf" (None: the N-1 lines, or L/100
+    # when there are no N-1 rows)
+    base_lines: int | None = None
 
 
 PRESETS = {
     # 14 buses, 20 lines, 5 units, T=24, no contingency rows: ~1.5k variables
-    "scuc14": SCUCConfig(buses=14, lines=20, units=5, T=24, contingencies=0, seed=1),
+    "scuc14": SCUCConfig(buses=14, lines=20, units=5, T=24, contingencies=0, seed=1,
+                         network="btheta"),
     # 2,000-bus random geometric grid, 300 units, 50 N-1 lines
     "scuc2k": SCUCConfig(buses=2000, lines=2800, units=300, T=36, contingencies=50, seed=2),
     # 6,500 buses, 1,000 units, 100 N-1 lines (successive-fixing loop)
@@ -312,13 +320,19 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
 
     # ---- variable layout ----
     nU = NVU * G * T
-    n = nU + 2 * B * T
+    ptdf_net = cfg.network == "ptdf"
+    if cfg.network not in ("ptdf", "btheta"):
+        raise ValueError("network must be 'ptdf' or 'btheta'")
+    n = nU + (1 if ptdf_net else 2) * B * T
 
     def uv(g, t, k):
         return (t * G + g) * NVU + k
 
-    def bv(b, t, k):
+    def bv(b, t, k):  # "btheta": (theta, d) per bus-hour
         return nU + (t * B + b) * 2 + k
+
+    def dcol(b, t):   # unserved-load column of bus b, hour t
+        return nU + t * B + b if ptdf_net else bv(b, t, 1)
 
     gg, tt = np.meshgrid(np.arange(G), np.arange(T), indexing="ij")
     gg, tt = gg.ravel(), tt.ravel()          # g-major, t-minor
@@ -337,11 +351,12 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
     c[base + U] = cl_s[gg]
     bb, bt = np.meshgrid(np.arange(B), np.arange(T), indexing="ij")
     bb, bt = bb.ravel(), bt.ravel()
-    th_col = bv(bb, bt, 0)
-    d_col = bv(bb, bt, 1)
-    xl[th_col] = -INF; xu[th_col] = INF
-    ref = bb == 0
-    xl[th_col[ref]] = 0.0; xu[th_col[ref]] = 0.0
+    d_col = dcol(bb, bt)
+    if not ptdf_net:
+        th_col = bv(bb, bt, 0)
+        xl[th_col] = -INF; xu[th_col] = INF
+        ref = bb == 0
+        xl[th_col[ref]] = 0.0; xu[th_col[ref]] = 0.0
     xu[d_col] = Dbt_s[bb, bt]
     c[d_col] = pen_s
 
@@ -354,8 +369,13 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
         rows.append(r.ravel()); cols.append(cidx.ravel()); vals.append(np.array(v).ravel())
 
     mU = NRU * GT
-    m_bus = B * T
-    m_line = L * T
+    if ptdf_net:
+        Kb = cfg.base_lines if cfg.base_lines is not None else (K if K > 0 else max(5, L // 100))
+        Kb = min(Kb, L)
+        m_bus, m_line = T, Kb * T
+    else:
+        Kb = 0
+        m_bus, m_line = B * T, L * T
     m_res = T
     m_ctg = K * T
     m = mU + m_bus + m_line + m_res + m_ctg
@@ -414,26 +434,52 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
     add(r, base + S1, 1.0); add(r, base + S2, 1.0); add(r, base + S3, 1.0); add(r, base + P, -1.0)
     sense[r] = ord("E")
 
-    # nodal balance (b,t): sum_{g in G_b}(p' + P^L u) + d - sum_l b_l (th_b - th_o) = D_bt
-    rb0 = mU
-    rowb = rb0 + bt * B + bb
-    add(rowb, d_col, 1.0)
-    rg = rb0 + tt * B + bus_g[gg]
-    add(rg, base + P, 1.0); add(rg, base + U, pmin_s[gg])
-    for t in range(T):
-        rf = rb0 + t * B + fr
-        rt = rb0 + t * B + to
-        add(rf, bv(fr, t, 0), -bl); add(rf, bv(to, t, 0), bl)
-        add(rt, bv(to, t, 0), -bl); add(rt, bv(fr, t, 0), bl)
-    sense[rowb] = ord("E"); rhs[rowb] = Dbt_s[bb, bt]
+    def add_ptdf_row(r, db, t):
+        """Row sum_b db_b (sum_{g in G_b}(p'_gt + P^L_g u_gt) + d_bt); returns
+        the load term sum_b db_b D_bt that goes to the row bounds."""
+        nzb = np.flatnonzero(db)
+        gsel = np.flatnonzero(db[bus_g] != 0.0)
+        add(np.full(len(gsel), r), uv(gsel, t, P), db[bus_g[gsel]])
+        add(np.full(len(gsel), r), uv(gsel, t, U), db[bus_g[gsel]] * pmin_s[gsel])
+        add(np.full(len(nzb), r), dcol(nzb, t), db[nzb])
+        return float((db[nzb] * Dbt_s[nzb, t]).sum())
 
-    # line flow (l,t): -F <= b_l (th_from - th_to) <= F
+    load = np.abs(flow).max(axis=1)
+    rb0 = mU
     rl0 = rb0 + m_bus
-    ll, lt = np.meshgrid(np.arange(L), np.arange(T), indexing="ij")
-    ll, lt = ll.ravel(), lt.ravel()
-    r = rl0 + lt * L + ll
-    add(r, bv(fr[ll], lt, 0), bl[ll]); add(r, bv(to[ll], lt, 0), -bl[ll])
-    sense[r] = ord("R"); rhs[r] = -F_s[ll]; rngv[r] = 2.0 * F_s[ll]
+    if ptdf_net:
+        # Eq. 6, first line: sum_g p_gt + sum_b d_bt = sum_b D_bt
+        ones = np.ones(B)
+        for t in range(T):
+            tot = add_ptdf_row(rb0 + t, ones, t)
+            sense[rb0 + t] = ord("E"); rhs[rb0 + t] = tot
+        # Eq. 6, second line for c = 0 on the monitored lines (PTDF rows)
+        mon_b = np.argsort(-load, kind="stable")[:Kb]
+        ptdf_b = dc.ptdf_rows(mon_b) if Kb > 0 else np.zeros((0, B))
+        ptdf_b[np.abs(ptdf_b) < cfg.ptdf_trunc] = 0.0
+        for kk in range(Kb):
+            for t in range(T):
+                r = rl0 + t * Kb + kk
+                const = add_ptdf_row(r, ptdf_b[kk], t)
+                sense[r] = ord("R"); rhs[r] = -F_s[mon_b[kk]] + const; rngv[r] = 2.0 * F_s[mon_b[kk]]
+    else:
+        # nodal balance (b,t): sum_{g in G_b}(p' + P^L u) + d - sum_l b_l (th_b - th_o) = D_bt
+        rowb = rb0 + bt * B + bb
+        add(rowb, d_col, 1.0)
+        rg = rb0 + tt * B + bus_g[gg]
+        add(rg, base + P, 1.0); add(rg, base + U, pmin_s[gg])
+        for t in range(T):
+            rf = rb0 + t * B + fr
+            rt = rb0 + t * B + to
+            add(rf, bv(fr, t, 0), -bl); add(rf, bv(to, t, 0), bl)
+            add(rt, bv(to, t, 0), -bl); add(rt, bv(fr, t, 0), bl)
+        sense[rowb] = ord("E"); rhs[rowb] = Dbt_s[bb, bt]
+        # line flow (l,t): -F <= b_l (th_from - th_to) <= F
+        ll, lt = np.meshgrid(np.arange(L), np.arange(T), indexing="ij")
+        ll, lt = ll.ravel(), lt.ravel()
+        r = rl0 + lt * L + ll
+        add(r, bv(fr[ll], lt, 0), bl[ll]); add(r, bv(to[ll], lt, 0), -bl[ll])
+        sense[r] = ord("R"); rhs[r] = -F_s[ll]; rngv[r] = 2.0 * F_s[ll]
 
     # spinning reserve (t): sum_g ((P^U - P^L) u - p') >= reserve_frac * D_t
     rr0 = rl0 + m_line
@@ -445,7 +491,6 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
     rc0 = rr0 + m_res
     ctg_info = None
     if K > 0:
-        load = np.abs(flow).max(axis=1)
         mon = np.argsort(-load, kind="stable")[:K]
         ptdf_m = dc.ptdf_rows(mon)                          # [K, B]
         num = ptdf_m[:, fr] - ptdf_m[:, to]                 # transfer PTDF of each line c
@@ -475,16 +520,10 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
         Fc = cfg.ctg_rating * F_s[mon]
         ctg_info = {"monitored": mon, "outage": outage, "lodf": lodf}
         for kk in range(K):
-            db = delta[kk]
-            nzb = np.flatnonzero(db)
-            gsel = np.flatnonzero(db[bus_g] != 0.0)
-            const = (db[nzb][:, None] * Dbt_s[nzb, :]).sum(axis=0)      # [T]
             for t in range(T):
                 r = rc0 + t * K + kk
-                add(np.full(len(gsel), r), uv(gsel, t, P), db[bus_g[gsel]])
-                add(np.full(len(gsel), r), uv(gsel, t, U), db[bus_g[gsel]] * pmin_s[gsel])
-                add(np.full(len(nzb), r), bv(nzb, t, 1), db[nzb])
-                sense[r] = ord("R"); rhs[r] = -Fc[kk] + const[t]; rngv[r] = 2.0 * Fc[kk]
+                const = add_ptdf_row(r, delta[kk], t)
+                sense[r] = ord("R"); rhs[r] = -Fc[kk] + const; rngv[r] = 2.0 * Fc[kk]
 
     R_ = np.concatenate(rows)
     C_ = np.concatenate(cols)
@@ -503,7 +542,8 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
                   p_init=p_init, etaP=etaP, etaC=etaC, ctg=ctg_info,
                   row_blocks=dict(unit=(0, mU), bus=(rb0, rb0 + m_bus), line=(rl0, rl0 + m_line),
                                   reserve=(rr0, rr0 + m_res), ctg=(rc0, rc0 + m_ctg)),
-                  col_blocks=dict(unit=(0, nU), bus=(nU, n)))
+                  col_blocks=dict(unit=(0, nU), bus=(nU, n)), network=cfg.network,
+                  base_lines=Kb)
     return SCUCInstance(cfg=cfg, m=m, n=n, row_ptr=A.indptr.astype(np.int64),
                         col=A.indices.astype(np.int32), val=A.data.astype(np.float64),
                         c=c, xl=xl, xu=xu, sense=sense, rhs=rhs, rng_=rngv, G=G, T=T,

@@ -41,6 +41,8 @@ def _schedule(inst):
                 take = min(left, p["segw"][g, h] / etaP)
                 x[base + S1 + h] = take
                 left -= take
+    if inst.cfg.network == "ptdf":
+        return x
     # angles: solve the nodal balance for theta (reference bus 0)
     from scuc_gen.scuc import _DCGrid
     dc = _DCGrid(B, p["fr"], p["to"], p["x"])
@@ -91,3 +93,29 @@ def test_dense_rows_present():
     assert b1 - b0 == 3 * inst.T
     lens = np.diff(inst.row_ptr)[b0:b1]
     assert lens.min() > 4
+
+
+def test_ptdf_network_rows():
+    """Eq. 6 as written (network="ptdf"): one balance row per hour, tight at
+    the proportional dispatch; base-case PTDF rows of the monitored lines hold
+    with the 1.5x margin the limits were sized with; no angle columns."""
+    from scuc_gen import SCUCConfig, make_scuc
+    inst = make_scuc(SCUCConfig(buses=60, lines=84, units=12, T=8, contingencies=4, seed=5,
+                                network="ptdf"))
+    G, T, B = inst.G, inst.T, inst.cfg.buses
+    assert inst.n == 7 * G * T + B * T
+    assert np.all(np.isfinite(inst.xl)) and np.all(np.isfinite(inst.xu))
+    lp = oracle.as_lp(inst)
+    x = _schedule(inst)
+    ax = inst.csr() @ x
+    blocks = inst.params["row_blocks"]
+    b0, b1 = blocks["bus"]
+    assert b1 - b0 == T
+    np.testing.assert_allclose(ax[b0:b1], lp["lo"][b0:b1], rtol=1e-12)
+    l0, l1 = blocks["line"]
+    assert l1 - l0 == 4 * T
+    w = (lp["hi"][l0:l1] - lp["lo"][l0:l1]) / 2
+    mid = (lp["hi"][l0:l1] + lp["lo"][l0:l1]) / 2
+    assert np.all(np.abs(ax[l0:l1] - mid) <= w / 1.5 + 2e-3 * np.abs(mid).max() + 1e-9)
+    u0, u1 = blocks["unit"]
+    assert np.all(ax[u0:u1] >= lp["lo"][u0:u1] - 1e-9) and np.all(ax[u0:u1] <= lp["hi"][u0:u1] + 1e-9)
