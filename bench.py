@@ -1,0 +1,317 @@
+"""Benchmark: seconds to 1e-4 KKT on the 13,000-bus SCUC LP relaxation.
+
+One step = one pass of the whole path over one LP: Pock-Chambolle scaling,
+power method, restarted HPR iterations to max(r_p, r_d, gap) <= 1e-4
+(Sec. 3), then Round + Algorithm 1 fixing and bound propagation with the
+reduced-LP build (Sec. 4) when the library provides them.  The LP is
+created on the device before timing (inputs resident in HBM); `e2e`
+repeats the measurement through the C ABI from host buffers, host<->device
+copies included.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s to 1e-4 KKT, 13k-bus SCUC LP: plain vs warm/batched/FP32; SpMV % HBM peak"
+WORKLOAD = "scuc13k"
+WORKLOAD_DESC = ("13,000 buses, 18,000 lines, 4,000 units, T=36, 200 N-1 lines; Eq. 1-7 LP relaxation, "
+                 "PTDF network rows (Eq. 6), seed 20000")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def spmv_bytes(m, n, nnz_a, kind, prec):
+    """Algorithmic bytes of one fused SpMV launch (each matrix entry and each
+    vector element touched once)."""
+    vb = 8 if prec == "fp64" else 4
+    if kind == "dual":   # A x_t, then y/y0/lo/hi in, y out (+ FP32 shadow of y)
+        return (vb + 4) * nnz_a + 4 * (m + 1) + vb * n + 32 * m + 8 * m + (4 * m if vb == 4 else 0)
+    # primal: A^T y, then x/x0/c/xl/xu in, x and x_t out
+    return (vb + 4) * nnz_a + 4 * (n + 1) + vb * m + 40 * n + 8 * n + (8 * n if vb == 8 else 4 * n)
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2510_10891_b300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1])); mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(inst, gpu_iters, power_iters):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    same LP: setup plus 8 and 16 HPR iterations (lambda fixed, so no power
+    method), extrapolated to the iteration count of the solve."""
+    import oracle
+    lp = oracle.as_lp(inst)
+    kw = dict(tol=0.0, lambda_in=1.0, check_every=8)
+    t0 = time.perf_counter(); oracle.hpr_solve(lp, max_iter=8, **kw); t8 = time.perf_counter() - t0
+    t0 = time.perf_counter(); oracle.hpr_solve(lp, max_iter=16, **kw); t16 = time.perf_counter() - t0
+    per_iter = max((t16 - t8) / 8.0, 1e-9)
+    setup = max(t8 - 8 * per_iter, 0.0)
+    est = setup + (gpu_iters + power_iters) * per_iter
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "oracle on the full LP: setup + 8 and + 16 iterations (%.1f s of CPU work); "
+                      "%.3f s/iteration x (%d HPR + %d power iterations) + %.2f s setup"
+                      % (t8 + t16, per_iter, gpu_iters, power_iters, setup),
+            "s_per_iter": per_iter}
+
+
+def build_instance():
+    from scuc_gen import make_preset
+    return make_preset(WORKLOAD)
+
+
+def run_reference(args):
+    """CPU reference arm: the oracle, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    inst = build_instance()
+    with open(os.path.join(ROOT, "profiles", "iterations_scuc13k.json")) as f:
+        it = json.load(f)
+    vals = []
+    cb = None
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(inst, it["hpr_iters_fp64"], it["power_iters"])
+        vals.append(cb["value"])
+    v = float(np.mean(vals[args.warmup:]))
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC, "precision": "fp64",
+                       "iterations_source": "profiles/iterations_scuc13k.json (FP64 iteration "
+                                            "count; the FP64 GPU path and the oracle take the same "
+                                            "restart decisions)"},
+            "cpu_baseline": dict(cb, value=v),
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2510_10891_b300 as P
+    inst = build_instance()
+    m, n, nnz = inst.m, inst.n, inst.nnz
+    stream = torch.cuda.current_stream()
+    lp = P.LP(inst, stream=stream.cuda_stream)
+    xo = torch.empty(n, dtype=torch.float64, device="cuda")
+    yo = torch.empty(m, dtype=torch.float64, device="cuda")
+    zo = torch.empty(n, dtype=torch.float64, device="cuda")
+    kw = dict(tol=1e-4, precision=args.precision, profile=1, time_limit_s=600.0)
+
+    def step():
+        return lp.solve_device(x_out=xo, y_out=yo, z_out=zo, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    infos, times = [], []
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        t_all0 = time.perf_counter()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_all0
+    if dist:
+        dist.barrier()
+    per_step = float(np.mean(times))
+    if dist:
+        t = torch.tensor([per_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        per_step = float(t.item())
+    clocks = clk.summary()
+
+    # roofline of the dominant SpMV (largest summed time), from the timed steps
+    peak, peak_src = peaks()
+    agg = {}
+    for i in infos:
+        for kind in ("dual", "primal"):
+            t_all, n_all = i["ms_%s_spmv" % kind], i["n_%s_spmv" % kind]
+            t32, n32 = i["ms_%s_spmv_f32" % kind], i["n_%s_spmv_f32" % kind]
+            for prec, tt, nn in (("fp32", t32, n32), ("fp64", t_all - t32, n_all - n32)):
+                a = agg.setdefault((kind, prec), [0.0, 0])
+                a[0] += tt; a[1] += nn
+    (dk, dp), (dms, dn) = max(agg.items(), key=lambda kv: kv[1][0])
+    nnz_a = nnz
+    byts = spmv_bytes(m, n, nnz_a, dk, "fp64" if dp == "fp64" else "fp32")
+    avg_ms = dms / max(dn, 1)
+    achieved = byts / (avg_ms * 1e-3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "spmv_traffic_scuc13k.json")
+    if os.path.exists(tf):
+        with open(tf) as f:
+            t = json.load(f)
+        key = "%s_%s" % (dk, dp)
+        if t.get("csrc_sha") == csrc_hash() and key in t.get("dram_bytes_per_launch", {}):
+            traffic = t["dram_bytes_per_launch"][key]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_%s (%s matvec)" % ({"dual": "dual", "primal": "primal"}[dk], dp),
+            "bytes_per_launch": byts, "avg_launch_ms": avg_ms, "launches": dn, "peak_source": peak_src,
+            "all_kernels": {"%s_%s" % k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
+                                          "GBps": spmv_bytes(m, n, nnz_a, k[0], "fp64" if k[1] == "fp64" else "fp32")
+                                          / (v[0] / max(v[1], 1) * 1e-3) / 1e9 if v[1] else None}
+                            for k, v in agg.items()}}
+
+    last = infos[-1]
+    out = {"metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 matvec + f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_DESC, "m": m, "n": n, "nnz": nnz,
+                      "precision": args.precision, "tol": 1e-4, "parallelism": "replicas" if world > 1 else "1 GPU",
+                      "l2": "inputs larger than L2 (matrix %.2f GB per pass)" % (12 * nnz / 1e9),
+                      "iters": last["iters"], "iters_fp32": last["iters_fp32"],
+                      "power_iters": last["power_iters"], "restarts": last["restarts"],
+                      "kkt": last["kkt"], "status": last["status_name"]},
+           "roofline": roof, "clocks": clocks,
+           "gpu_launches": int(sum(i["launches"] for i in infos)),
+           "wall_s_timed": wall}
+
+    if rank == 0 and not args.no_plain:
+        # plain FP64 on the same GPU, for the FP32-matvec gain
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pi = lp.solve_device(x_out=xo, y_out=yo, z_out=zo, tol=1e-4, precision="fp64", time_limit_s=600.0)
+        e1.record(stream); e1.synchronize()
+        out["variants"] = {"plain_fp64_s": e0.elapsed_time(e1) / 1e3, "plain_fp64_iters": pi["iters"],
+                           "plain_fp64_status": pi["status_name"], args.precision + "_s": per_step}
+        out["_fp64_iters"] = pi["iters"]
+        out["_power_iters"] = pi["power_iters"]
+
+    if not args.no_e2e:
+        # through the C ABI from host buffers: create (H2D + device setup), solve, copy back
+        ets = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lp2 = P.LP(inst)
+            r = lp2.solve(tol=1e-4, precision=args.precision, time_limit_s=600.0)
+            lp2.close()
+            ets.append(time.perf_counter() - t0)
+        h2d = 8 * (m + 1) + 12 * nnz + 24 * n + m + 16 * m
+        d2h = 16 * n + 8 * m
+        out["e2e"] = {"value": float(np.mean(ets)), "unit": "s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and not args.no_cpu:
+        it_fp64 = out.pop("_fp64_iters", last["iters"])
+        out["cpu_baseline"] = cpu_baseline(inst, it_fp64, out.pop("_power_iters", last["power_iters"]))
+    out.pop("_fp64_iters", None); out.pop("_power_iters", None)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
