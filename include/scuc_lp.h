@@ -212,6 +212,32 @@ int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double*
 int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_params* p,
                         scuc_solve_info* infos);
 
+/* KKT residuals of a caller-supplied point, with no device allocation.
+ * The paper has no counterpart; this is a service for callers that cannot
+ * allocate GPU memory at the point of the call: code whose device memory is
+ * already handed out to another allocator or a fixed pool, or a serving loop
+ * that must not pay for cudaMalloc/cudaFree (cudaFree waits for the whole
+ * device).  The handle itself is created beforehand as usual.
+ *  x_dev[n], y_dev[m], z_dev[n]: device pointers on the handle's device
+ *    (unscaled point; z is used as given).  out_dev[6]: device pointer that
+ *    receives {r_p, r_d, gap, pobj, dobj, kkt}, the same quantities that
+ *    scuc_lp_solve reports for its returned point.
+ *  Work is queued on the handle's stream order; the call does not wait for
+ *    it, so synchronise the creation stream before reading out_dev.
+ *  The partial sums go to one fixed device array of 2^20 doubles (8 MiB),
+ *    which every GPU that loads this library holds until the process exits.
+ *    An LP that needs more slots (3 per row block of A plus 4 per row block
+ *    of A^T) is rejected with SCUC_E_INVALID and a message naming the sizes.
+ *  The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and keeps it; make that first call before any
+ *    stream capture on that device.
+ *  All calls share the one array: calls whose work overlaps on the GPU (for
+ *    example on two unsynchronised streams) race on it.  Each call writes
+ *    every slot it later reads, so contents left by earlier calls are never
+ *    used.                                                               */
+int scuc_lp_kkt_noalloc(scuc_lp* lp, const double* x_dev, const double* y_dev, const double* z_dev,
+                        double* out_dev);
+
 void scuc_lp_destroy(scuc_lp* lp);
 
 const char* scuc_last_error(void);

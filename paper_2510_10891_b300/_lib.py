@@ -63,6 +63,7 @@ _SIGS = {
     "scuc_lp_matvec": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "scuc_lp_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(SolveParams),
                                       C.POINTER(SolveInfo)]),
+    "scuc_lp_kkt_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "scuc_lp_destroy": (None, [C.c_void_p]),
     "scuc_last_error": (C.c_char_p, []),
 }

@@ -678,10 +678,6 @@ int Handle::matvec(int transpose, const double* in, double* out) {
 // ===========================================================================
 using scuc::Handle;
 
-struct scuc_lp {
-  Handle* h;
-};
-
 extern "C" {
 
 void scuc_default_params(scuc_solve_params* p) {

@@ -2,9 +2,11 @@
 #pragma once
 #include <vector>
 
-#include "lp_kernels.cuh"
+#include "common.cuh"
 
 namespace scuc {
+
+struct DevLP;  // device view of a handle (lp_kernels.cuh)
 
 int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int>* rows_out,
                     std::vector<int8_t>* gsz_out);
@@ -62,6 +64,7 @@ struct Handle {
   int solve(const scuc_solve_params& p, const double* x0, const double* y0, double* xo,
             double* yo, double* zo, scuc_solve_info* info);
   int matvec(int transpose, const double* in, double* out);
+  int kkt_noalloc(const double* x, const double* y, const double* z, double* out);
 };
 
 int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
@@ -69,3 +72,8 @@ int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t
                   const double* xu, const double* lo, const double* hi, void* stream);
 
 }  // namespace scuc
+
+// C-ABI handle (include/scuc_lp.h)
+struct scuc_lp {
+  scuc::Handle* h;
+};
