@@ -24,19 +24,26 @@ void set_error(const char* fmt, ...);
     if (_r != SCUC_OK) return _r;   \
   } while (0)
 
-constexpr int kBlock = 256;     // threads per SpMV block
-constexpr int kNnzCap = 2048;   // nonzeros staged in shared memory per multi-row block
-constexpr int kMaxRows = 256;   // rows per multi-row block
-constexpr int kLongRow = 256;   // rows longer than this get a whole block
+constexpr int kBlock = 256;        // threads per SpMV block
+constexpr int kNnzCap = 2048;      // nonzeros staged in shared memory per staged block
+constexpr int kMaxRows = 256;      // rows per staged block
+constexpr int kShortMax = 32;      // short rows: <= this many nonzeros
+constexpr int kWarpRowMax = 4096;  // warp-per-row rows: up to this many; longer rows get a block
+constexpr int kStagedMinRun = 32;  // contiguous short-row runs at least this long are staged
+constexpr int kShortPerBlock = kBlock / 4;   // short-list rows per block (4 threads each)
+constexpr int kWarpRowsPerBlock = kBlock / 32;
 constexpr int kDecideThreads = 1024;
 
-// Row-block partition of a CSR matrix for the SpMV kernels: block b covers
-// rows [row[b], row[b+1]); gsz[b] = threads per row (1..32), or 0 when the
-// block is a single long row reduced by the whole block.
+// block types of a partition entry
+constexpr int kStagedBlock = 0, kShortListBlock = 1, kWarpRowsBlock = 2, kLongRowBlock = 3;
+
+// Partition of a CSR matrix for the SpMV kernels: desc[b] = {type, first,
+// count, gsz}.  Staged blocks cover rows [first, first + count) with gsz
+// threads per row; list blocks cover rows list[first .. first + count).
 struct Partition {
   int nblk = 0;
-  int* row = nullptr;
-  int8_t* gsz = nullptr;
+  int4* desc = nullptr;
+  int* list = nullptr;
 };
 
 // Device-resident solver state.  Parameters are written by the host before a

@@ -38,46 +38,72 @@ static int grid_for(int64_t work, int block = kBlock) {
   return (int)g;
 }
 
-// Row-block partition (host): rows longer than kLongRow get a block each;
-// other rows are packed in order into blocks of <= kMaxRows rows and
-// <= kNnzCap nonzeros; threads per row = largest power of two <= 256/rows.
-int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int>* rows_out,
-                    std::vector<int8_t>* gsz_out) {
-  std::vector<int> rows;
-  std::vector<int8_t> gsz;
-  rows.reserve(m / 64 + 16);
-  int r = 0;
-  rows.push_back(0);
-  while (r < m) {
+// Partition (host): rows longer than kWarpRowMax get a block each; rows of
+// kShortMax+1..kWarpRowMax nonzeros get a warp each (8 per block); contiguous
+// runs of >= kStagedMinRun short rows are packed into staged blocks of
+// <= kMaxRows rows / <= kNnzCap nonzeros (threads per row = largest power of
+// two with gsz * rows <= kBlock); the remaining short rows get 4 threads each
+// (64 per block).  Longest work first.
+int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
+                    std::vector<int>* list_out) {
+  std::vector<int> Lr, Mr, Sr;
+  std::vector<int4> staged;
+  auto flush_run = [&](int a, int b) {  // short rows [a, b)
+    if (b - a < kStagedMinRun) {
+      for (int r = a; r < b; r++) Sr.push_back(r);
+      return;
+    }
+    int r = a;
+    while (r < b) {
+      const int start = r;
+      int nz = 0;
+      while (r < b && r - start < kMaxRows && nz + (rp[r + 1] - rp[r]) <= kNnzCap) {
+        nz += rp[r + 1] - rp[r];
+        r++;
+      }
+      const int nr = r - start;
+      int g = 1;
+      while (g < 32 && g * 2 * nr <= kBlock) g *= 2;
+      staged.push_back(make_int4(kStagedBlock, start, nr, g));
+    }
+  };
+  int run0 = 0;
+  for (int r = 0; r < m; r++) {
     const int len = rp[r + 1] - rp[r];
-    if (len > kLongRow) {
-      gsz.push_back(0);
-      r++;
-      rows.push_back(r);
-      continue;
-    }
-    const int start = r;
-    int nz = 0;
-    while (r < m && r - start < kMaxRows) {
-      const int l = rp[r + 1] - rp[r];
-      if (l > kLongRow || nz + l > kNnzCap) break;
-      nz += l;
-      r++;
-    }
-    const int nr = r - start;
-    int g = 1;
-    while (g < 32 && g * 2 * nr <= kBlock) g *= 2;
-    gsz.push_back((int8_t)g);
-    rows.push_back(r);
+    if (len <= kShortMax) continue;
+    flush_run(run0, r);
+    run0 = r + 1;
+    if (len > kWarpRowMax) Lr.push_back(r);
+    else Mr.push_back(r);
   }
-  P->nblk = (int)gsz.size();
-  SCUC_TRY(dalloc(&P->row, rows.size()));
-  SCUC_TRY(dalloc(&P->gsz, gsz.size()));
-  SCUC_CUDA(cudaMemcpy(P->row, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
-  if (!gsz.empty())
-    SCUC_CUDA(cudaMemcpy(P->gsz, gsz.data(), gsz.size() * sizeof(int8_t), cudaMemcpyHostToDevice));
-  if (rows_out) *rows_out = rows;
-  if (gsz_out) *gsz_out = gsz;
+  flush_run(run0, m);
+  std::vector<int> list;
+  std::vector<int4> desc;
+  list.reserve(Lr.size() + Mr.size() + Sr.size());
+  for (int r : Lr) {
+    desc.push_back(make_int4(kLongRowBlock, (int)list.size(), 1, 0));
+    list.push_back(r);
+  }
+  for (size_t i = 0; i < Mr.size(); i += kWarpRowsPerBlock) {
+    const int cnt = (int)std::min<size_t>(kWarpRowsPerBlock, Mr.size() - i);
+    desc.push_back(make_int4(kWarpRowsBlock, (int)list.size(), cnt, 0));
+    for (int k = 0; k < cnt; k++) list.push_back(Mr[i + k]);
+  }
+  desc.insert(desc.end(), staged.begin(), staged.end());
+  for (size_t i = 0; i < Sr.size(); i += kShortPerBlock) {
+    const int cnt = (int)std::min<size_t>(kShortPerBlock, Sr.size() - i);
+    desc.push_back(make_int4(kShortListBlock, (int)list.size(), cnt, 0));
+    for (int k = 0; k < cnt; k++) list.push_back(Sr[i + k]);
+  }
+  P->nblk = (int)desc.size();
+  SCUC_TRY(dalloc(&P->desc, desc.size()));
+  SCUC_TRY(dalloc(&P->list, list.size()));
+  if (!desc.empty())
+    SCUC_CUDA(cudaMemcpy(P->desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!list.empty())
+    SCUC_CUDA(cudaMemcpy(P->list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (desc_out) *desc_out = desc;
+  if (list_out) *list_out = list;
   return SCUC_OK;
 }
 
@@ -280,10 +306,10 @@ int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, c
 
   SCUC_TRY(build_partition(rp32, m, &pA, nullptr, nullptr));
   SCUC_TRY(build_partition(rpt_h, n, &pT, nullptr, nullptr));
-  allocs.push_back(pA.row);
-  allocs.push_back(pA.gsz);
-  allocs.push_back(pT.row);
-  allocs.push_back(pT.gsz);
+  allocs.push_back(pA.desc);
+  allocs.push_back(pA.list);
+  allocs.push_back(pT.desc);
+  allocs.push_back(pT.list);
 
   // scaled data and iterates
   SCUC_TRY(alloc(&vs, nnz));

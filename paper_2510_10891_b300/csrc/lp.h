@@ -8,8 +8,8 @@ namespace scuc {
 
 struct DevLP;  // device view of a handle (lp_kernels.cuh)
 
-int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int>* rows_out,
-                    std::vector<int8_t>* gsz_out);
+int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
+                    std::vector<int>* list_out);
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s);
 
 struct Handle {
