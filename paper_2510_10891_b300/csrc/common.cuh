@@ -27,15 +27,20 @@ void set_error(const char* fmt, ...);
 constexpr int kBlock = 256;        // threads per SpMV block
 constexpr int kNnzCap = 2048;      // nonzeros staged in shared memory per staged block
 constexpr int kMaxRows = 256;      // rows per staged block
-constexpr int kShortMax = 32;      // short rows: <= this many nonzeros
-constexpr int kWarpRowMax = 4096;  // warp-per-row rows: up to this many; longer rows get a block
-constexpr int kStagedMinRun = 32;  // contiguous short-row runs at least this long are staged
-constexpr int kShortPerBlock = kBlock / 4;   // short-list rows per block (4 threads each)
-constexpr int kWarpRowsPerBlock = kBlock / 32;
+constexpr int kShortMax = 32;        // short rows: <= this many nonzeros
+constexpr int kGroupRowMax = 4096;   // list rows up to this many; longer rows get a block
+constexpr int kStagedMinRun = 32;    // contiguous short-row runs at least this long are staged
 constexpr int kDecideThreads = 1024;
 
 // block types of a partition entry
-constexpr int kStagedBlock = 0, kShortListBlock = 1, kWarpRowsBlock = 2, kLongRowBlock = 3;
+constexpr int kStagedBlock = 0, kGroupListBlock = 1, kLongRowBlock = 3;
+
+// threads per row of a list row: about 16 entries per thread, 4..32
+inline int group_size_for(int len) {
+  int g = 4;
+  while (g < 32 && g * 16 < len) g *= 2;
+  return g;
+}
 
 // Partition of a CSR matrix for the SpMV kernels: desc[b] = {type, first,
 // count, gsz}.  Staged blocks cover rows [first, first + count) with gsz

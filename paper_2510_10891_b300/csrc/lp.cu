@@ -38,19 +38,19 @@ static int grid_for(int64_t work, int block = kBlock) {
   return (int)g;
 }
 
-// Partition (host): rows longer than kWarpRowMax get a block each; rows of
-// kShortMax+1..kWarpRowMax nonzeros get a warp each (8 per block); contiguous
-// runs of >= kStagedMinRun short rows are packed into staged blocks of
-// <= kMaxRows rows / <= kNnzCap nonzeros (threads per row = largest power of
-// two with gsz * rows <= kBlock); the remaining short rows get 4 threads each
-// (64 per block).  Longest work first.
+// Partition (host): rows longer than kGroupRowMax get a block each; other
+// rows get a group of group_size_for(len) threads (about 16 entries per
+// thread), kBlock/gsz rows of the same group size per block, except
+// contiguous runs of >= kStagedMinRun short rows, which are packed into
+// staged blocks of <= kMaxRows rows / <= kNnzCap nonzeros (threads per row =
+// largest power of two with gsz * rows <= kBlock).  Longest work first.
 int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
                     std::vector<int>* list_out) {
-  std::vector<int> Lr, Mr, Sr;
+  std::vector<int> Lr, G[6];  // G[k]: rows with group size 1 << k (k = 2..5)
   std::vector<int4> staged;
   auto flush_run = [&](int a, int b) {  // short rows [a, b)
     if (b - a < kStagedMinRun) {
-      for (int r = a; r < b; r++) Sr.push_back(r);
+      for (int r = a; r < b; r++) G[2].push_back(r);
       return;
     }
     int r = a;
@@ -73,27 +73,25 @@ int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector
     if (len <= kShortMax) continue;
     flush_run(run0, r);
     run0 = r + 1;
-    if (len > kWarpRowMax) Lr.push_back(r);
-    else Mr.push_back(r);
+    if (len > kGroupRowMax) Lr.push_back(r);
+    else G[__builtin_ctz(group_size_for(len))].push_back(r);
   }
   flush_run(run0, m);
   std::vector<int> list;
   std::vector<int4> desc;
-  list.reserve(Lr.size() + Mr.size() + Sr.size());
   for (int r : Lr) {
     desc.push_back(make_int4(kLongRowBlock, (int)list.size(), 1, 0));
     list.push_back(r);
   }
-  for (size_t i = 0; i < Mr.size(); i += kWarpRowsPerBlock) {
-    const int cnt = (int)std::min<size_t>(kWarpRowsPerBlock, Mr.size() - i);
-    desc.push_back(make_int4(kWarpRowsBlock, (int)list.size(), cnt, 0));
-    for (int k = 0; k < cnt; k++) list.push_back(Mr[i + k]);
-  }
-  desc.insert(desc.end(), staged.begin(), staged.end());
-  for (size_t i = 0; i < Sr.size(); i += kShortPerBlock) {
-    const int cnt = (int)std::min<size_t>(kShortPerBlock, Sr.size() - i);
-    desc.push_back(make_int4(kShortListBlock, (int)list.size(), cnt, 0));
-    for (int k = 0; k < cnt; k++) list.push_back(Sr[i + k]);
+  for (int k = 5; k >= 2; k--) {
+    const int gsz = 1 << k, per = kBlock / gsz;
+    const std::vector<int>& R = G[k];
+    for (size_t i = 0; i < R.size(); i += per) {
+      const int cnt = (int)std::min<size_t>(per, R.size() - i);
+      desc.push_back(make_int4(kGroupListBlock, (int)list.size(), cnt, gsz));
+      for (int q = 0; q < cnt; q++) list.push_back(R[i + q]);
+    }
+    if (k == 3) desc.insert(desc.end(), staged.begin(), staged.end());
   }
   P->nblk = (int)desc.size();
   SCUC_TRY(dalloc(&P->desc, desc.size()));

@@ -1,17 +1,16 @@
 // CSR SpMV core with a per-row epilogue hook (fused into the HPR steps).
 //
 // One CTA of kBlock threads per entry of a host-built partition; each entry
-// is one of four block types, chosen from the row lengths:
-//  * kLongRowBlock   (type 3): one row with more than kWarpRowMax nonzeros; the
-//    whole block streams it (4 independent accumulators per thread) and
-//    reduces with a fixed tree;
-//  * kWarpRowsBlock  (type 2): up to 8 rows of kShortMax+1..kWarpRowMax nonzeros
-//    from a row list, one warp per row (4 accumulators per lane);
-//  * kShortListBlock (type 1): up to 64 rows of <= kShortMax nonzeros from a row
-//    list, 4 threads per row;
-//  * kStagedBlock    (type 0): a contiguous run of short rows whose val/col slice
-//    (<= kNnzCap entries) is staged in shared memory with coalesced loads,
-//    then reduced by groups of gsz threads.
+// is one of three block types, chosen from the row lengths:
+//  * kLongRowBlock   (type 3): one row with more than kGroupRowMax nonzeros;
+//    the whole block streams it and reduces with a fixed tree;
+//  * kGroupListBlock (type 1): kBlock/gsz rows from a row list, gsz = 4, 8,
+//    16 or 32 threads per row chosen from the row length;
+//  * kStagedBlock    (type 0): a contiguous run of short rows whose val/col
+//    slice (<= kNnzCap entries) is staged in shared memory with coalesced
+//    loads, then reduced by groups of gsz threads.
+// Long and list rows are read lane-strided (consecutive lanes, consecutive
+// entries), four entries in flight per thread.
 // All reductions have a fixed order, so results are deterministic run to
 // run.  Exactly one fused multiply-add per nonzero (FP64 issues at 2 DFMA per
 // clock per SM on B300, so products are never formed separately).  Matrix
@@ -80,24 +79,31 @@ __device__ __forceinline__ T ldcs(const T* p) {
   return __ldcs(p);
 }
 
-// Sum of val[e] * x[col[e]] for e = a, a + step, ... < z, four independent
-// accumulators combined in a fixed order.
+// fused multiply-add in the value type (explicit, so nothing is promoted)
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Partial sum of val[e] * x[col[e]] for e = a + li, a + li + nl, ... < z:
+// consecutive lanes take consecutive entries, so one warp-wide gather touches
+// neighbouring columns (rows of these matrices list their columns in
+// increasing order, mostly a few apart); four independent accumulators,
+// combined in a fixed order.
 template <typename VT>
-__device__ __forceinline__ VT strided_dot(const int* __restrict__ col, const VT* __restrict__ val,
-                                          const VT* __restrict__ x, int a, int z, int step) {
+__device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* __restrict__ val,
+                                        const VT* __restrict__ x, int a, int z, int li, int nl) {
   VT s0 = VT(0), s1 = VT(0), s2 = VT(0), s3 = VT(0);
-  int e = a;
-  for (; e + 3 * step < z; e += 4 * step) {
-    const int c0 = ldcs(col + e), c1 = ldcs(col + e + step), c2 = ldcs(col + e + 2 * step),
-              c3 = ldcs(col + e + 3 * step);
-    const VT v0 = ldcs(val + e), v1 = ldcs(val + e + step), v2 = ldcs(val + e + 2 * step),
-             v3 = ldcs(val + e + 3 * step);
-    s0 = fma(v0, ldg(x + c0), s0);
-    s1 = fma(v1, ldg(x + c1), s1);
-    s2 = fma(v2, ldg(x + c2), s2);
-    s3 = fma(v3, ldg(x + c3), s3);
+  int e = a + li;
+  for (; e + 3 * nl < z; e += 4 * nl) {
+    const int c0 = ldcs(col + e), c1 = ldcs(col + e + nl), c2 = ldcs(col + e + 2 * nl),
+              c3 = ldcs(col + e + 3 * nl);
+    const VT v0 = ldcs(val + e), v1 = ldcs(val + e + nl), v2 = ldcs(val + e + 2 * nl),
+             v3 = ldcs(val + e + 3 * nl);
+    s0 = fma_t(v0, ldg(x + c0), s0);
+    s1 = fma_t(v1, ldg(x + c1), s1);
+    s2 = fma_t(v2, ldg(x + c2), s2);
+    s3 = fma_t(v3, ldg(x + c3), s3);
   }
-  for (; e < z; e += step) s0 = fma(ldcs(val + e), ldg(x + ldcs(col + e)), s0);
+  for (; e < z; e += nl) s0 = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s0);
   return (s0 + s1) + (s2 + s3);
 }
 
@@ -111,31 +117,17 @@ __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int
   const int tid = threadIdx.x;
   if (d.x == kLongRowBlock) {
     const int r = part.list[d.y];
-    const VT acc = block_sum(strided_dot(col, val, x, ldg(rp + r) + tid, ldg(rp + r + 1), kBlock));
+    const VT acc = block_sum(group_dot(col, val, x, ldg(rp + r), ldg(rp + r + 1), tid, kBlock));
     if (tid == 0) epi.row(r, acc);
     return;
   }
-  if (d.x == kWarpRowsBlock) {
-    const int w = tid >> 5, lane = tid & 31;
-    if (w < d.z) {
-      const int r = part.list[d.y + w];
-      VT acc = strided_dot(col, val, x, ldg(rp + r) + lane, ldg(rp + r + 1), 32);
-      acc = warp_sum(acc);
-      if (lane == 0) epi.row(r, acc);
-    }
-    return;
-  }
-  if (d.x == kShortListBlock) {
-    const int g = tid >> 2, li = tid & 3;
+  if (d.x == kGroupListBlock) {
+    const int gsz = d.w;  // 4, 8, 16 or 32 threads per row
+    const int g = tid / gsz, li = tid - g * gsz;
     const bool act = g < d.z;
     const int r = act ? part.list[d.y + g] : 0;
-    VT acc = VT(0);
-    if (act) {
-      const int z = ldg(rp + r + 1);
-      for (int e = ldg(rp + r) + li; e < z; e += 4) acc = fma(ldcs(val + e), ldg(x + ldcs(col + e)), acc);
-    }
-    acc += __shfl_down_sync(0xffffffffu, acc, 2, 4);
-    acc += __shfl_down_sync(0xffffffffu, acc, 1, 4);
+    VT acc = act ? group_dot(col, val, x, ldg(rp + r), ldg(rp + r + 1), li, gsz) : VT(0);
+    for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, gsz);
     if (act && li == 0) epi.row(r, acc);
     return;
   }
@@ -155,7 +147,7 @@ __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int
     VT acc = VT(0);
     if (r < r1) {
       const int a = ldg(rp + r) - e0, z = ldg(rp + r + 1) - e0;
-      for (int e = a + li; e < z; e += gsz) acc = fma(s_val[e], ldg(x + s_col[e]), acc);
+      for (int e = a + li; e < z; e += gsz) acc = fma_t(s_val[e], ldg(x + s_col[e]), acc);
     }
     for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, gsz);
     if (r < r1 && li == 0) epi.row(r, acc);
