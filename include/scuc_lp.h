@@ -212,6 +212,72 @@ int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double*
 int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_params* p,
                         scuc_solve_info* infos);
 
+/* ---------------------------------------------------------------------- */
+/* Logic-driven fixing and presolve (Sec. 4.1 Round + Algorithm 1; the      */
+/* MILP-/LP-Presolve steps of Algorithm 2, Sec. 4.2)                        */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t G, T;            /* generators, hours                              */
+  const int32_t* u_idx;    /* [G*T] column of u_{g,t}, index g*T + t (host)  */
+  const int32_t* v_idx;    /* [G*T] column of v_{g,t}                        */
+  const int32_t* w_idx;    /* [G*T] column of w_{g,t}                        */
+  const int8_t* u_init;    /* [G] commitment before the first hour (0/1)     */
+} scuc_map;
+
+typedef struct {
+  double tau;              /* Round threshold, 0 <= tau < 0.5 (0.1)          */
+  int32_t t_first;         /* 1: Algorithm 1 from the second hour (as
+                              written); 0: also the first, against u_init   */
+  int32_t max_passes;      /* propagation passes (100)                       */
+  int32_t x_on_device;     /* x_relaxed is a device pointer (0)              */
+  int32_t build_reduced;   /* build the reduced LP when asked for (1)        */
+} scuc_fix_params;
+
+typedef struct {
+  int64_t nfixed;          /* (g,t) triples fixed by Algorithm 1             */
+  int32_t passes;          /* propagation passes run                         */
+  int32_t infeasible;      /* bounds crossed, or an emptied row is violated  */
+  int32_t m_red, n_red;    /* reduced LP size                                */
+  int64_t nnz_red;
+  int64_t n_fixed_cols;    /* columns with xl == xu after propagation        */
+  double obj_const;        /* c^T x of the removed (fixed) columns           */
+  double ms;               /* wall time of the call                          */
+} scuc_fix_info;
+
+void scuc_default_fix_params(scuc_fix_params* p);
+
+/* One fixing round on the model held by lp (the relaxed MILP M):
+ *  1. Round(x, tau) of every u, v, w value of x_relaxed[n] (unscaled, host
+ *     or device per p->x_on_device) and Algorithm 1 per generator: hours are
+ *     fixed in order while all four rounded values are confident and
+ *     u_t - u_{t-1} = v_t - w_t, v_t + w_t <= 1 (Eq. 1); fix_out[3*(g*T+t)
+ *     + {0,1,2}] (host, nullable) = fixed u, v, w or -1.
+ *  2. The fixed columns get xl = xu = value in lp's bounds (M is updated).
+ *  3. Bound propagation (Jacobi passes until no change or max_passes):
+ *     each row's activity range bounds every column of the row; integer
+ *     columns (is_int[n], host, nullable = the map's u, v, w) are rounded
+ *     inward with 1e-6 slack; continuous changes below 1e-9 relative are
+ *     ignored.  lp's bounds receive the result.
+ *  4. Reduced LP: fixed columns removed and folded into the row bounds,
+ *     rows whose activity range lies inside [lo, hi] removed.
+ *     *reduced_out (nullable) receives a new handle (caller destroys) on the
+ *     caller's stream of lp; col_map_out[n_red] / row_map_out[m_red] (host,
+ *     nullable, sized n / m) map reduced indices to lp's indices.
+ * Returns SCUC_E_INFEASIBLE (info->infeasible = 1) when propagation crosses
+ * a column's bounds or an emptied row is violated; no reduced LP then.   */
+int scuc_fix_and_propagate(scuc_lp* lp, const scuc_map* map, const uint8_t* is_int,
+                           const double* x_relaxed, const scuc_fix_params* p, int8_t* fix_out,
+                           scuc_lp** reduced_out, int32_t* col_map_out, int32_t* row_map_out,
+                           scuc_fix_info* info);
+
+/* Host copies of the handle's column bounds (xl, xu nullable, length n). */
+int scuc_lp_get_bounds(const scuc_lp* lp, double* xl, double* xu);
+
+/* Host copies of the handle's LP (each pointer nullable): row_ptr[m+1],
+ * col[nnz], val[nnz], c[n], xl[n], xu[n], lo[m], hi[m] (unscaled).      */
+int scuc_lp_export(const scuc_lp* lp, int64_t* row_ptr, int32_t* col, double* val, double* c,
+                   double* xl, double* xu, double* lo, double* hi);
+
 /* KKT residuals of a caller-supplied point, with no device allocation.
  * The paper has no counterpart; this is a service for callers that cannot
  * allocate GPU memory at the point of the call: code whose device memory is

@@ -44,6 +44,22 @@ class CheckLog(C.Structure):
                 ("fp64", C.c_int32), ("pad", C.c_int32)]
 
 
+class ScucMap(C.Structure):
+    _fields_ = [("G", C.c_int32), ("T", C.c_int32), ("u_idx", C.c_void_p), ("v_idx", C.c_void_p),
+                ("w_idx", C.c_void_p), ("u_init", C.c_void_p)]
+
+
+class FixParams(C.Structure):
+    _fields_ = [("tau", C.c_double), ("t_first", C.c_int32), ("max_passes", C.c_int32),
+                ("x_on_device", C.c_int32), ("build_reduced", C.c_int32)]
+
+
+class FixInfo(C.Structure):
+    _fields_ = [("nfixed", C.c_int64), ("passes", C.c_int32), ("infeasible", C.c_int32),
+                ("m_red", C.c_int32), ("n_red", C.c_int32), ("nnz_red", C.c_int64),
+                ("n_fixed_cols", C.c_int64), ("obj_const", C.c_double), ("ms", C.c_double)]
+
+
 _lib = None
 
 # exported symbols and their signatures
@@ -64,6 +80,13 @@ _SIGS = {
     "scuc_lp_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(SolveParams),
                                       C.POINTER(SolveInfo)]),
     "scuc_lp_kkt_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_default_fix_params": (None, [C.POINTER(FixParams)]),
+    "scuc_fix_and_propagate": (C.c_int, [C.c_void_p, C.POINTER(ScucMap), C.c_void_p, C.c_void_p,
+                                         C.POINTER(FixParams), C.c_void_p, C.POINTER(C.c_void_p),
+                                         C.c_void_p, C.c_void_p, C.POINTER(FixInfo)]),
+    "scuc_lp_get_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_lp_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "scuc_lp_destroy": (None, [C.c_void_p]),
     "scuc_last_error": (C.c_char_p, []),
 }

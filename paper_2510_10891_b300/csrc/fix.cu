@@ -1,0 +1,553 @@
+// Logic-driven fixing (Round + Algorithm 1, Sec. 4.1) and the presolve of
+// Algorithm 2 (Sec. 4.2): activity-based bound propagation and the reduced
+// LP (fixed columns folded into the row bounds, redundant rows dropped).
+//
+// Row activities, candidate bounds and the folded row bounds use explicitly
+// rounded FP64 operations in entry order (no contraction), so propagated
+// bounds and reduced-LP data are bit-identical run to run; min/max over a
+// column's candidates is order-free.  Every fixing and presolve decision is
+// made from those values.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "lp.h"
+#include "spmv.cuh"
+
+namespace scuc {
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid1(int64_t work) {
+  int64_t g = (work + kThreads - 1) / kThreads;
+  return (int)(g < 1 ? 1 : (g > 148 * 32 ? 148 * 32 : g));
+}
+
+// Round(s, tau) of Sec. 4.1
+__device__ __forceinline__ int round_tau(double s, double tau) {
+  if (s >= 1.0 - tau) return 1;
+  if (s >= 0.0 && s <= tau) return 0;
+  return -1;
+}
+
+// Algorithm 1, one thread per generator: fixes (u, v, w)_t for t = t_first..T-1
+// while the rounded values are confident and consistent with Eq. 1; writes
+// fix_out (-1 = free) and sets xl = xu = value on the fixed columns.
+__global__ void k_fix(int G, int T, const double* __restrict__ x, const int* __restrict__ ui,
+                      const int* __restrict__ vi, const int* __restrict__ wi,
+                      const int8_t* __restrict__ u_init, double tau, int t_first,
+                      int8_t* __restrict__ fix_out, double* __restrict__ xl, double* __restrict__ xu,
+                      unsigned long long* __restrict__ nfixed) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int64_t base = (int64_t)g * T;
+  for (int t = 0; t < T; t++) {
+    fix_out[3 * (base + t) + 0] = -1;
+    fix_out[3 * (base + t) + 1] = -1;
+    fix_out[3 * (base + t) + 2] = -1;
+  }
+  unsigned long long cnt = 0;
+  for (int t = t_first; t < T; t++) {
+    const int ut = round_tau(x[ui[base + t]], tau);
+    const int up = t > 0 ? round_tau(x[ui[base + t - 1]], tau) : (int)u_init[g];
+    const int vt = round_tau(x[vi[base + t]], tau);
+    const int wt = round_tau(x[wi[base + t]], tau);
+    if (ut == -1 || up == -1 || vt == -1 || wt == -1) break;
+    if (ut - up == vt - wt && vt + wt <= 1) {
+      fix_out[3 * (base + t) + 0] = (int8_t)ut;
+      fix_out[3 * (base + t) + 1] = (int8_t)vt;
+      fix_out[3 * (base + t) + 2] = (int8_t)wt;
+      const int cu = ui[base + t], cv = vi[base + t], cw = wi[base + t];
+      xl[cu] = xu[cu] = (double)ut;
+      xl[cv] = xu[cv] = (double)vt;
+      xl[cw] = xu[cw] = (double)wt;
+      cnt++;
+    } else {
+      break;
+    }
+  }
+  if (cnt) atomicAdd(nfixed, cnt);
+}
+
+// Activity range of each row over the current bounds: finite parts summed in
+// entry order, plus the number of infinite contributions (thread per row).
+__global__ void k_row_activity(const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ val, int m, const double* __restrict__ xl,
+                               const double* __restrict__ xu, double* __restrict__ mn,
+                               double* __restrict__ mx, int* __restrict__ cmn, int* __restrict__ cmx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double a_mn = 0.0, a_mx = 0.0;
+  int c_mn = 0, c_mx = 0;
+  for (int e = rp[i]; e < rp[i + 1]; e++) {
+    const double a = val[e];
+    const int j = col[e];
+    const double lmin = a > 0.0 ? xl[j] : xu[j];
+    const double lmax = a > 0.0 ? xu[j] : xl[j];
+    if (isinf(lmin)) c_mn++;
+    else a_mn = __dadd_rn(a_mn, __dmul_rn(a, lmin));
+    if (isinf(lmax)) c_mx++;
+    else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
+  }
+  mn[i] = a_mn;
+  mx[i] = a_mx;
+  cmn[i] = c_mn;
+  cmx[i] = c_mx;
+}
+
+// One Jacobi pass for each column (thread per column over its A^T entries):
+// candidate bounds from every row, integer rounding, acceptance thresholds.
+// Only column j's own bounds are read and written by thread j; row
+// activities come from the previous kernel, so the pass is Jacobi.
+__global__ void k_col_propagate(const int* __restrict__ rpt, const int* __restrict__ colt,
+                                const double* __restrict__ valt, int n, const double* __restrict__ lo,
+                                const double* __restrict__ hi, const double* __restrict__ mn,
+                                const double* __restrict__ mx, const int* __restrict__ cmn,
+                                const int* __restrict__ cmx, const uint8_t* __restrict__ is_int,
+                                double* __restrict__ xl, double* __restrict__ xu, int* __restrict__ flags) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double oxl = xl[j], oxu = xu[j];
+  double nlo = oxl, nhi = oxu;
+  for (int e = rpt[j]; e < rpt[j + 1]; e++) {
+    const int i = colt[e];
+    const double a = valt[e];
+    const double lmin = a > 0.0 ? oxl : oxu;
+    const double lmax = a > 0.0 ? oxu : oxl;
+    if (isfinite(hi[i])) {  // a x_j <= hi - (min activity of the other entries)
+      const bool ok = isinf(lmin) ? (cmn[i] == 1) : (cmn[i] == 0);
+      if (ok) {
+        const double rest = isinf(lmin) ? mn[i] : __dsub_rn(mn[i], __dmul_rn(a, lmin));
+        const double b = __ddiv_rn(__dsub_rn(hi[i], rest), a);
+        if (a > 0.0) { if (b < nhi) nhi = b; }
+        else { if (b > nlo) nlo = b; }
+      }
+    }
+    if (isfinite(lo[i])) {  // a x_j >= lo - (max activity of the other entries)
+      const bool ok = isinf(lmax) ? (cmx[i] == 1) : (cmx[i] == 0);
+      if (ok) {
+        const double rest = isinf(lmax) ? mx[i] : __dsub_rn(mx[i], __dmul_rn(a, lmax));
+        const double b = __ddiv_rn(__dsub_rn(lo[i], rest), a);
+        if (a > 0.0) { if (b > nlo) nlo = b; }
+        else { if (b < nhi) nhi = b; }
+      }
+    }
+  }
+  double l = nlo, u = nhi, nxl = oxl, nxu = oxu;
+  int changed = 0;
+  if (is_int[j]) {
+    if (isfinite(u)) u = floor(__dadd_rn(u, 1e-6));
+    if (isfinite(l)) l = ceil(__dsub_rn(l, 1e-6));
+    if (l > nxl) { nxl = l; changed = 1; }
+    if (u < nxu) { nxu = u; changed = 1; }
+  } else {
+    const double tl = 1e-9 * fmax(1.0, isfinite(oxl) ? fabs(oxl) : 1.0);
+    const double tu = 1e-9 * fmax(1.0, isfinite(oxu) ? fabs(oxu) : 1.0);
+    if (l > __dadd_rn(oxl, tl)) { nxl = l; changed = 1; }
+    if (u < __dsub_rn(oxu, tu)) { nxu = u; changed = 1; }
+  }
+  if (changed) {
+    xl[j] = nxl;
+    xu[j] = nxu;
+    atomicOr(flags + 0, 1);
+  }
+  if (nxl > __dadd_rn(nxu, 1e-6)) atomicOr(flags + 1, 1);
+}
+
+// Reduction, per row: fold fixed columns into the bounds (entry order),
+// activity of the free columns, keep flag (non-redundant, non-empty), kept
+// entry count, violated emptied rows.
+__global__ void k_reduce_rows(const int* __restrict__ rp, const int* __restrict__ col,
+                              const double* __restrict__ val, int m, const double* __restrict__ lo,
+                              const double* __restrict__ hi, const double* __restrict__ xl,
+                              const double* __restrict__ xu, int* __restrict__ keep, int* __restrict__ knz,
+                              double* __restrict__ lo_r, double* __restrict__ hi_r, int* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double shift = 0.0;
+  int kept = 0;
+  for (int e = rp[i]; e < rp[i + 1]; e++) {
+    const int j = col[e];
+    if (xl[j] == xu[j]) shift = __dadd_rn(shift, __dmul_rn(val[e], xl[j]));
+    else kept++;
+  }
+  const double l = __dsub_rn(lo[i], shift), u = __dsub_rn(hi[i], shift);
+  lo_r[i] = l;
+  hi_r[i] = u;
+  if (kept == 0) {
+    if (l > 1e-6 * fmax(1.0, fabs(l)) || u < -1e-6 * fmax(1.0, fabs(u))) atomicOr(flags + 1, 1);
+    keep[i] = 0;
+    knz[i] = 0;
+    return;
+  }
+  double a_mn = 0.0, a_mx = 0.0;
+  int c_mn = 0, c_mx = 0;
+  for (int e = rp[i]; e < rp[i + 1]; e++) {
+    const int j = col[e];
+    if (xl[j] == xu[j]) continue;
+    const double a = val[e];
+    const double lmin = a > 0.0 ? xl[j] : xu[j];
+    const double lmax = a > 0.0 ? xu[j] : xl[j];
+    if (isinf(lmin)) c_mn++;
+    else a_mn = __dadd_rn(a_mn, __dmul_rn(a, lmin));
+    if (isinf(lmax)) c_mx++;
+    else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
+  }
+  const bool lo_red = !isfinite(l) || (c_mn == 0 && a_mn >= l);
+  const bool hi_red = !isfinite(u) || (c_mx == 0 && a_mx <= u);
+  keep[i] = (lo_red && hi_red) ? 0 : 1;
+  knz[i] = keep[i] ? kept : 0;
+}
+
+__global__ void k_col_keep(int n, const double* __restrict__ xl, const double* __restrict__ xu,
+                           int* __restrict__ keepc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) keepc[j] = xl[j] != xu[j] ? 1 : 0;
+}
+
+// kept rows: entries of free columns, renumbered, in the original order
+__global__ void k_scatter_rows(const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ val, int m, const int* __restrict__ keep,
+                               const int* __restrict__ newrow, const int* __restrict__ rp_r,
+                               const int* __restrict__ newcol, const int* __restrict__ keepc,
+                               const double* __restrict__ lo_t, const double* __restrict__ hi_t,
+                               int* __restrict__ col_r, double* __restrict__ val_r, double* __restrict__ lo_r,
+                               double* __restrict__ hi_r, int* __restrict__ row_map) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || !keep[i]) return;
+  const int r = newrow[i];
+  int k = rp_r[r];
+  for (int e = rp[i]; e < rp[i + 1]; e++) {
+    const int j = col[e];
+    if (!keepc[j]) continue;
+    col_r[k] = newcol[j];
+    val_r[k] = val[e];
+    k++;
+  }
+  lo_r[r] = lo_t[i];
+  hi_r[r] = hi_t[i];
+  row_map[r] = i;
+}
+
+__global__ void k_scatter_cols(int n, const int* __restrict__ keepc, const int* __restrict__ newcol,
+                               const double* __restrict__ c, const double* __restrict__ xl,
+                               const double* __restrict__ xu, double* __restrict__ c_r,
+                               double* __restrict__ xl_r, double* __restrict__ xu_r, int* __restrict__ col_map) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || !keepc[j]) return;
+  const int k = newcol[j];
+  c_r[k] = c[j];
+  xl_r[k] = xl[j];
+  xu_r[k] = xu[j];
+  col_map[k] = j;
+}
+
+// objective of the fixed columns (one block, fixed order)
+__global__ void __launch_bounds__(1024) k_fixed_obj(int n, const double* __restrict__ c,
+                                                    const double* __restrict__ xl,
+                                                    const double* __restrict__ xu, double* __restrict__ out) {
+  __shared__ double s_w[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += 1024)
+    if (xl[j] == xu[j]) s += c[j] * xl[j];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < 32; w++) r += s_w[w];
+    *out = r;
+  }
+}
+
+}  // namespace
+
+int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, const double* x_in,
+                              const scuc_fix_params& p, int8_t* fix_out_h, Handle** reduced,
+                              int32_t* col_map_h, int32_t* row_map_h, scuc_fix_info* info) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  if (map.G < 0 || map.T < 1 || (map.G > 0 && (!map.u_idx || !map.v_idx || !map.w_idx || !map.u_init)) ||
+      !(p.tau >= 0.0 && p.tau < 0.5) || p.t_first < 0 || p.t_first > 1 || p.max_passes < 0 || !x_in) {
+    set_error("scuc_fix_and_propagate: invalid map or parameters");
+    return SCUC_E_INVALID;
+  }
+  const int64_t GT = (int64_t)map.G * map.T;
+  for (int64_t k = 0; k < GT; k++) {
+    const int32_t a = map.u_idx[k], b = map.v_idx[k], c2 = map.w_idx[k];
+    if (a < 0 || a >= n || b < 0 || b >= n || c2 < 0 || c2 >= n) {
+      set_error("scuc_fix_and_propagate: map index out of range at %lld", (long long)k);
+      return SCUC_E_INVALID;
+    }
+  }
+  SCUC_TRY(enter());
+  cudaStream_t s = work;
+  std::vector<void*> tmp;
+  auto talloc = [&](auto** ptr, size_t count) -> int {
+    void* q = nullptr;
+    SCUC_TRY(dev_alloc_bytes(&q, count * sizeof(**ptr)));
+    tmp.push_back(q);
+    *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q);
+    return SCUC_OK;
+  };
+  struct Free {
+    std::vector<void*>& v;
+    ~Free() {
+      for (void* q : v) cudaFree(q);
+    }
+  } freer{tmp};
+
+  int *ui = nullptr, *vi = nullptr, *wi = nullptr, *flags = nullptr;
+  int8_t *uinit = nullptr, *fixd = nullptr;
+  uint8_t* isint = nullptr;
+  unsigned long long* nfix = nullptr;
+  double* xd = nullptr;
+  SCUC_TRY(talloc(&ui, GT));
+  SCUC_TRY(talloc(&vi, GT));
+  SCUC_TRY(talloc(&wi, GT));
+  SCUC_TRY(talloc(&uinit, map.G));
+  SCUC_TRY(talloc(&fixd, 3 * GT));
+  SCUC_TRY(talloc(&isint, n));
+  SCUC_TRY(talloc(&flags, 2));
+  SCUC_TRY(talloc(&nfix, 1));
+  if (GT) {
+    SCUC_CUDA(cudaMemcpyAsync(ui, map.u_idx, GT * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaMemcpyAsync(vi, map.v_idx, GT * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaMemcpyAsync(wi, map.w_idx, GT * sizeof(int), cudaMemcpyHostToDevice, s));
+    SCUC_CUDA(cudaMemcpyAsync(uinit, map.u_init, map.G, cudaMemcpyHostToDevice, s));
+  }
+  std::vector<uint8_t> isint_h;
+  if (!is_int_h) {  // default: the map's u, v, w columns
+    isint_h.assign(n, 0);
+    for (int64_t k = 0; k < GT; k++) isint_h[map.u_idx[k]] = isint_h[map.v_idx[k]] = isint_h[map.w_idx[k]] = 1;
+    is_int_h = isint_h.data();
+  }
+  if (n) SCUC_CUDA(cudaMemcpyAsync(isint, is_int_h, n, cudaMemcpyHostToDevice, s));
+  if (p.x_on_device) {
+    xd = const_cast<double*>(x_in);
+  } else {
+    SCUC_TRY(talloc(&xd, n));
+    SCUC_CUDA(cudaMemcpyAsync(xd, x_in, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  SCUC_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+  SCUC_CUDA(cudaMemsetAsync(nfix, 0, sizeof(unsigned long long), s));
+
+  // F1/F2: Round + Algorithm 1, fixing the bounds of the model
+  if (map.G > 0)
+    k_fix<<<grid1(map.G), kThreads, 0, s>>>(map.G, map.T, xd, ui, vi, wi, uinit, p.tau, p.t_first, fixd, xl, xu,
+                                            nfix);
+  SCUC_CUDA(cudaGetLastError());
+
+  // F3: Jacobi propagation
+  double *mn = nullptr, *mx = nullptr;
+  int *cmn = nullptr, *cmx = nullptr;
+  SCUC_TRY(talloc(&mn, m));
+  SCUC_TRY(talloc(&mx, m));
+  SCUC_TRY(talloc(&cmn, m));
+  SCUC_TRY(talloc(&cmx, m));
+  int passes = 0, infeasible = 0;
+  int hflags[2] = {0, 0};
+  for (int pass = 0; pass < p.max_passes; pass++) {
+    SCUC_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));  // changed; flags[1] (infeasible) persists
+    if (m) k_row_activity<<<grid1(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx);
+    if (n)
+      k_col_propagate<<<grid1(n), kThreads, 0, s>>>(rpt, colt, valt, n, lo, hi, mn, mx, cmn, cmx, isint, xl, xu,
+                                                   flags);
+    SCUC_CUDA(cudaGetLastError());
+    SCUC_CUDA(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    passes = pass + 1;
+    if (hflags[1]) { infeasible = 1; break; }
+    if (!hflags[0]) break;
+  }
+  unsigned long long nf = 0;
+  SCUC_CUDA(cudaMemcpyAsync(&nf, nfix, sizeof(nf), cudaMemcpyDeviceToHost, s));
+  if (fix_out_h && GT) SCUC_CUDA(cudaMemcpyAsync(fix_out_h, fixd, 3 * GT, cudaMemcpyDeviceToHost, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));
+
+  scuc_fix_info I{};
+  I.nfixed = (int64_t)nf;
+  I.passes = passes;
+  I.infeasible = infeasible;
+  if (!infeasible && (reduced || col_map_h || row_map_h || info)) {
+    // reduced LP
+    int *keep = nullptr, *knz = nullptr, *keepc = nullptr, *newrow = nullptr, *newcol = nullptr, *rpr = nullptr;
+    double *lo_t = nullptr, *hi_t = nullptr, *objc = nullptr;
+    SCUC_TRY(talloc(&keep, m + 1));
+    SCUC_TRY(talloc(&knz, m + 1));
+    SCUC_TRY(talloc(&keepc, n + 1));
+    SCUC_TRY(talloc(&newrow, m + 1));
+    SCUC_TRY(talloc(&newcol, n + 1));
+    SCUC_TRY(talloc(&rpr, m + 1));
+    SCUC_TRY(talloc(&lo_t, m));
+    SCUC_TRY(talloc(&hi_t, m));
+    SCUC_TRY(talloc(&objc, 1));
+    if (m)
+      k_reduce_rows<<<grid1(m), kThreads, 0, s>>>(rp, col, val, m, lo, hi, xl, xu, keep, knz, lo_t, hi_t, flags);
+    if (n) k_col_keep<<<grid1(n), kThreads, 0, s>>>(n, xl, xu, keepc);
+    k_fixed_obj<<<1, 1024, 0, s>>>(n, c, xl, xu, objc);
+    SCUC_CUDA(cudaGetLastError());
+    SCUC_TRY(exclusive_scan(keep, m, newrow, s));
+    SCUC_TRY(exclusive_scan(keepc, n, newcol, s));
+    int mr = 0, nr = 0;
+    SCUC_CUDA(cudaMemcpyAsync(&mr, newrow + m, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaMemcpyAsync(&nr, newcol + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaMemcpyAsync(&I.obj_const, objc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    I.infeasible = hflags[1] ? 1 : 0;
+    I.n_fixed_cols = n - nr;
+    // kept-entry counts of the kept rows, in kept-row order, then scan
+    std::vector<int> knz_h(m), keep_h(m);
+    if (m) {
+      SCUC_CUDA(cudaMemcpyAsync(knz_h.data(), knz, m * sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCUC_CUDA(cudaMemcpyAsync(keep_h.data(), keep, m * sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCUC_CUDA(cudaStreamSynchronize(s));
+    }
+    std::vector<int> rpr_h(mr + 1, 0);
+    {
+      int r = 0;
+      for (int i = 0; i < m; i++)
+        if (keep_h[i]) {
+          rpr_h[r + 1] = rpr_h[r] + knz_h[i];
+          r++;
+        }
+    }
+    const int64_t nnzr = rpr_h[mr];
+    I.m_red = mr;
+    I.n_red = nr;
+    I.nnz_red = nnzr;
+    // device arrays of the reduced LP (ownership passes to the new handle)
+    void *d_rp = nullptr, *d_col = nullptr, *d_val = nullptr, *d_c = nullptr, *d_xl = nullptr, *d_xu = nullptr,
+         *d_lo = nullptr, *d_hi = nullptr;
+    int *rmap = nullptr, *cmap = nullptr;
+    SCUC_TRY(dev_alloc_bytes(&d_rp, (mr + 1) * sizeof(int)));
+    SCUC_TRY(dev_alloc_bytes(&d_col, nnzr * sizeof(int)));
+    SCUC_TRY(dev_alloc_bytes(&d_val, nnzr * sizeof(double)));
+    SCUC_TRY(dev_alloc_bytes(&d_c, nr * sizeof(double)));
+    SCUC_TRY(dev_alloc_bytes(&d_xl, nr * sizeof(double)));
+    SCUC_TRY(dev_alloc_bytes(&d_xu, nr * sizeof(double)));
+    SCUC_TRY(dev_alloc_bytes(&d_lo, mr * sizeof(double)));
+    SCUC_TRY(dev_alloc_bytes(&d_hi, mr * sizeof(double)));
+    SCUC_TRY(talloc(&rmap, mr));
+    SCUC_TRY(talloc(&cmap, nr));
+    int* rp_dev = static_cast<int*>(d_rp);
+    SCUC_CUDA(cudaMemcpyAsync(rp_dev, rpr_h.data(), (mr + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    // row offsets of kept rows by original row index for the scatter
+    if (m)
+      k_scatter_rows<<<grid1(m), kThreads, 0, s>>>(rp, col, val, m, keep, newrow, rp_dev, newcol, keepc, lo_t, hi_t,
+                                                   static_cast<int*>(d_col), static_cast<double*>(d_val),
+                                                   static_cast<double*>(d_lo), static_cast<double*>(d_hi), rmap);
+    if (n)
+      k_scatter_cols<<<grid1(n), kThreads, 0, s>>>(n, keepc, newcol, c, xl, xu, static_cast<double*>(d_c),
+                                                   static_cast<double*>(d_xl), static_cast<double*>(d_xu), cmap);
+    SCUC_CUDA(cudaGetLastError());
+    if (row_map_h && mr) SCUC_CUDA(cudaMemcpyAsync(row_map_h, rmap, mr * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (col_map_h && nr) SCUC_CUDA(cudaMemcpyAsync(col_map_h, cmap, nr * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    if (reduced && !I.infeasible) {
+      Handle* H = new Handle();
+      const int rc = H->init_device(mr, nr, nnzr, rp_dev, static_cast<int*>(d_col), static_cast<double*>(d_val),
+                                    static_cast<double*>(d_c), static_cast<double*>(d_xl),
+                                    static_cast<double*>(d_xu), static_cast<double*>(d_lo),
+                                    static_cast<double*>(d_hi), user);
+      if (rc != SCUC_OK) {
+        delete H;
+        return rc;
+      }
+      *reduced = H;
+    } else {
+      for (void* q : {d_rp, d_col, d_val, d_c, d_xl, d_xu, d_lo, d_hi}) cudaFree(q);
+    }
+  }
+  I.ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  if (info) *info = I;
+  SCUC_TRY(leave());
+  return I.infeasible ? SCUC_E_INFEASIBLE : SCUC_OK;
+}
+
+int Handle::get_bounds(double* xl_h, double* xu_h) {
+  SCUC_TRY(enter());
+  if (n && xl_h) SCUC_CUDA(cudaMemcpyAsync(xl_h, xl, n * sizeof(double), cudaMemcpyDeviceToHost, work));
+  if (n && xu_h) SCUC_CUDA(cudaMemcpyAsync(xu_h, xu, n * sizeof(double), cudaMemcpyDeviceToHost, work));
+  SCUC_CUDA(cudaStreamSynchronize(work));
+  return leave();
+}
+
+int Handle::export_lp(int64_t* row_ptr, int32_t* col_h, double* val_h, double* c_h, double* xl_h, double* xu_h,
+                      double* lo_h, double* hi_h) {
+  SCUC_TRY(enter());
+  cudaStream_t s = work;
+  std::vector<int> rp32(m + 1);
+  SCUC_CUDA(cudaMemcpyAsync(rp32.data(), rp, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (nnz && col_h) SCUC_CUDA(cudaMemcpyAsync(col_h, col, nnz * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (nnz && val_h) SCUC_CUDA(cudaMemcpyAsync(val_h, val, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (n && c_h) SCUC_CUDA(cudaMemcpyAsync(c_h, c, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (n && xl_h) SCUC_CUDA(cudaMemcpyAsync(xl_h, xl, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (n && xu_h) SCUC_CUDA(cudaMemcpyAsync(xu_h, xu, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (m && lo_h) SCUC_CUDA(cudaMemcpyAsync(lo_h, lo, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (m && hi_h) SCUC_CUDA(cudaMemcpyAsync(hi_h, hi, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  if (row_ptr)
+    for (int i = 0; i <= m; i++) row_ptr[i] = rp32[i];
+  return leave();
+}
+
+}  // namespace scuc
+
+using scuc::Handle;
+
+extern "C" {
+
+void scuc_default_fix_params(scuc_fix_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->tau = 0.1;
+  p->t_first = 1;
+  p->max_passes = 100;
+  p->x_on_device = 0;
+  p->build_reduced = 1;
+}
+
+int scuc_fix_and_propagate(scuc_lp* lp, const scuc_map* map, const uint8_t* is_int, const double* x_relaxed,
+                           const scuc_fix_params* p, int8_t* fix_out, scuc_lp** reduced_out,
+                           int32_t* col_map_out, int32_t* row_map_out, scuc_fix_info* info) {
+  if (!lp || !lp->h || !map) {
+    scuc::set_error("scuc_fix_and_propagate: null argument");
+    return SCUC_E_INVALID;
+  }
+  scuc_fix_params d;
+  if (!p) {
+    scuc_default_fix_params(&d);
+    p = &d;
+  }
+  if (reduced_out) *reduced_out = nullptr;
+  Handle* red = nullptr;
+  const int rc = lp->h->fix_and_propagate(*map, is_int, x_relaxed, *p, fix_out,
+                                          (reduced_out && p->build_reduced) ? &red : nullptr, col_map_out,
+                                          row_map_out, info);
+  if (red) *reduced_out = new scuc_lp{red};
+  return rc;
+}
+
+int scuc_lp_get_bounds(const scuc_lp* lp, double* xl, double* xu) {
+  if (!lp || !lp->h) {
+    scuc::set_error("null handle");
+    return SCUC_E_INVALID;
+  }
+  return lp->h->get_bounds(xl, xu);
+}
+
+int scuc_lp_export(const scuc_lp* lp, int64_t* row_ptr, int32_t* col, double* val, double* c, double* xl,
+                   double* xu, double* lo, double* hi) {
+  if (!lp || !lp->h) {
+    scuc::set_error("null handle");
+    return SCUC_E_INVALID;
+  }
+  return lp->h->export_lp(row_ptr, col, val, c, xl, xu, lo, hi);
+}
+
+}  // extern "C"

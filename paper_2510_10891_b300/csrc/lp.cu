@@ -31,6 +31,12 @@ static int dalloc(T** p, size_t count) {
   return SCUC_OK;
 }
 
+int dev_alloc_bytes(void** p, size_t bytes) {
+  *p = nullptr;
+  SCUC_CUDA(cudaMalloc(p, bytes + 16));
+  return SCUC_OK;
+}
+
 static int grid_for(int64_t work, int block = kBlock) {
   int64_t g = (work + block - 1) / block;
   if (g < 1) g = 1;
@@ -223,18 +229,7 @@ int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t
 int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, const int32_t* col_,
                  const double* val_, const double* c_, const double* xl_, const double* xu_,
                  const double* lo_, const double* hi_, cudaStream_t user_) {
-  m = m_;
-  n = n_;
-  nnz = nnz_;
-  user = user_;
-  SCUC_CUDA(cudaGetDevice(&device));
-  SCUC_CUDA(cudaStreamCreateWithFlags(&work, cudaStreamNonBlocking));
-  SCUC_CUDA(cudaEventCreateWithFlags(&ev_user, cudaEventDisableTiming));
-  SCUC_CUDA(cudaEventCreateWithFlags(&ev_work, cudaEventDisableTiming));
-  SCUC_CUDA(cudaEventCreateWithFlags(&ev_slot[0], cudaEventDisableTiming));
-  SCUC_CUDA(cudaEventCreateWithFlags(&ev_slot[1], cudaEventDisableTiming));
-  SCUC_CUDA(cudaMallocHost((void**)&ctrl_h, 2 * sizeof(Ctrl)));
-  SCUC_TRY(enter());
+  SCUC_TRY(begin(m_, n_, nnz_, user_));
   cudaStream_t s = work;
 
   std::vector<int> rp32(m + 1);
@@ -261,6 +256,43 @@ int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, c
     SCUC_CUDA(cudaMemcpyAsync(lo, lo_, m * sizeof(double), cudaMemcpyHostToDevice, s));
     SCUC_CUDA(cudaMemcpyAsync(hi, hi_, m * sizeof(double), cudaMemcpyHostToDevice, s));
   }
+  return setup_device(rp32);
+}
+
+int Handle::begin(int32_t m_, int32_t n_, int64_t nnz_, cudaStream_t user_) {
+  m = m_;
+  n = n_;
+  nnz = nnz_;
+  user = user_;
+  SCUC_CUDA(cudaGetDevice(&device));
+  SCUC_CUDA(cudaStreamCreateWithFlags(&work, cudaStreamNonBlocking));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_user, cudaEventDisableTiming));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_work, cudaEventDisableTiming));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_slot[0], cudaEventDisableTiming));
+  SCUC_CUDA(cudaEventCreateWithFlags(&ev_slot[1], cudaEventDisableTiming));
+  SCUC_CUDA(cudaMallocHost((void**)&ctrl_h, 2 * sizeof(Ctrl)));
+  return enter();
+}
+
+// Adopts device arrays (allocated by the library; ownership moves to the
+// handle) that already satisfy the input rules, then builds the device state.
+int Handle::init_device(int32_t m_, int32_t n_, int64_t nnz_, int* d_rp, int* d_col, double* d_val,
+                        double* d_c, double* d_xl, double* d_xu, double* d_lo, double* d_hi,
+                        cudaStream_t user_) {
+  rp = d_rp; col = d_col; val = d_val; c = d_c; xl = d_xl; xu = d_xu; lo = d_lo; hi = d_hi;
+  for (void* p : {(void*)d_rp, (void*)d_col, (void*)d_val, (void*)d_c, (void*)d_xl, (void*)d_xu,
+                  (void*)d_lo, (void*)d_hi})
+    allocs.push_back(p);
+  SCUC_TRY(begin(m_, n_, nnz_, user_));
+  std::vector<int> rp32(m + 1);
+  SCUC_CUDA(cudaMemcpyAsync(rp32.data(), rp, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, work));
+  SCUC_CUDA(cudaStreamSynchronize(work));
+  return setup_device(rp32);
+}
+
+// transpose, partitions and solver buffers (data already on the device)
+int Handle::setup_device(const std::vector<int>& rp32) {
+  cudaStream_t s = work;
 
   // transpose: count, scan, scatter, per-column sort by row, gather values
   SCUC_TRY(alloc(&rpt, n + 1));

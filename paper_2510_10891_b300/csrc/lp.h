@@ -11,6 +11,7 @@ struct DevLP;  // device view of a handle (lp_kernels.cuh)
 int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
                     std::vector<int>* list_out);
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s);
+int dev_alloc_bytes(void** p, size_t bytes);
 
 struct Handle {
   int32_t m = 0, n = 0;
@@ -54,6 +55,10 @@ struct Handle {
   int init(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
            const double* val, const double* c, const double* xl, const double* xu,
            const double* lo, const double* hi, cudaStream_t user);
+  int begin(int32_t m, int32_t n, int64_t nnz, cudaStream_t user);
+  int init_device(int32_t m, int32_t n, int64_t nnz, int* d_rp, int* d_col, double* d_val, double* d_c,
+                  double* d_xl, double* d_xu, double* d_lo, double* d_hi, cudaStream_t user);
+  int setup_device(const std::vector<int>& rp32);
   int enter();
   int leave();
   DevLP dev() const;
@@ -65,6 +70,11 @@ struct Handle {
             double* yo, double* zo, scuc_solve_info* info);
   int matvec(int transpose, const double* in, double* out);
   int kkt_noalloc(const double* x, const double* y, const double* z, double* out);
+  int fix_and_propagate(const scuc_map& map, const uint8_t* is_int, const double* x, const scuc_fix_params& p,
+                        int8_t* fix_out, Handle** reduced, int32_t* col_map, int32_t* row_map, scuc_fix_info* info);
+  int get_bounds(double* xl, double* xu);
+  int export_lp(int64_t* row_ptr, int32_t* col, double* val, double* c, double* xl, double* xu, double* lo,
+                double* hi);
 };
 
 int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,

@@ -112,3 +112,72 @@ class LP:
         L.check(L.lib().scuc_lp_matvec(self.h, 1 if transpose else 0, C.c_void_p(inp.data_ptr()),
                                        C.c_void_p(out.data_ptr())))
         return out
+
+    # ----- fixing + presolve (Sec. 4.1-4.2) -----
+
+    @classmethod
+    def _adopt(cls, h):
+        self = cls.__new__(cls)
+        self.h = h
+        m, n, nnz = C.c_int32(), C.c_int32(), C.c_int64()
+        L.check(L.lib().scuc_lp_dims(h, C.byref(m), C.byref(n), C.byref(nnz)))
+        self.m, self.n, self.nnz = m.value, n.value, nnz.value
+        return self
+
+    def fix_and_propagate(self, G, T, u_idx, v_idx, w_idx, u_init, x, tau=0.1, t_first=1,
+                          max_passes=100, is_int=None, build_reduced=True):
+        """One fixing round (Round + Algorithm 1, propagation, reduced LP).
+        x: numpy array (host) or torch CUDA float64 tensor.  Updates this LP's
+        bounds; returns fix (int8 [3*G*T]), the reduced LP (or None), maps and info."""
+        keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (u_idx, v_idx, w_idx)]
+        ui = np.ascontiguousarray(u_init, dtype=np.int8)
+        mp = L.ScucMap(int(G), int(T), keep[0].ctypes.data, keep[1].ctypes.data, keep[2].ctypes.data,
+                       ui.ctypes.data)
+        p = L.FixParams()
+        L.lib().scuc_default_fix_params(C.byref(p))
+        p.tau, p.t_first, p.max_passes = float(tau), int(t_first), int(max_passes)
+        p.build_reduced = 1 if build_reduced else 0
+        if isinstance(x, np.ndarray):
+            xa = _f64(x)
+            xp = C.c_void_p(xa.ctypes.data)
+            p.x_on_device = 0
+        else:
+            xp = C.c_void_p(x.data_ptr())
+            p.x_on_device = 1
+        ii = None if is_int is None else np.ascontiguousarray(is_int, dtype=np.uint8)
+        fix = np.full(3 * int(G) * int(T), -1, dtype=np.int8)
+        cmap = np.zeros(max(self.n, 1), dtype=np.int32)
+        rmap = np.zeros(max(self.m, 1), dtype=np.int32)
+        red = C.c_void_p()
+        info = L.FixInfo()
+        rc = L.lib().scuc_fix_and_propagate(self.h, C.byref(mp), _ptr(ii), xp, C.byref(p),
+                                            C.c_void_p(fix.ctypes.data),
+                                            C.byref(red) if build_reduced else None,
+                                            C.c_void_p(cmap.ctypes.data), C.c_void_p(rmap.ctypes.data),
+                                            C.byref(info))
+        d = {f[0]: getattr(info, f[0]) for f in L.FixInfo._fields_}
+        if rc == L.SCUC_E_INFEASIBLE:
+            return dict(fix=fix, reduced=None, col_map=None, row_map=None, info=d, infeasible=True)
+        L.check(rc)
+        out = dict(fix=fix, info=d, infeasible=False, col_map=cmap[:d["n_red"]].copy(),
+                   row_map=rmap[:d["m_red"]].copy(), reduced=None)
+        if build_reduced and red.value:
+            out["reduced"] = LP._adopt(red)
+        return out
+
+    def get_bounds(self):
+        xl, xu = np.zeros(self.n), np.zeros(self.n)
+        L.check(L.lib().scuc_lp_get_bounds(self.h, C.c_void_p(xl.ctypes.data), C.c_void_p(xu.ctypes.data)))
+        return xl, xu
+
+    def export(self) -> dict:
+        """The LP as host arrays (unscaled): row_ptr, col, val, c, xl, xu, lo, hi."""
+        m, n, nnz = self.m, self.n, self.nnz
+        d = dict(m=m, n=n, row_ptr=np.zeros(m + 1, np.int64), col=np.zeros(max(nnz, 1), np.int32),
+                 val=np.zeros(max(nnz, 1)), c=np.zeros(max(n, 1)), xl=np.zeros(max(n, 1)),
+                 xu=np.zeros(max(n, 1)), lo=np.zeros(max(m, 1)), hi=np.zeros(max(m, 1)))
+        L.check(L.lib().scuc_lp_export(self.h, *[C.c_void_p(d[k].ctypes.data) for k in
+                                                 ("row_ptr", "col", "val", "c", "xl", "xu", "lo", "hi")]))
+        for k, ln in (("col", nnz), ("val", nnz), ("c", n), ("xl", n), ("xu", n), ("lo", m), ("hi", m)):
+            d[k] = d[k][:ln]
+        return d
