@@ -273,6 +273,12 @@ int scuc_fix_and_propagate(scuc_lp* lp, const scuc_map* map, const uint8_t* is_i
 /* Host copies of the handle's column bounds (xl, xu nullable, length n). */
 int scuc_lp_get_bounds(const scuc_lp* lp, double* xl, double* xu);
 
+/* Replace the handle's column bounds (n each): host arrays (validated: no
+ * NaN, xl <= xu, xl != +INF, xu != -INF) or, with on_device = 1, device
+ * arrays on the handle's device (not validated).  Used to restore or set
+ * the bounds of the model between fixing rounds.                        */
+int scuc_lp_set_bounds(scuc_lp* lp, const double* xl, const double* xu, int32_t on_device);
+
 /* Host copies of the handle's LP (each pointer nullable): row_ptr[m+1],
  * col[nnz], val[nnz], c[n], xl[n], xu[n], lo[m], hi[m] (unscaled).      */
 int scuc_lp_export(const scuc_lp* lp, int64_t* row_ptr, int32_t* col, double* val, double* c,

@@ -85,6 +85,7 @@ _SIGS = {
                                          C.POINTER(FixParams), C.c_void_p, C.POINTER(C.c_void_p),
                                          C.c_void_p, C.c_void_p, C.POINTER(FixInfo)]),
     "scuc_lp_get_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_lp_set_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "scuc_lp_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "scuc_lp_destroy": (None, [C.c_void_p]),

@@ -21,9 +21,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// one thread per item: the grid covers every item (no cap)
 int grid1(int64_t work) {
-  int64_t g = (work + kThreads - 1) / kThreads;
-  return (int)(g < 1 ? 1 : (g > 148 * 32 ? 148 * 32 : g));
+  const int64_t g = (work + kThreads - 1) / kThreads;
+  return (int)(g < 1 ? 1 : g);
 }
 
 // Round(s, tau) of Sec. 4.1
@@ -477,6 +478,24 @@ int Handle::get_bounds(double* xl_h, double* xu_h) {
   return leave();
 }
 
+int Handle::set_bounds(const double* xl_in, const double* xu_in, int on_device) {
+  if (!on_device)
+    for (int32_t j = 0; j < n; j++)
+      if (std::isnan(xl_in[j]) || std::isnan(xu_in[j]) || xl_in[j] > xu_in[j] || xl_in[j] == INFINITY ||
+          xu_in[j] == -INFINITY) {
+        set_error("scuc_lp_set_bounds: invalid bounds at column %d", j);
+        return SCUC_E_INVALID;
+      }
+  SCUC_TRY(enter());
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n) {
+    SCUC_CUDA(cudaMemcpyAsync(xl, xl_in, n * sizeof(double), k, work));
+    SCUC_CUDA(cudaMemcpyAsync(xu, xu_in, n * sizeof(double), k, work));
+  }
+  SCUC_CUDA(cudaStreamSynchronize(work));
+  return leave();
+}
+
 int Handle::export_lp(int64_t* row_ptr, int32_t* col_h, double* val_h, double* c_h, double* xl_h, double* xu_h,
                       double* lo_h, double* hi_h) {
   SCUC_TRY(enter());
@@ -539,6 +558,14 @@ int scuc_lp_get_bounds(const scuc_lp* lp, double* xl, double* xu) {
     return SCUC_E_INVALID;
   }
   return lp->h->get_bounds(xl, xu);
+}
+
+int scuc_lp_set_bounds(scuc_lp* lp, const double* xl, const double* xu, int32_t on_device) {
+  if (!lp || !lp->h || (lp->h->n > 0 && (!xl || !xu))) {
+    scuc::set_error("scuc_lp_set_bounds: null argument");
+    return SCUC_E_INVALID;
+  }
+  return lp->h->set_bounds(xl, xu, on_device);
 }
 
 int scuc_lp_export(const scuc_lp* lp, int64_t* row_ptr, int32_t* col, double* val, double* c, double* xl,

@@ -73,6 +73,7 @@ struct Handle {
   int fix_and_propagate(const scuc_map& map, const uint8_t* is_int, const double* x, const scuc_fix_params& p,
                         int8_t* fix_out, Handle** reduced, int32_t* col_map, int32_t* row_map, scuc_fix_info* info);
   int get_bounds(double* xl, double* xu);
+  int set_bounds(const double* xl, const double* xu, int on_device);
   int export_lp(int64_t* row_ptr, int32_t* col, double* val, double* c, double* xl, double* xu, double* lo,
                 double* hi);
 };

@@ -170,6 +170,10 @@ class LP:
         L.check(L.lib().scuc_lp_get_bounds(self.h, C.c_void_p(xl.ctypes.data), C.c_void_p(xu.ctypes.data)))
         return xl, xu
 
+    def set_bounds(self, xl, xu):
+        xl, xu = _f64(xl), _f64(xu)
+        L.check(L.lib().scuc_lp_set_bounds(self.h, C.c_void_p(xl.ctypes.data), C.c_void_p(xu.ctypes.data), 0))
+
     def export(self) -> dict:
         """The LP as host arrays (unscaled): row_ptr, col, val, c, xl, xu, lo, hi."""
         m, n, nnz = self.m, self.n, self.nnz

@@ -296,9 +296,11 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
     F = 1.5 * np.abs(flow).max(axis=1)
     F = np.maximum(F, 0.05 * F.mean())
 
-    # ---- initial state: all units on at the proportional dispatch of hour 1 ----
+    # ---- initial state: all units on at the proportional dispatch of hour 1,
+    # capped at 0.9 x the shut-down capacity so that stopping in hour 1 is
+    # always possible (Eq. 4 ramp-down row at t = 1) ----
     u_init = np.ones(G, dtype=np.int8)
-    p_init = share * Dt[0]
+    p_init = np.minimum(share * Dt[0], 0.9 * sd)
 
     # ---- instance-aware scaling (Sec. 3.A) ----
     if cfg.eta_scaling:

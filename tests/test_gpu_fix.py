@@ -118,3 +118,29 @@ def test_successive_rounds(P):
         assert s["info"]["status"] == 0
         x = xl.copy()                       # fixed columns at their values
         x[r["col_map"]] = s["x"]            # free columns from the reduced solve
+
+
+def test_fix_propagate_full_size_13k(P):
+    """The 13,000-bus LP (the benchmarked workload, same launch path as
+    bench.py): fixing decisions, propagated bounds and reduced-LP sizes and
+    maps equal the oracle's on the same solution."""
+    inst = make_preset("scuc13k")
+    d = oracle.as_lp(inst)
+    lp = P.LP(inst)
+    x = lp.solve(tol=1e-4, precision="mixed")["x"]
+    fix, nf, pl, pu, passes = _oracle_round(inst, d, x, 0.1)
+    r = lp.fix_and_propagate(inst.G, inst.T, inst.u_idx, inst.v_idx, inst.w_idx, inst.u_init, x, tau=0.1,
+                             is_int=inst.is_int)
+    np.testing.assert_array_equal(r["fix"], fix)
+    assert r["infeasible"] == (passes < 0)
+    if passes < 0:
+        return
+    assert r["info"]["passes"] == passes
+    gxl, gxu = lp.get_bounds()
+    np.testing.assert_array_equal(gxl, pl)
+    np.testing.assert_array_equal(gxu, pu)
+    red, rmap, cmap, oc, bad = oracle.reduce(d, pl, pu)
+    gi = r["info"]
+    assert (gi["m_red"], gi["n_red"], gi["nnz_red"]) == (red["m"], red["n"], len(red["val"]))
+    np.testing.assert_array_equal(r["row_map"], rmap)
+    np.testing.assert_array_equal(r["col_map"], cmap)
