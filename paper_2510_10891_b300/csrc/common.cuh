@@ -33,7 +33,7 @@ constexpr int kStagedMinRun = 32;    // contiguous short-row runs at least this 
 constexpr int kDecideThreads = 1024;
 
 // block types of a partition entry
-constexpr int kStagedBlock = 0, kGroupListBlock = 1, kLongRowBlock = 3;
+constexpr int kStagedBlock = 0, kGroupListBlock = 1;
 
 // threads per row of a list row: about 16 entries per thread, 4..32
 inline int group_size_for(int len) {
@@ -42,13 +42,31 @@ inline int group_size_for(int len) {
   return g;
 }
 
-// Partition of a CSR matrix for the SpMV kernels: desc[b] = {type, first,
-// count, gsz}.  Staged blocks cover rows [first, first + count) with gsz
-// threads per row; list blocks cover rows list[first .. first + count).
+// streamed long rows: tiles of kTile entries, kStages-deep shared-memory ring
+constexpr int kTile = 960;
+constexpr int kStages = 4;
+constexpr int kTileSlack = 8;                                   // alignment slack (entries)
+constexpr int kStageBytes = (kTile + kTileSlack) * 12;          // int index + FP64 value
+constexpr int kStreamSmem = 128 + kStages * kStageBytes;        // mbarriers + ring
+constexpr int kStagedSmem = kNnzCap * 12 + kBlock * 12;  // staging + row sums/ids
+constexpr long long kWaitBudgetCycles = 4000000000LL;           // ~2 s at 2 GHz
+
+// Partition of a CSR matrix for the SpMV kernels.  Blocks [0, nstream) are
+// persistent CTAs that stream the long rows (long_rows[c], c = blockIdx,
+// blockIdx + nstream, ...) through shared memory with bulk copies; block
+// nstream + b runs desc[b] = {type, first, count, gsz}: staged blocks cover
+// rows [first, first + count) with gsz threads per row, list blocks cover
+// rows list[first .. first + count).  nblk = nstream + number of desc
+// entries (grid size and number of partial-sum slots).
 struct Partition {
   int nblk = 0;
+  int nstream = 0;
+  int nlong = 0;
+  int smem = kStagedSmem;        // dynamic shared memory of a launch
   int4* desc = nullptr;
   int* list = nullptr;
+  int* long_rows = nullptr;
+  int* err = nullptr;            // set to 1 when a bounded wait runs out
 };
 
 // Device-resident solver state.  Parameters are written by the host before a

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(const int* __restrict__ rp,
                                                      const double* __restrict__ x, const double* __restrict__ lo,
                                                      const double* __restrict__ hi, const double* __restrict__ y,
                                                      double* __restrict__ partial) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   RowEpi epi{lo, hi, y, {0.0, 0.0, 0.0}};
   spmv_block<double>(rp, col, val, x, part, smem, epi);
   block_store<3>(epi.acc, partial, part.nblk);
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(const int* __restrict__ rpt
                                                      const double* __restrict__ xl, const double* __restrict__ xu,
                                                      const double* __restrict__ x, const double* __restrict__ z,
                                                      double* __restrict__ partial) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   ColEpi epi{c, xl, xu, x, z, {0.0, 0.0, 0.0, 0.0}};
   spmv_block<double>(rpt, colt, valt, y, part, smem, epi);
   block_store<4>(epi.acc, partial, part.nblk);
@@ -163,12 +163,14 @@ int Handle::kkt_noalloc(const double* xd, const double* yd, const double* zd, do
   SCUC_TRY(enter());
   double* scratch = nullptr;
   SCUC_TRY(scratch_address(device, &scratch));
+  SCUC_CUDA(cudaFuncSetAttribute(k_kkt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem));
+  SCUC_CUDA(cudaFuncSetAttribute(k_kkt_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem));
   cudaStream_t s = work;
   // every slot read by the final reduction is written by a block first, so
   // nothing left by an earlier call is read
-  if (pA.nblk) k_kkt_rows<<<pA.nblk, kBlock, 0, s>>>(rp, col, val, pA, xd, lo, hi, yd, scratch);
+  if (pA.nblk) k_kkt_rows<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, val, pA, xd, lo, hi, yd, scratch);
   if (pT.nblk)
-    k_kkt_cols<<<pT.nblk, kBlock, 0, s>>>(rpt, colt, valt, pT, yd, c, xl, xu, xd, zd,
+    k_kkt_cols<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, valt, pT, yd, c, xl, xu, xd, zd,
                                           scratch + 3 * (int64_t)pA.nblk);
   k_kkt_final<<<1, kFinalThreads, 0, s>>>(scratch, pA.nblk, pT.nblk, out);
   SCUC_CUDA(cudaGetLastError());

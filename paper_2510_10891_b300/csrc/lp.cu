@@ -27,13 +27,13 @@ template <typename T>
 static int dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  SCUC_CUDA(cudaMalloc((void**)p, count * sizeof(T) + 16));
+  SCUC_CUDA(cudaMalloc((void**)p, count * sizeof(T) + 64));  // padding: aligned bulk copies
   return SCUC_OK;
 }
 
 int dev_alloc_bytes(void** p, size_t bytes) {
   *p = nullptr;
-  SCUC_CUDA(cudaMalloc(p, bytes + 16));
+  SCUC_CUDA(cudaMalloc(p, bytes + 64));
   return SCUC_OK;
 }
 
@@ -85,10 +85,6 @@ int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector
   flush_run(run0, m);
   std::vector<int> list;
   std::vector<int4> desc;
-  for (int r : Lr) {
-    desc.push_back(make_int4(kLongRowBlock, (int)list.size(), 1, 0));
-    list.push_back(r);
-  }
   for (int k = 5; k >= 2; k--) {
     const int gsz = 1 << k, per = kBlock / gsz;
     const std::vector<int>& R = G[k];
@@ -99,9 +95,17 @@ int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector
     }
     if (k == 3) desc.insert(desc.end(), staged.begin(), staged.end());
   }
-  P->nblk = (int)desc.size();
+  P->nlong = (int)Lr.size();
+  P->nstream = std::min<int>(P->nlong, 2 * 148);  // persistent streaming CTAs, two per SM
+  P->smem = P->nlong ? std::max(kStagedSmem, kStreamSmem) : kStagedSmem;
+  P->nblk = P->nstream + (int)desc.size();
   SCUC_TRY(dalloc(&P->desc, desc.size()));
   SCUC_TRY(dalloc(&P->list, list.size()));
+  SCUC_TRY(dalloc(&P->long_rows, Lr.size()));
+  SCUC_TRY(dalloc(&P->err, 1));
+  SCUC_CUDA(cudaMemset(P->err, 0, sizeof(int)));
+  if (!Lr.empty())
+    SCUC_CUDA(cudaMemcpy(P->long_rows, Lr.data(), Lr.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!desc.empty())
     SCUC_CUDA(cudaMemcpy(P->desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice));
   if (!list.empty())
@@ -290,9 +294,25 @@ int Handle::init_device(int32_t m_, int32_t n_, int64_t nnz_, int* d_rp, int* d_
   return setup_device(rp32);
 }
 
+// SpMV kernels take the streaming ring as dynamic shared memory, which with
+// their static shared memory exceeds the 48 KB default
+static int allow_stream_smem() {
+  const int bytes = kStreamSmem;
+  SCUC_CUDA(cudaFuncSetAttribute(k_primal<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SCUC_CUDA(cudaFuncSetAttribute(k_primal<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SCUC_CUDA(cudaFuncSetAttribute(k_dual<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SCUC_CUDA(cudaFuncSetAttribute(k_dual<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SCUC_CUDA(cudaFuncSetAttribute(k_res_primal, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SCUC_CUDA(cudaFuncSetAttribute(k_res_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SCUC_CUDA(cudaFuncSetAttribute(k_power_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SCUC_CUDA(cudaFuncSetAttribute(k_spmv_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return SCUC_OK;
+}
+
 // transpose, partitions and solver buffers (data already on the device)
 int Handle::setup_device(const std::vector<int>& rp32) {
   cudaStream_t s = work;
+  SCUC_TRY(allow_stream_smem());
 
   // transpose: count, scan, scatter, per-column sort by row, gather values
   SCUC_TRY(alloc(&rpt, n + 1));
@@ -336,10 +356,8 @@ int Handle::setup_device(const std::vector<int>& rp32) {
 
   SCUC_TRY(build_partition(rp32, m, &pA, nullptr, nullptr));
   SCUC_TRY(build_partition(rpt_h, n, &pT, nullptr, nullptr));
-  allocs.push_back(pA.desc);
-  allocs.push_back(pA.list);
-  allocs.push_back(pT.desc);
-  allocs.push_back(pT.list);
+  for (Partition* P : {&pA, &pT})
+    for (void* q : {(void*)P->desc, (void*)P->list, (void*)P->long_rows, (void*)P->err}) allocs.push_back(q);
 
   // scaled data and iterates
   SCUC_TRY(alloc(&vs, nnz));
@@ -462,8 +480,8 @@ int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters
   PowerCtrl P{};
   for (int it = 0; it < p.power_max_iter; it += 16) {
     for (int j = 0; j < 16; j++) {
-      if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, 0, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
-      if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, 0, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
+      if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
+      if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
       k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);
       k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, pctrl);
       nlaunch += 2 + (pA.nblk ? 1 : 0) + (pT.nblk ? 1 : 0);
@@ -498,19 +516,19 @@ int Handle::launch_period(int check_every, bool profile) {
     const bool chk = (j == check_every - 1);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 0], s));
     if (pT.nblk) {
-      if (chk) k_primal<true><<<pT.nblk, kBlock, 0, s>>>(L, j);
-      else k_primal<false><<<pT.nblk, kBlock, 0, s>>>(L, j);
+      if (chk) k_primal<true><<<pT.nblk, kBlock, pT.smem, s>>>(L, j);
+      else k_primal<false><<<pT.nblk, kBlock, pT.smem, s>>>(L, j);
     }
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 1], s));
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 2], s));
     if (pA.nblk) {
-      if (chk) k_dual<true><<<pA.nblk, kBlock, 0, s>>>(L, j);
-      else k_dual<false><<<pA.nblk, kBlock, 0, s>>>(L, j);
+      if (chk) k_dual<true><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
+      else k_dual<false><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
     }
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 3], s));
   }
-  if (pA.nblk) k_res_primal<<<pA.nblk, kBlock, 0, s>>>(L);
-  if (pT.nblk) k_res_dual<<<pT.nblk, kBlock, 0, s>>>(L);
+  if (pA.nblk) k_res_primal<<<pA.nblk, kBlock, pA.smem, s>>>(L);
+  if (pT.nblk) k_res_dual<<<pT.nblk, kBlock, pT.smem, s>>>(L);
   k_decide<<<1, kDecideThreads, 0, s>>>(L, check_every);
   SCUC_CUDA(cudaGetLastError());
   nlaunch += 2 + (int64_t)check_every * ((pT.nblk ? 1 : 0) + (pA.nblk ? 1 : 0)) + (pA.nblk ? 1 : 0) +
@@ -692,6 +710,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   }
   last_nlog = std::min(C.nlog, log_cap);
   SCUC_CUDA(cudaStreamSynchronize(s));
+  SCUC_TRY(device_error());
   if (info) {
     memset(info, 0, sizeof(*info));
     info->status = timed_out && !C.done ? SCUC_ST_TIME_LIMIT : (C.status < 0 ? SCUC_ST_ITER_LIMIT : C.status);
@@ -714,16 +733,33 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   return leave();
 }
 
+// a bounded device-side wait ran out in a streaming SpMV
+int Handle::device_error() {
+  int e[2] = {0, 0};
+  SCUC_CUDA(cudaMemcpyAsync(&e[0], pA.err, sizeof(int), cudaMemcpyDeviceToHost, work));
+  SCUC_CUDA(cudaMemcpyAsync(&e[1], pT.err, sizeof(int), cudaMemcpyDeviceToHost, work));
+  SCUC_CUDA(cudaStreamSynchronize(work));
+  if (e[0] || e[1]) {
+    SCUC_CUDA(cudaMemsetAsync(pA.err, 0, sizeof(int), work));
+    SCUC_CUDA(cudaMemsetAsync(pT.err, 0, sizeof(int), work));
+    SCUC_CUDA(cudaStreamSynchronize(work));
+    set_error("a device-side wait for a bulk copy ran out of its time budget");
+    return SCUC_E_DEVICE_TIMEOUT;
+  }
+  return SCUC_OK;
+}
+
 int Handle::matvec(int transpose, const double* in, double* out) {
   SCUC_TRY(enter());
   cudaStream_t s = work;
   if (!transpose) {
-    if (pA.nblk) k_spmv_plain<<<pA.nblk, kBlock, 0, s>>>(rp, col, val, in, pA, out);
+    if (pA.nblk) k_spmv_plain<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, val, in, pA, out);
   } else {
-    if (pT.nblk) k_spmv_plain<<<pT.nblk, kBlock, 0, s>>>(rpt, colt, valt, in, pT, out);
+    if (pT.nblk) k_spmv_plain<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, valt, in, pT, out);
   }
   SCUC_CUDA(cudaGetLastError());
   SCUC_CUDA(cudaStreamSynchronize(s));
+  SCUC_TRY(device_error());
   return leave();
 }
 

@@ -69,6 +69,7 @@ struct Handle {
   int solve(const scuc_solve_params& p, const double* x0, const double* y0, double* xo,
             double* yo, double* zo, scuc_solve_info* info);
   int matvec(int transpose, const double* in, double* out);
+  int device_error();
   int kkt_noalloc(const double* x, const double* y, const double* z, double* out);
   int fix_and_propagate(const scuc_map& map, const uint8_t* is_int, const double* x, const scuc_fix_params& p,
                         int8_t* fix_out, Handle** reduced, int32_t* col_map, int32_t* row_map, scuc_fix_info* info);

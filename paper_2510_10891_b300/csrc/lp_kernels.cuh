@@ -67,7 +67,7 @@ struct PrimalEpi {
 
 template <bool CHECK>
 __global__ void __launch_bounds__(kBlock) k_primal(DevLP L, int j) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
   PrimalEpi<CHECK> epi{L, ctrl->sigma, L.coef[2 * j], L.coef[2 * j + 1], ctrl->fp64_phase != 0,
@@ -115,7 +115,7 @@ struct DualEpi {
 
 template <bool CHECK>
 __global__ void __launch_bounds__(kBlock) k_dual(DevLP L, int j) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
   DualEpi<CHECK> epi{L, ctrl->s_step, L.coef[2 * j], L.coef[2 * j + 1], ctrl->fp64_phase != 0,
@@ -151,7 +151,7 @@ struct ResPrimalEpi {  // A x_bar: primal violation (unscaled), y-part of dobj, 
 };
 
 __global__ void __launch_bounds__(kBlock) k_res_primal(DevLP L) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   if (L.ctrl->done) return;
   ResPrimalEpi epi{L, L.ctrl->beta, {0.0, 0.0, 0.0}};
   spmv_block<double>(L.rp, L.col, L.vs, L.xbar, L.pA, smem, epi);
@@ -169,7 +169,7 @@ struct ResDualEpi {  // A^T y_bar: dual residual (unscaled)
 };
 
 __global__ void __launch_bounds__(kBlock) k_res_dual(DevLP L) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   if (L.ctrl->done) return;
   ResDualEpi epi{L, L.ctrl->gamma, {0.0}};
   spmv_block<double>(L.rpt, L.colt, L.vst, L.ybar, L.pT, smem, epi);

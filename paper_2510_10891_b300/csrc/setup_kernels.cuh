@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kBlock) k_power_spmv(const int* __restrict__ r
                                                        const double* __restrict__ in, Partition part,
                                                        double* __restrict__ out, double* __restrict__ psum,
                                                        const PowerCtrl* __restrict__ P) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   if (P->done) return;
   StoreEpi epi{out, {0.0}};
   spmv_block<double>(rp, col, val, in, part, smem, epi);
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_plain(const int* __restrict__ r
                                                        const double* __restrict__ val,
                                                        const double* __restrict__ in, Partition part,
                                                        double* __restrict__ out) {
-  __shared__ __align__(16) unsigned char smem[kNnzCap * 12];
+  extern __shared__ __align__(128) unsigned char smem[];
   PlainEpi epi{out};
   spmv_block<double>(rp, col, val, in, part, smem, epi);
 }

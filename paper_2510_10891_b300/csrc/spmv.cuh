@@ -1,9 +1,12 @@
 // CSR SpMV core with a per-row epilogue hook (fused into the HPR steps).
 //
-// One CTA of kBlock threads per entry of a host-built partition; each entry
-// is one of three block types, chosen from the row lengths:
-//  * kLongRowBlock   (type 3): one row with more than kGroupRowMax nonzeros;
-//    the whole block streams it and reduces with a fixed tree;
+// Rows with more than kGroupRowMax nonzeros are streamed by persistent CTAs
+// (blocks [0, nstream)): one thread issues 1-D bulk copies (cp.async.bulk,
+// completion on an mbarrier) of kTile-entry tiles of the row's indices and
+// values into a kStages-deep shared-memory ring, so the matrix stream never
+// waits on the gathers; all threads then gather and accumulate from shared
+// memory and reduce with a fixed tree at each row's end.  Every other block
+// runs one entry of a host-built partition, one of two types:
 //  * kGroupListBlock (type 1): kBlock/gsz rows from a row list, gsz = 4, 8,
 //    16 or 32 threads per row chosen from the row length;
 //  * kStagedBlock    (type 0): a contiguous run of short rows whose val/col
@@ -107,20 +110,167 @@ __device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* _
   return (s0 + s1) + (s2 + s3);
 }
 
+// ---- bulk-copy (TMA) ring for long rows -----------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1-D bulk copy global -> shared, completion counted on bar (16-byte aligned
+// addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Waits for the given phase of bar within a clock budget; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitBudgetCycles) return false;
+  return true;
+}
+
+// tile sequence of a streaming CTA: rows long_rows[c], c = blockIdx.x +
+// k * nstream, each cut into kTile-entry tiles
+struct TileIt {
+  int c, e, rend, row;
+  __device__ void start(const Partition& P, const int* rp) {
+    c = blockIdx.x;
+    if (c < P.nlong) {
+      row = P.long_rows[c];
+      e = rp[row];
+      rend = rp[row + 1];
+    }
+  }
+  __device__ bool valid(const Partition& P) const { return c < P.nlong; }
+  __device__ void next(const Partition& P, const int* rp) {
+    e += kTile;
+    if (e >= rend) {
+      c += P.nstream;
+      if (c < P.nlong) {
+        row = P.long_rows[c];
+        e = rp[row];
+        rend = rp[row + 1];
+      }
+    }
+  }
+};
+
+// Issues the bulk copies of the tile at `it` into ring stage `st`.
+template <typename VT>
+__device__ __forceinline__ void issue_tile(const TileIt& it, const int* col, const VT* val, unsigned char* ring,
+                                           uint64_t* bars, int st) {
+  const int e1 = min(it.e + kTile, it.rend);
+  const int ea = it.e & ~3, eb = (e1 + 3) & ~3;  // 16-byte aligned span (arrays are padded)
+  const uint32_t nb_col = (uint32_t)(eb - ea) * 4u, nb_val = (uint32_t)(eb - ea) * (uint32_t)sizeof(VT);
+  unsigned char* stage = ring + st * kStageBytes;
+  mbar_arrive_expect_tx(bars + st, nb_col + nb_val);
+  bulk_g2s(stage, col + ea, nb_col, bars + st);
+  bulk_g2s(stage + (kTile + kTileSlack) * 4, val + ea, nb_val, bars + st);
+}
+
+// Persistent streaming of the long rows: tid 0 keeps kStages tiles in flight;
+// all threads read each tile from shared memory (thread t: entries t,
+// t + kBlock, ...), gather x and accumulate; at a row's last tile a fixed
+// block reduction feeds epi.row.
+template <typename VT, class Epi>
+__device__ void stream_long_rows(const int* __restrict__ rp, const int* __restrict__ col,
+                                 const VT* __restrict__ val, const VT* __restrict__ x, const Partition& P,
+                                 unsigned char* smem, Epi& epi) {
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* ring = smem + 128;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(bars + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  __syncthreads();
+  TileIt prod, cons;
+  prod.start(P, rp);
+  cons.start(P, rp);
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < kStages && prod.valid(P); issued++, prod.next(P, rp)) issue_tile<VT>(prod, col, val, ring, bars, issued);
+  VT a0 = VT(0), a1 = VT(0);
+  for (int k = 0; cons.valid(P); k++) {
+    const int st = k % kStages;
+    if (!mbar_wait_bounded(bars + st, (uint32_t)((k / kStages) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    const unsigned char* stage = ring + st * kStageBytes;
+    const int ea = cons.e & ~3;
+    const int* s_col = reinterpret_cast<const int*>(stage) - ea;
+    const VT* s_val = reinterpret_cast<const VT*>(stage + (kTile + kTileSlack) * 4) - ea;
+    const int e1 = min(cons.e + kTile, cons.rend);
+    int e = cons.e + tid;
+    for (; e + kBlock < e1; e += 2 * kBlock) {
+      a0 = fma_t(s_val[e], ldg(x + s_col[e]), a0);
+      a1 = fma_t(s_val[e + kBlock], ldg(x + s_col[e + kBlock]), a1);
+    }
+    if (e < e1) a0 = fma_t(s_val[e], ldg(x + s_col[e]), a0);
+    const bool last = e1 >= cons.rend;
+    const int row = cons.row;
+    __syncthreads();  // stage st fully read
+    if (tid == 0 && prod.valid(P)) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_tile<VT>(prod, col, val, ring, bars, st);
+      prod.next(P, rp);
+      issued++;
+    }
+    if (last) {
+      const VT acc = block_sum(a0 + a1);
+      if (tid == 0) epi.row(row, acc);
+      a0 = VT(0);
+      a1 = VT(0);
+    }
+    cons.next(P, rp);
+  }
+  if (s_fail) {
+    // a wait ran out: record it and let copies still in flight land (bounded)
+    if (tid == 0) {
+      atomicOr(P.err, 1);
+      for (int s = 0; s < kStages; s++) mbar_wait_bounded(bars + s, 0u), mbar_wait_bounded(bars + s, 1u);
+    }
+    __syncthreads();
+  }
+}
+
 // Runs the SpMV of one partition entry; calls epi.row(r, acc) once per row,
-// from a single thread.  smem must hold kNnzCap * (sizeof(VT) + 4) bytes.
+// from a single thread.  smem must hold part.smem bytes (dynamic).
 template <typename VT, class Epi>
 __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int* __restrict__ col,
                                            const VT* __restrict__ val, const VT* __restrict__ x,
                                            const Partition& part, unsigned char* smem, Epi& epi) {
-  const int4 d = part.desc[blockIdx.x];  // {type, first, count, gsz}
-  const int tid = threadIdx.x;
-  if (d.x == kLongRowBlock) {
-    const int r = part.list[d.y];
-    const VT acc = block_sum(group_dot(col, val, x, ldg(rp + r), ldg(rp + r + 1), tid, kBlock));
-    if (tid == 0) epi.row(r, acc);
+  if ((int)blockIdx.x < part.nstream) {
+    stream_long_rows<VT>(rp, col, val, x, part, smem, epi);
     return;
   }
+  const int4 d = part.desc[blockIdx.x - part.nstream];  // {type, first, count, gsz}
+  const int tid = threadIdx.x;
+  // row sums of the block (behind the staging buffer), so that the epilogue
+  // runs one row per thread with full warps (a warp instruction costs the
+  // FP64 pipe the same however few of its lanes are active)
+  VT* s_sum = reinterpret_cast<VT*>(smem + kNnzCap * 12);
+  int* s_row = reinterpret_cast<int*>(smem + kNnzCap * 12 + kBlock * 8);
   if (d.x == kGroupListBlock) {
     const int gsz = d.w;  // 4, 8, 16 or 32 threads per row
     const int g = tid / gsz, li = tid - g * gsz;
@@ -128,7 +278,12 @@ __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int
     const int r = act ? part.list[d.y + g] : 0;
     VT acc = act ? group_dot(col, val, x, ldg(rp + r), ldg(rp + r + 1), li, gsz) : VT(0);
     for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, gsz);
-    if (act && li == 0) epi.row(r, acc);
+    if (act && li == 0) {
+      s_sum[g] = acc;
+      s_row[g] = r;
+    }
+    __syncthreads();
+    if (tid < d.z) epi.row(s_row[tid], s_sum[tid]);
     return;
   }
   // staged contiguous run of short rows
@@ -150,7 +305,15 @@ __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int
       for (int e = a + li; e < z; e += gsz) acc = fma_t(s_val[e], ldg(x + s_col[e]), acc);
     }
     for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, gsz);
-    if (r < r1 && li == 0) epi.row(r, acc);
+    if (gsz == 1) {  // thread per row: every lane already holds a row
+      if (r < r1) epi.row(r, acc);
+    } else if (r < r1 && li == 0) {
+      s_sum[r - r0] = acc;
+    }
+  }
+  if (gsz > 1) {
+    __syncthreads();
+    if (tid < r1 - r0) epi.row(r0 + tid, s_sum[tid]);
   }
 }
 
