@@ -48,6 +48,9 @@ constexpr int kStages = 4;
 constexpr int kTileSlack = 8;                                   // alignment slack (entries)
 constexpr int kStageBytes = (kTile + kTileSlack) * 12;          // int index + FP64 value
 constexpr int kStreamSmem = 128 + kStages * kStageBytes;        // mbarriers + ring
+// the SpMV kernels keep static shared memory small so that the ring fits
+// under the 48 KB a launch may take without a function attribute
+static_assert(kStreamSmem + 1024 <= 48 * 1024, "streaming ring must fit the default shared memory");
 constexpr int kStagedSmem = kNnzCap * 12 + kBlock * 12;  // staging + row sums/ids
 constexpr long long kWaitBudgetCycles = 4000000000LL;           // ~2 s at 2 GHz
 

@@ -163,8 +163,6 @@ int Handle::kkt_noalloc(const double* xd, const double* yd, const double* zd, do
   SCUC_TRY(enter());
   double* scratch = nullptr;
   SCUC_TRY(scratch_address(device, &scratch));
-  SCUC_CUDA(cudaFuncSetAttribute(k_kkt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem));
-  SCUC_CUDA(cudaFuncSetAttribute(k_kkt_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem));
   cudaStream_t s = work;
   // every slot read by the final reduction is written by a block first, so
   // nothing left by an earlier call is read

@@ -294,25 +294,9 @@ int Handle::init_device(int32_t m_, int32_t n_, int64_t nnz_, int* d_rp, int* d_
   return setup_device(rp32);
 }
 
-// SpMV kernels take the streaming ring as dynamic shared memory, which with
-// their static shared memory exceeds the 48 KB default
-static int allow_stream_smem() {
-  const int bytes = kStreamSmem;
-  SCUC_CUDA(cudaFuncSetAttribute(k_primal<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SCUC_CUDA(cudaFuncSetAttribute(k_primal<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SCUC_CUDA(cudaFuncSetAttribute(k_dual<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SCUC_CUDA(cudaFuncSetAttribute(k_dual<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SCUC_CUDA(cudaFuncSetAttribute(k_res_primal, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SCUC_CUDA(cudaFuncSetAttribute(k_res_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SCUC_CUDA(cudaFuncSetAttribute(k_power_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SCUC_CUDA(cudaFuncSetAttribute(k_spmv_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  return SCUC_OK;
-}
-
 // transpose, partitions and solver buffers (data already on the device)
 int Handle::setup_device(const std::vector<int>& rp32) {
   cudaStream_t s = work;
-  SCUC_TRY(allow_stream_smem());
 
   // transpose: count, scan, scatter, per-column sort by row, gather values
   SCUC_TRY(alloc(&rpt, n + 1));

@@ -218,15 +218,27 @@ __device__ void stream_long_rows(const int* __restrict__ rp, const int* __restri
     if (s_fail) break;
     const unsigned char* stage = ring + st * kStageBytes;
     const int ea = cons.e & ~3;
-    const int* s_col = reinterpret_cast<const int*>(stage) - ea;
-    const VT* s_val = reinterpret_cast<const VT*>(stage + (kTile + kTileSlack) * 4) - ea;
+    const int* s_col = reinterpret_cast<const int*>(stage);  // entry e at [e - ea]
+    const VT* s_val = reinterpret_cast<const VT*>(stage + (kTile + kTileSlack) * 4);
     const int e1 = min(cons.e + kTile, cons.rend);
-    int e = cons.e + tid;
-    for (; e + kBlock < e1; e += 2 * kBlock) {
-      a0 = fma_t(s_val[e], ldg(x + s_col[e]), a0);
-      a1 = fma_t(s_val[e + kBlock], ldg(x + s_col[e + kBlock]), a1);
+    // this thread's (at most kPerThread) entries of the tile: indices and
+    // values from shared memory first, then all gathers, then the FMAs
+    constexpr int kPerThread = (kTile + kBlock - 1) / kBlock;
+    int cc[kPerThread];
+    VT vv[kPerThread], xx[kPerThread];
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) {
+      const int e = cons.e + tid + q * kBlock;
+      cc[q] = e < e1 ? s_col[e - ea] : -1;
+      vv[q] = e < e1 ? s_val[e - ea] : VT(0);
     }
-    if (e < e1) a0 = fma_t(s_val[e], ldg(x + s_col[e]), a0);
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) xx[q] = cc[q] >= 0 ? ldg(x + cc[q]) : VT(0);
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) {
+      if (q & 1) a1 = fma_t(vv[q], xx[q], a1);
+      else a0 = fma_t(vv[q], xx[q], a0);
+    }
     const bool last = e1 >= cons.rend;
     const int row = cons.row;
     __syncthreads();  // stage st fully read
@@ -269,6 +281,10 @@ __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int
   // row sums of the block (behind the staging buffer), so that the epilogue
   // runs one row per thread with full warps (a warp instruction costs the
   // FP64 pipe the same however few of its lanes are active)
+  // Launches that also stream long rows are limited by shared memory to a few
+  // CTAs per SM; there the extra barrier costs more than it saves, so rows go
+  // straight to the epilogue from their group leader.
+  const bool smem_epi = part.nstream == 0;
   VT* s_sum = reinterpret_cast<VT*>(smem + kNnzCap * 12);
   int* s_row = reinterpret_cast<int*>(smem + kNnzCap * 12 + kBlock * 8);
   if (d.x == kGroupListBlock) {
@@ -278,6 +294,10 @@ __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int
     const int r = act ? part.list[d.y + g] : 0;
     VT acc = act ? group_dot(col, val, x, ldg(rp + r), ldg(rp + r + 1), li, gsz) : VT(0);
     for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, gsz);
+    if (!smem_epi) {
+      if (act && li == 0) epi.row(r, acc);
+      return;
+    }
     if (act && li == 0) {
       s_sum[g] = acc;
       s_row[g] = r;
@@ -305,13 +325,13 @@ __device__ __forceinline__ void spmv_block(const int* __restrict__ rp, const int
       for (int e = a + li; e < z; e += gsz) acc = fma_t(s_val[e], ldg(x + s_col[e]), acc);
     }
     for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, gsz);
-    if (gsz == 1) {  // thread per row: every lane already holds a row
-      if (r < r1) epi.row(r, acc);
+    if (gsz == 1 || !smem_epi) {  // thread per row, or direct epilogue
+      if (r < r1 && li == 0) epi.row(r, acc);
     } else if (r < r1 && li == 0) {
       s_sum[r - r0] = acc;
     }
   }
-  if (gsz > 1) {
+  if (gsz > 1 && smem_epi) {
     __syncthreads();
     if (tid < r1 - r0) epi.row(r0 + tid, s_sum[tid]);
   }
