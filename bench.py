@@ -175,9 +175,20 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--ncu-case", default=None,
+                    help="profiling target: 128 mixed-precision iterations (FP32 matvecs, no graph) "
+                         "on this preset, no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        import paper_2510_10891_b300 as P
+        from scuc_gen import make_preset
+        lp = P.LP(make_preset(args.ncu_case))
+        r = lp.solve(want=("x",), tol=0.0, max_iter=128, use_graph=0, precision="mixed",
+                     polish_stall=10 ** 6, polish_factor=0.0)
+        print("ncu case %s: %d iterations" % (args.ncu_case, r["info"]["iters"]))
+        return 0
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
