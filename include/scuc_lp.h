@@ -133,6 +133,12 @@ typedef struct {
   double ms_dual_spmv_f32, ms_primal_spmv_f32;
   int64_t n_dual_spmv_f32, n_primal_spmv_f32;
   int64_t launches;       /* kernels launched by this solve                 */
+  int64_t warm_iters;     /* scuc_lp_solve_warm: iterations of a rejected
+                             warm run (included in iters); 0 otherwise     */
+  int64_t ref_iters;      /* scuc_lp_solve_warm: iterations of the cold
+                             reference period (included in iters)         */
+  double cold_first_kkt;  /* scuc_lp_solve_warm: KKT measure at the cold
+                             start's first check; 0 otherwise             */
 } scuc_solve_info;
 
 typedef struct {

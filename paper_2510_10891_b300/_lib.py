@@ -34,7 +34,8 @@ class SolveInfo(C.Structure):
                 ("ms_primal_spmv", C.c_double), ("n_dual_spmv", C.c_int64),
                 ("n_primal_spmv", C.c_int64), ("ms_dual_spmv_f32", C.c_double),
                 ("ms_primal_spmv_f32", C.c_double), ("n_dual_spmv_f32", C.c_int64),
-                ("n_primal_spmv_f32", C.c_int64), ("launches", C.c_int64)]
+                ("n_primal_spmv_f32", C.c_int64), ("launches", C.c_int64),
+                ("warm_iters", C.c_int64), ("ref_iters", C.c_int64), ("cold_first_kkt", C.c_double)]
 
 
 class CheckLog(C.Structure):
@@ -59,6 +60,26 @@ class FixInfo(C.Structure):
                 ("m_red", C.c_int32), ("n_red", C.c_int32), ("nnz_red", C.c_int64),
                 ("n_fixed_cols", C.c_int64), ("obj_const", C.c_double), ("ms", C.c_double)]
 
+
+class WsTrainParams(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("w_dispatch", C.c_float), ("w_price", C.c_float)]
+
+
+class WsLayout(C.Structure):
+    _fields_ = [("G", C.c_int32), ("T", C.c_int32), ("nseg", C.c_int32), ("fill", C.c_int32),
+                ("u_col", C.c_void_p), ("v_col", C.c_void_p), ("w_col", C.c_void_p),
+                ("p_col", C.c_void_p), ("seg_col", C.c_void_p), ("p_cap", C.c_void_p),
+                ("seg_cap", C.c_void_p), ("u_init", C.c_void_p), ("unit_price_row", C.c_void_p),
+                ("nprice", C.c_int32), ("price_row", C.c_void_p), ("price_ptr", C.c_void_p),
+                ("price_member", C.c_void_p), ("price_scale", C.c_double)]
+
+
+class WarmParams(C.Structure):
+    _fields_ = [("warm_max_iter", C.c_int64), ("first_check", C.c_int32), ("cold_first_kkt", C.c_double)]
+
+
+WS_FILL_VW, WS_FILL_SEGMENTS, WS_FILL_PRICES = 1, 2, 4
 
 _lib = None
 
@@ -89,6 +110,24 @@ _SIGS = {
     "scuc_lp_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "scuc_lp_destroy": (None, [C.c_void_p]),
+    "scuc_ws_default_train_params": (None, [C.POINTER(WsTrainParams)]),
+    "scuc_ws_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_void_p]),
+    "scuc_ws_num_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "scuc_ws_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "scuc_ws_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "scuc_ws_set_input_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_ws_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "scuc_ws_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                    C.POINTER(WsTrainParams), C.c_void_p, C.POINTER(C.c_double)]),
+    "scuc_ws_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
+                                C.c_int32, C.POINTER(WsTrainParams), C.c_void_p]),
+    "scuc_ws_destroy": (None, [C.c_void_p]),
+    "scuc_ws_assemble": (C.c_int, [C.c_void_p, C.POINTER(WsLayout), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_ws_targets": (C.c_int, [C.c_void_p, C.POINTER(WsLayout), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_default_warm_params": (None, [C.POINTER(WarmParams)]),
+    "scuc_lp_solve_warm": (C.c_int, [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p,
+                                     C.POINTER(WarmParams), C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(SolveInfo)]),
     "scuc_last_error": (C.c_char_p, []),
 }
 

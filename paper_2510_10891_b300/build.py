@@ -19,7 +19,7 @@ def sources():
 
 def deps():
     return sources() + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + sorted(
-        glob.glob(os.path.join(HERE, "csrc", "*.h"))) + [os.path.join(ROOT, "include", "scuc_lp.h")]
+        glob.glob(os.path.join(HERE, "csrc", "*.h"))) + sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

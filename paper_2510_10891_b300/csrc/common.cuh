@@ -85,6 +85,7 @@ struct Ctrl {
   int32_t first_check, done, status, restart_pending;
   int32_t restarts, nlog, fp64_phase, stall;
   double kkt, rp, rd, gap, pobj, dobj;
+  double reject_kkt;  // > 0: stop with SCUC_ST_FALLBACK_COLD if the first check has kkt >= this
 };
 
 struct PowerCtrl {

@@ -521,7 +521,7 @@ int Handle::launch_period(int check_every, bool profile) {
 }
 
 int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double* y0_in, double* xo,
-                  double* yo, double* zo, scuc_solve_info* info) {
+                  double* yo, double* zo, scuc_solve_info* info, double reject_kkt) {
   using clk = std::chrono::steady_clock;
   if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
       (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1) {
@@ -586,6 +586,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.k = 0; C.t = 0; C.iters_fp32 = 0;
   C.rho0 = 0; C.rho_prev = 0; C.best_kkt = INFINITY;
   C.first_check = 1; C.done = 0; C.status = -1; C.restart_pending = 0;
+  C.reject_kkt = reject_kkt;
   C.restarts = 0; C.nlog = 0; C.fp64_phase = mixed ? 0 : 1; C.stall = 0;
   SCUC_CUDA(cudaMemcpyAsync(ctrl, &C, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
   if (p.check_every > coef_cap) {

@@ -67,7 +67,8 @@ struct Handle {
   int ensure_log(int cap);
   int launch_period(int check_every, bool profile);
   int solve(const scuc_solve_params& p, const double* x0, const double* y0, double* xo,
-            double* yo, double* zo, scuc_solve_info* info);
+            double* yo, double* zo, scuc_solve_info* info, double reject_kkt = 0.0);
+  int* pt_flag = nullptr;  // index checks of scuc_ws_assemble / scuc_ws_targets
   int matvec(int transpose, const double* in, double* out);
   int device_error();
   int kkt_noalloc(const double* x, const double* y, const double* z, double* out);

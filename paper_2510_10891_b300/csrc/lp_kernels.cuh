@@ -248,6 +248,8 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, int chunk, double Sx,
     status = SCUC_ST_NUMERICAL;
   } else if (kkt <= C->tol) {
     status = SCUC_ST_OPTIMAL;
+  } else if (C->reject_kkt > 0.0 && t == (int64_t)C->check_every && kkt >= C->reject_kkt) {
+    status = SCUC_ST_FALLBACK_COLD;  // a warm start whose first check is no better than the cold start
   } else {
     if (C->first_check) {
       C->rho0 = rho;

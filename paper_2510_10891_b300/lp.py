@@ -99,6 +99,30 @@ class LP:
                                       dp(z_out), C.byref(info)))
         return info_dict(info)
 
+    def solve_warm(self, x0, y0=None, warm_max_iter=0, first_check=1, cold_first_kkt=0.0,
+                   x_out=None, y_out=None, z_out=None, **params) -> dict:
+        """Warm solve with cold start as the fallback (scuc_lp_solve_warm).
+        x0/y0 and the outputs are torch CUDA float64 tensors (device) or numpy
+        arrays (host; then the outputs are returned in the dict)."""
+        p = default_params(**params)
+        info = L.SolveInfo()
+        wp = L.WarmParams()
+        wp.warm_max_iter, wp.first_check, wp.cold_first_kkt = int(warm_max_iter), int(first_check), float(cold_first_kkt)
+        if hasattr(x0, "data_ptr"):
+            p.device_ptrs = 1
+            dp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+            L.check(L.lib().scuc_lp_solve_warm(self.h, C.byref(p), dp(x0), dp(y0), C.byref(wp),
+                                               dp(x_out), dp(y_out), dp(z_out), C.byref(info)))
+            return {"info": info_dict(info)}
+        p.device_ptrs = 0
+        out = {k: np.zeros(self.n if k in ("x", "z") else self.m) for k in ("x", "y", "z")}
+        L.check(L.lib().scuc_lp_solve_warm(self.h, C.byref(p), _ptr(_f64(x0)),
+                                           _ptr(_f64(y0)) if y0 is not None else None,
+                                           C.byref(wp), _ptr(out["x"]), _ptr(out["y"]),
+                                           _ptr(out["z"]), C.byref(info)))
+        out["info"] = info_dict(info)
+        return out
+
     def log(self, cap=None) -> list:
         cap = 4096 if cap is None else max(0, int(cap))
         buf = (L.CheckLog * max(cap, 1))()
