@@ -1,12 +1,15 @@
 """Benchmark: seconds to 1e-4 KKT on the 13,000-bus SCUC LP relaxation.
 
-One step = one pass of the whole path over one LP: Pock-Chambolle scaling,
-power method, restarted HPR iterations to max(r_p, r_d, gap) <= 1e-4
-(Sec. 3), then Round + Algorithm 1 fixing and bound propagation with the
-reduced-LP build (Sec. 4) when the library provides them.  The LP is
-created on the device before timing (inputs resident in HBM); `e2e`
+One step = one pass of the whole path over one LP: the warm-start network's
+prediction for every generator-hour and the assembled starting point, then
+Pock-Chambolle scaling, power method and restarted HPR iterations to
+max(r_p, r_d, gap) <= 1e-4 (Sec. 3) from that point (with the cold-start
+reference period and fallback), then Round + Algorithm 1 fixing and bound
+propagation with the reduced-LP build (Sec. 4).  The LP, the features and
+the network are on the device before timing (inputs resident in HBM); `e2e`
 repeats the measurement through the C ABI from host buffers, host<->device
-copies included.  Prints one JSON line.
+copies included.  Variants on the same GPU: plain FP64 from cold start, FP32
+matvecs from cold start.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -31,6 +34,8 @@ METRIC = "s to 1e-4 KKT, 13k-bus SCUC LP: plain vs warm/batched/FP32; SpMV % HBM
 WORKLOAD = "scuc13k"
 WORKLOAD_DESC = ("13,000 buses, 18,000 lines, 4,000 units, T=36, 200 N-1 lines; Eq. 1-7 LP relaxation, "
                  "PTDF network rows (Eq. 6), seed 20000")
+WS_WEIGHTS = os.path.join(ROOT, "paper_2510_10891_b300", "weights", "ws_mlp.npz")
+WS_FILL = 0   # u and p' from the network; v, w, segments and duals from the iteration
 
 
 def peaks():
@@ -175,6 +180,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--start", default="warm", choices=["warm", "cold"],
+                    help="warm: learned warm start (weights in paper_2510_10891_b300/weights)")
     ap.add_argument("--ncu-case", default=None,
                     help="profiling target: 128 mixed-precision iterations (FP32 matvecs, no graph) "
                          "on this preset, no JSON line")
@@ -201,6 +208,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2510_10891_b300 as P
+    from paper_2510_10891_b300 import warmstart as WS
+    from scuc_gen.features import ws_features, ws_layout_arrays
     inst = build_instance()
     m, n, nnz = inst.m, inst.n, inst.nnz
     stream = torch.cuda.current_stream()
@@ -211,10 +220,27 @@ def main():
     kw = dict(tol=1e-4, precision=args.precision, profile=1, time_limit_s=600.0)
     xl0, xu0 = lp.get_bounds()
     fix_ms = []
+    warm = args.start == "warm"
+    GT = inst.G * inst.T
+    if warm:
+        net = WS.WarmStartNet.load(WS_WEIGHTS, stream=stream.cuda_stream)
+        lay_arrays = ws_layout_arrays(inst)
+        layout = WS.Layout(lay_arrays, WS_FILL)
+        feats = ws_features(inst)
+        Xd = torch.as_tensor(feats, device="cuda")
+        pred = torch.empty((GT, 3), dtype=torch.float32, device="cuda")
+        x0 = torch.empty(n, dtype=torch.float64, device="cuda")
 
     def step():
-        # A0-A7: solve the relaxation; F1-F3: fix, propagate, build the reduced LP
-        info = lp.solve_device(x_out=xo, y_out=yo, z_out=zo, **kw)
+        # W: predictions and starting point; A0-A7: solve the relaxation;
+        # F1-F3: fix, propagate, build the reduced LP
+        if warm:
+            net.predict(Xd, out=pred)
+            WS.assemble(lp, layout, pred, x0=x0)
+            info = lp.solve_warm(x0, x_out=xo, y_out=yo, z_out=zo, **kw)["info"]
+            info["launches"] += WS.launches_predict(net.dims) + WS.launches_assemble(layout)
+        else:
+            info = lp.solve_device(x_out=xo, y_out=yo, z_out=zo, **kw)
         r = lp.fix_and_propagate(inst.G, inst.T, inst.u_idx, inst.v_idx, inst.w_idx, inst.u_init, xo,
                                  tau=0.1, is_int=inst.is_int)
         if r["reduced"] is not None:
@@ -305,26 +331,81 @@ def main():
            "gpu_launches": int(sum(i["launches"] for i in infos)),
            "wall_s_timed": wall}
 
+    if warm:
+        out["config"]["start"] = ("learned warm start: MLP %s (BF16 tensor cores) on %d generator-hours, "
+                                  "u and p' assembled, cold-start reference period + fallback" %
+                                  ("-".join(str(d) for d in net.dims), GT))
+        out["config"]["warm"] = {"status": last["status_name"], "ref_iters": last["ref_iters"],
+                                 "warm_iters_rejected": last["warm_iters"],
+                                 "cold_first_kkt": last["cold_first_kkt"]}
+    else:
+        out["config"]["start"] = "cold"
+
     if rank == 0 and not args.no_plain:
-        # plain FP64 on the same GPU, for the FP32-matvec gain (solve only)
-        lp.set_bounds(xl0, xu0)
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pi = lp.solve_device(x_out=xo, y_out=yo, z_out=zo, tol=1e-4, precision="fp64", time_limit_s=600.0)
-        e1.record(stream); e1.synchronize()
-        out["variants"] = {"plain_fp64_s": e0.elapsed_time(e1) / 1e3, "plain_fp64_iters": pi["iters"],
-                           "plain_fp64_status": pi["status_name"], args.precision + "_s": per_step}
-        out["_fp64_iters"] = pi["iters"]
-        out["_power_iters"] = pi["power_iters"]
+        # the same LP from cold start on the same GPU: plain FP64 and FP32
+        # matvecs (solve + fix, as in the step)
+        def timed(prec):
+            lp.set_bounds(xl0, xu0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pi = lp.solve_device(x_out=xo, y_out=yo, z_out=zo, tol=1e-4, precision=prec, time_limit_s=600.0)
+            r = lp.fix_and_propagate(inst.G, inst.T, inst.u_idx, inst.v_idx, inst.w_idx, inst.u_init, xo,
+                                     tau=0.1, is_int=inst.is_int)
+            e1.record(stream); e1.synchronize()
+            if r["reduced"] is not None:
+                r["reduced"].close()
+            return e0.elapsed_time(e1) / 1e3, pi, r["fix"]
+        xw = xo.clone() if warm else None
+        fix_w = None
+        if warm:
+            lp.set_bounds(xl0, xu0)
+            fix_w = lp.fix_and_propagate(inst.G, inst.T, inst.u_idx, inst.v_idx, inst.w_idx, inst.u_init, xw,
+                                         tau=0.1, is_int=inst.is_int, build_reduced=False)["fix"]
+        t64, p64, fix64 = timed("fp64")
+        x64 = xo.clone()
+        tmx, pmx, _ = timed("mixed")
+        v = {"plain_fp64_s": t64, "plain_fp64_iters": p64["iters"], "plain_fp64_status": p64["status_name"],
+             "cold_mixed_s": tmx, "cold_mixed_iters": pmx["iters"],
+             "speedup_vs_plain_fp64": t64 / per_step}
+        if warm:
+            v["warm_mixed_s"] = per_step
+            v["warm_mixed_iters"] = last["iters"]
+            v["warm_vs_plain_fp64"] = {
+                "rel_objective_diff": abs(last["pobj"] - p64["pobj"]) / max(1.0, abs(p64["pobj"])),
+                "kkt_warm": last["kkt"], "kkt_plain": p64["kkt"],
+                "rel_x_distance": float(torch.linalg.vector_norm(xw - x64) / torch.linalg.vector_norm(x64)),
+                "fix_decisions_differing": int(np.sum(fix_w != fix64))}
+        out["variants"] = v
+        out["_fp64_iters"] = p64["iters"]
+        out["_power_iters"] = p64["power_iters"]
 
     if not args.no_e2e:
         # through the C ABI from host buffers: create (H2D + device setup), solve, copy back
         ets = []
+        ws_h2d = 0
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             lp2 = P.LP(inst)
-            r = lp2.solve(tol=1e-4, precision=args.precision, time_limit_s=600.0)
+            if warm:
+                # this step's features and layout from host memory
+                Xh = torch.as_tensor(feats).pin_memory().to("cuda", non_blocking=True)
+                lay2 = WS.Layout(lay_arrays, WS_FILL)
+                p2 = net.predict(Xh)
+                x02, _ = WS.assemble(lp2, lay2, p2)
+                xd = torch.empty(n, dtype=torch.float64, device="cuda")
+                yd = torch.empty(m, dtype=torch.float64, device="cuda")
+                zd = torch.empty(n, dtype=torch.float64, device="cuda")
+                lp2.solve_warm(x02, x_out=xd, y_out=yd, z_out=zd, tol=1e-4, precision=args.precision,
+                               time_limit_s=600.0)
+                r = {"x": xd.cpu().numpy(), "y": yd.cpu().numpy(), "z": zd.cpu().numpy()}
+                ws_h2d = feats.nbytes + sum(np.asarray(lay_arrays[k]).nbytes for k in
+                                            ("u_col", "v_col", "w_col", "p_col", "seg_col", "p_cap", "seg_cap",
+                                             "u_init", "unit_price_row", "price_row", "price_ptr",
+                                             "price_member"))
+            else:
+                r = lp2.solve(tol=1e-4, precision=args.precision, time_limit_s=600.0)
             f = lp2.fix_and_propagate(inst.G, inst.T, inst.u_idx, inst.v_idx, inst.w_idx, inst.u_init,
                                       r["x"], tau=0.1, is_int=inst.is_int)
             fix_h = f["fix"]                 # decisions back on the host
@@ -332,8 +413,7 @@ def main():
                 f["reduced"].close()
             lp2.close()
             ets.append(time.perf_counter() - t0)
-        GT = inst.G * inst.T
-        h2d = 8 * (m + 1) + 12 * nnz + 24 * n + m + 16 * m + 8 * n + 12 * GT + inst.G + n
+        h2d = 8 * (m + 1) + 12 * nnz + 24 * n + m + 16 * m + 8 * n + 12 * GT + inst.G + n + ws_h2d
         d2h = 16 * n + 8 * m + 3 * GT
         out["e2e"] = {"value": float(np.mean(ets)), "unit": "s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h}

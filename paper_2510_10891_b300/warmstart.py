@@ -165,6 +165,23 @@ class Layout:
         return other
 
 
+def launches_predict(dims) -> int:
+    """Kernels one scuc_ws_predict launches: standardisation, a product and a
+    bias/activation kernel per layer, the output maps."""
+    return 2 + 2 * (len(dims) - 1)
+
+
+def launches_assemble(layout: "Layout") -> int:
+    """Kernels one scuc_ws_assemble launches: the index checks of the arrays
+    the fill bits use, the base point, the unit-hours and the price rows."""
+    f = layout.s.fill
+    checks = 2 + (2 if f & L.WS_FILL_VW else 0) + (1 if f & L.WS_FILL_SEGMENTS else 0)
+    prices = f & L.WS_FILL_PRICES and layout.s.nprice > 0
+    if prices:
+        checks += 3                       # rows, pointers, members
+    return checks + 2 + (1 if prices else 0)
+
+
 def assemble(lp, layout: Layout, pred, x0=None, y0=None):
     """Starting point from predictions (scuc_ws_assemble); returns (x0, y0)
     CUDA float64 tensors (y0 only when given or when FILL_PRICES is set)."""
