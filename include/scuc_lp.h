@@ -213,10 +213,40 @@ int scuc_lp_get_log(const scuc_lp* lp, scuc_check_log* out, int32_t cap, int32_t
  * Uses the same SpMV kernels as the solver (FP64).                      */
 int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double* out_dev);
 
-/* Solve several LPs (each with its own handle; they may live on different
- * streams of the same device) with the same parameters.  infos[count]. */
+/* Batch of LP solves: the successive-fixing rounds of many instances are
+ * independent relaxations (Sec. 4, Algorithm 2), solved here together.
+ * The LPs are laid out as one block-diagonal LP and each iteration of Eq. 9
+ * is one launch over all of them; every LP keeps its own scaling (Sec.
+ * 3.A), lambda, sigma, Halpern counter, restarts, precision phase and stop
+ * test, so each follows the iteration of its own scuc_lp_solve (the same
+ * checks and restart decisions; matvec sums may differ in rounding order).
+ *  lps[count]: distinct handles on one device (SCUC_E_INVALID otherwise).
+ *  p: as scuc_lp_solve (profile is ignored); NULL: defaults.
+ *  x_out[count], y_out[count], z_out[count]: NULL, or per-LP output
+ *    pointers (each may be NULL), device or host per p->device_ptrs.
+ *  infos[count]: per-LP results; setup_ms/solve_ms/launches are those of
+ *    the whole batch.  Each handle's check log is replaced by its LP's.
+ *  binfo (may be NULL): autotune is read (NULL: on); the chosen SpMV
+ *    partition shapes and the batch timings are written.
+ * The call returns after all work has completed.                        */
+typedef struct {
+  int32_t autotune;        /* in: 1 = time candidate partition shapes       */
+  int32_t ept_A, run_A;    /* out: entries per thread of list rows, shortest
+                              staged run, for A                            */
+  int32_t ept_T, run_T;    /* out: the same for A^T                         */
+  int32_t candidates;      /* out: shapes timed                             */
+  int32_t blocks_A, blocks_T;  /* out: blocks of one SpMV launch            */
+  double setup_ms;         /* out: scaling, power methods, layout, tuning   */
+  double tune_ms;          /* out: of which the partition tuning            */
+  double solve_ms;         /* out: iterations                               */
+  double total_ms;         /* out: whole call                               */
+  int64_t launches;        /* out: kernels launched                         */
+  int64_t periods;         /* out: check periods run                        */
+} scuc_batch_info;
+
 int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_params* p,
-                        scuc_solve_info* infos);
+                        double* const* x_out, double* const* y_out, double* const* z_out,
+                        scuc_solve_info* infos, scuc_batch_info* binfo);
 
 /* ---------------------------------------------------------------------- */
 /* Logic-driven fixing and presolve (Sec. 4.1 Round + Algorithm 1; the      */

@@ -38,6 +38,14 @@ class SolveInfo(C.Structure):
                 ("warm_iters", C.c_int64), ("ref_iters", C.c_int64), ("cold_first_kkt", C.c_double)]
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("autotune", C.c_int32), ("ept_A", C.c_int32), ("run_A", C.c_int32), ("ept_T", C.c_int32),
+                ("run_T", C.c_int32), ("candidates", C.c_int32), ("blocks_A", C.c_int32),
+                ("blocks_T", C.c_int32), ("setup_ms", C.c_double), ("tune_ms", C.c_double),
+                ("solve_ms", C.c_double), ("total_ms", C.c_double), ("launches", C.c_int64),
+                ("periods", C.c_int64)]
+
+
 class CheckLog(C.Structure):
     _fields_ = [("iter", C.c_int64), ("restart", C.c_int32), ("first", C.c_int32),
                 ("rp", C.c_double), ("rd", C.c_double), ("gap", C.c_double), ("pobj", C.c_double),
@@ -99,7 +107,8 @@ _SIGS = {
     "scuc_lp_get_log": (C.c_int, [C.c_void_p, C.POINTER(CheckLog), C.c_int32, C.POINTER(C.c_int32)]),
     "scuc_lp_matvec": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "scuc_lp_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(SolveParams),
-                                      C.POINTER(SolveInfo)]),
+                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(SolveInfo), C.POINTER(BatchInfo)]),
     "scuc_lp_kkt_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "scuc_default_fix_params": (None, [C.POINTER(FixParams)]),
     "scuc_fix_and_propagate": (C.c_int, [C.c_void_p, C.POINTER(ScucMap), C.c_void_p, C.c_void_p,

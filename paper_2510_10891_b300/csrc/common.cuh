@@ -29,18 +29,23 @@ constexpr int kNnzCap = 2048;      // nonzeros staged in shared memory per stage
 constexpr int kMaxRows = 256;      // rows per staged block
 constexpr int kShortMax = 32;        // short rows: <= this many nonzeros
 constexpr int kGroupRowMax = 4096;   // list rows up to this many; longer rows get a block
-constexpr int kStagedMinRun = 32;    // contiguous short-row runs at least this long are staged
 constexpr int kDecideThreads = 1024;
 
 // block types of a partition entry
 constexpr int kStagedBlock = 0, kGroupListBlock = 1;
 
-// threads per row of a list row: about 16 entries per thread, 4..32
-inline int group_size_for(int len) {
+// threads per row of a list row: about ept entries per thread, 4..32
+inline int group_size_for(int len, int ept = 16) {
   int g = 4;
-  while (g < 32 && g * 16 < len) g *= 2;
+  while (g < 32 && g * ept < len) g *= 2;
   return g;
 }
+
+// tunable shape of a partition (plan_partition)
+struct PartShape {
+  int ept = 16;      // target entries per thread of list rows
+  int min_run = 32;  // shortest run of short rows that is staged in shared memory
+};
 
 // streamed long rows: tiles of kTile entries, kStages-deep shared-memory ring
 constexpr int kTile = 960;

@@ -44,18 +44,22 @@ static int grid_for(int64_t work, int block = kBlock) {
   return (int)g;
 }
 
-// Partition (host): rows longer than kGroupRowMax get a block each; other
-// rows get a group of group_size_for(len) threads (about 16 entries per
-// thread), kBlock/gsz rows of the same group size per block, except
-// contiguous runs of >= kStagedMinRun short rows, which are packed into
-// staged blocks of <= kMaxRows rows / <= kNnzCap nonzeros (threads per row =
-// largest power of two with gsz * rows <= kBlock).  Longest work first.
-int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
-                    std::vector<int>* list_out) {
-  std::vector<int> Lr, G[6];  // G[k]: rows with group size 1 << k (k = 2..5)
+// Host plan of a partition (see Partition): rows with more than kGroupRowMax
+// nonzeros are streamed (long_rows) when allow_stream, else they go to
+// 32-thread list groups; rows of kShortMax+1..kGroupRowMax nonzeros get a
+// group of group_size_for(len, shape.ept) threads, kBlock/gsz rows of the
+// same group size per block; runs of at least shape.min_run consecutive
+// short rows are packed into staged blocks of <= kMaxRows rows / <= kNnzCap
+// nonzeros (threads per row = largest power of two with gsz * rows <=
+// kBlock), shorter runs go to 4-thread list groups.  Longest work first.
+void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_stream,
+                    std::vector<int4>* desc_out, std::vector<int>* list_out, std::vector<int>* long_out) {
+  std::vector<int> G[6];  // G[k]: rows with group size 1 << k (k = 2..5)
   std::vector<int4> staged;
+  std::vector<int>& Lr = *long_out;
+  Lr.clear();
   auto flush_run = [&](int a, int b) {  // short rows [a, b)
-    if (b - a < kStagedMinRun) {
+    if (b - a < shape.min_run) {
       for (int r = a; r < b; r++) G[2].push_back(r);
       return;
     }
@@ -79,12 +83,14 @@ int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector
     if (len <= kShortMax) continue;
     flush_run(run0, r);
     run0 = r + 1;
-    if (len > kGroupRowMax) Lr.push_back(r);
-    else G[__builtin_ctz(group_size_for(len))].push_back(r);
+    if (len > kGroupRowMax && allow_stream) Lr.push_back(r);
+    else G[__builtin_ctz(group_size_for(len, shape.ept))].push_back(r);
   }
   flush_run(run0, m);
-  std::vector<int> list;
-  std::vector<int4> desc;
+  std::vector<int>& list = *list_out;
+  std::vector<int4>& desc = *desc_out;
+  list.clear();
+  desc.clear();
   for (int k = 5; k >= 2; k--) {
     const int gsz = 1 << k, per = kBlock / gsz;
     const std::vector<int>& R = G[k];
@@ -95,6 +101,11 @@ int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector
     }
     if (k == 3) desc.insert(desc.end(), staged.begin(), staged.end());
   }
+}
+
+// device copies of a planned partition (freed by free_partition)
+int upload_partition(const std::vector<int4>& desc, const std::vector<int>& list, const std::vector<int>& Lr,
+                     Partition* P) {
   P->nlong = (int)Lr.size();
   P->nstream = std::min<int>(P->nlong, 2 * 148);  // persistent streaming CTAs, two per SM
   P->smem = P->nlong ? std::max(kStagedSmem, kStreamSmem) : kStagedSmem;
@@ -110,6 +121,24 @@ int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector
     SCUC_CUDA(cudaMemcpy(P->desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice));
   if (!list.empty())
     SCUC_CUDA(cudaMemcpy(P->list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return SCUC_OK;
+}
+
+void free_partition(Partition* P) {
+  for (void* q : {(void*)P->desc, (void*)P->list, (void*)P->long_rows, (void*)P->err})
+    if (q) cudaFree(q);
+  P->desc = nullptr;
+  P->list = nullptr;
+  P->long_rows = nullptr;
+  P->err = nullptr;
+}
+
+int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
+                    std::vector<int>* list_out) {
+  std::vector<int4> desc;
+  std::vector<int> list, Lr;
+  plan_partition(rp, m, PartShape{}, true, &desc, &list, &Lr);
+  SCUC_TRY(upload_partition(desc, list, Lr, P));
   if (desc_out) *desc_out = desc;
   if (list_out) *list_out = list;
   return SCUC_OK;
@@ -407,6 +436,10 @@ DevLP Handle::dev() const {
   L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
   L.pA = pA; L.pT = pT;
   L.ctrl = ctrl; L.log = log_d;
+  L.nlp = 1;
+  L.blkA = L.blkT = L.ablk0 = L.tblk0 = L.row0 = L.col0 = nullptr;
+  L.coef_stride = 0;
+  L.log_stride = 0;
   return L;
 }
 
@@ -868,15 +901,25 @@ int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double*
 }
 
 int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_params* p,
-                        scuc_solve_info* infos) {
-  if (!lps || count < 0 || (count > 0 && !infos)) { scuc::set_error("null argument"); return SCUC_E_INVALID; }
-  for (int32_t i = 0; i < count; i++) {
-    scuc_solve_params q;
-    if (p) q = *p; else scuc_default_params(&q);
-    q.device_ptrs = 0;
-    SCUC_TRY(scuc_lp_solve(lps[i], &q, nullptr, nullptr, nullptr, nullptr, nullptr, &infos[i]));
+                        double* const* x_out, double* const* y_out, double* const* z_out,
+                        scuc_solve_info* infos, scuc_batch_info* binfo) {
+  if (!lps || count < 0 || (count > 0 && !infos)) {
+    scuc::set_error("scuc_lp_solve_batch: null argument");
+    return SCUC_E_INVALID;
   }
-  return SCUC_OK;
+  if (count == 0) return SCUC_OK;
+  std::vector<Handle*> H(count);
+  for (int32_t i = 0; i < count; i++) {
+    if (!lps[i] || !lps[i]->h) {
+      scuc::set_error("scuc_lp_solve_batch: LP %d is null", i);
+      return SCUC_E_INVALID;
+    }
+    H[i] = lps[i]->h;
+  }
+  scuc_solve_params q;
+  if (p) q = *p;
+  else scuc_default_params(&q);
+  return scuc::solve_batch(H.data(), count, q, x_out, y_out, z_out, infos, binfo);
 }
 
 void scuc_lp_destroy(scuc_lp* lp) {

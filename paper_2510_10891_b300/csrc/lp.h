@@ -10,6 +10,11 @@ struct DevLP;  // device view of a handle (lp_kernels.cuh)
 
 int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
                     std::vector<int>* list_out);
+void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_stream,
+                    std::vector<int4>* desc_out, std::vector<int>* list_out, std::vector<int>* long_out);
+int upload_partition(const std::vector<int4>& desc, const std::vector<int>& list, const std::vector<int>& Lr,
+                     Partition* P);
+void free_partition(Partition* P);
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s);
 int dev_alloc_bytes(void** p, size_t bytes);
 
@@ -83,6 +88,10 @@ struct Handle {
 int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
                   const int32_t* col, const double* val, const double* c, const double* xl,
                   const double* xu, const double* lo, const double* hi, void* stream);
+
+// scuc_lp_solve_batch (batch.cu)
+int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* const* xo, double* const* yo,
+                double* const* zo, scuc_solve_info* infos, scuc_batch_info* bi);
 
 }  // namespace scuc
 

@@ -25,11 +25,34 @@ struct DevLP {
   Partition pA, pT;
   Ctrl* ctrl;
   scuc_check_log* log;
+  // A batch of nlp LPs stored as one block-diagonal LP (nlp = 1: one LP).
+  // Blocks of pA / pT never span two LPs: blkA / blkT give the LP of each
+  // block (nullptr: LP 0), ablk0 / tblk0 the first block of each LP, row0 /
+  // col0 its first row and column.  Per-LP state: ctrl[lp], coef + lp *
+  // coef_stride, log + lp * log_stride.
+  int nlp;
+  const int *blkA, *blkT, *ablk0, *tblk0, *row0, *col0;
+  int coef_stride, log_stride;
 };
+
+// range [a, b) of LP lp in an offsets array (nullptr: the whole range)
+__device__ __forceinline__ void lp_range(const int* off, int lp, int total, int& a, int& b) {
+  if (off) {
+    a = off[lp];
+    b = off[lp + 1];
+  } else {
+    a = 0;
+    b = total;
+  }
+}
 
 __device__ __forceinline__ double clampd(double v, double l, double u) {
   return v < l ? l : (v > u ? u : v);
 }
+
+// Kernels and their helpers have internal linkage: every translation unit
+// that launches them compiles its own copy.
+namespace {
 
 // ---------------------------------------------------------------------------
 // primal step over A^T y: x_bar = Pi_K(x + sigma (g - c)), reflection, Halpern
@@ -68,9 +91,11 @@ struct PrimalEpi {
 template <bool CHECK>
 __global__ void __launch_bounds__(kBlock) k_primal(DevLP L, int j) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const Ctrl* ctrl = L.ctrl;
+  const int lp = L.blkT ? L.blkT[blockIdx.x] : 0;
+  const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
-  PrimalEpi<CHECK> epi{L, ctrl->sigma, L.coef[2 * j], L.coef[2 * j + 1], ctrl->fp64_phase != 0,
+  const double* cf = L.coef + (size_t)lp * L.coef_stride;
+  PrimalEpi<CHECK> epi{L, ctrl->sigma, cf[2 * j], cf[2 * j + 1], ctrl->fp64_phase != 0,
                        {0.0, 0.0, 0.0, 0.0}};
   if (epi.fp64) {
     spmv_block<double>(L.rpt, L.colt, L.vst, L.y, L.pT, smem, epi);
@@ -116,9 +141,11 @@ struct DualEpi {
 template <bool CHECK>
 __global__ void __launch_bounds__(kBlock) k_dual(DevLP L, int j) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const Ctrl* ctrl = L.ctrl;
+  const int lp = L.blkA ? L.blkA[blockIdx.x] : 0;
+  const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
-  DualEpi<CHECK> epi{L, ctrl->s_step, L.coef[2 * j], L.coef[2 * j + 1], ctrl->fp64_phase != 0,
+  const double* cf = L.coef + (size_t)lp * L.coef_stride;
+  DualEpi<CHECK> epi{L, ctrl->s_step, cf[2 * j], cf[2 * j + 1], ctrl->fp64_phase != 0,
                      {0.0, 0.0}};
   if (epi.fp64) {
     spmv_block<double>(L.rp, L.col, L.vs, L.xt, L.pA, smem, epi);
@@ -152,8 +179,9 @@ struct ResPrimalEpi {  // A x_bar: primal violation (unscaled), y-part of dobj, 
 
 __global__ void __launch_bounds__(kBlock) k_res_primal(DevLP L) {
   extern __shared__ __align__(128) unsigned char smem[];
-  if (L.ctrl->done) return;
-  ResPrimalEpi epi{L, L.ctrl->beta, {0.0, 0.0, 0.0}};
+  const Ctrl* ctrl = L.ctrl + (L.blkA ? L.blkA[blockIdx.x] : 0);
+  if (ctrl->done) return;
+  ResPrimalEpi epi{L, ctrl->beta, {0.0, 0.0, 0.0}};
   spmv_block<double>(L.rp, L.col, L.vs, L.xbar, L.pA, smem, epi);
   block_store<3>(epi.acc, L.partRA, L.pA.nblk);
 }
@@ -170,8 +198,9 @@ struct ResDualEpi {  // A^T y_bar: dual residual (unscaled)
 
 __global__ void __launch_bounds__(kBlock) k_res_dual(DevLP L) {
   extern __shared__ __align__(128) unsigned char smem[];
-  if (L.ctrl->done) return;
-  ResDualEpi epi{L, L.ctrl->gamma, {0.0}};
+  const Ctrl* ctrl = L.ctrl + (L.blkT ? L.blkT[blockIdx.x] : 0);
+  if (ctrl->done) return;
+  ResDualEpi epi{L, ctrl->gamma, {0.0}};
   spmv_block<double>(L.rpt, L.colt, L.vst, L.ybar, L.pT, smem, epi);
   block_store<1>(epi.acc, L.partRT, L.pT.nblk);
 }
@@ -194,38 +223,47 @@ __device__ double decide_sum(const double* p, int cnt) {
 // ---------------------------------------------------------------------------
 // decide: residuals, restart rule, sigma update, stop (one block)
 // ---------------------------------------------------------------------------
-__device__ long long decide_logic(const DevLP& L, Ctrl* C, int chunk, double Sx, double Sxa,
-                                  double pobj_s, double dz, double Sy, double Sya, double viol2,
+__device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, int chunk, double Sx,
+                                  double Sxa, double pobj_s, double dz, double Sy, double Sya, double viol2,
                                   double dy, double dres2, double cross);
 
+// one block per LP of the batch (blockIdx.x = LP)
 __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
-  Ctrl* C = L.ctrl;
+  const int lp = blockIdx.x;
+  Ctrl* C = L.ctrl + lp;
   if (C->done) return;
   const int nA = L.pA.nblk, nT = L.pT.nblk;
-  const double Sx = decide_sum(L.partP + 0 * nT, nT);
-  const double Sxa = decide_sum(L.partP + 1 * nT, nT);
-  const double pobj_s = decide_sum(L.partP + 2 * nT, nT);
-  const double dz = decide_sum(L.partP + 3 * nT, nT);
-  const double Sy = decide_sum(L.partD + 0 * nA, nA);
-  const double Sya = decide_sum(L.partD + 1 * nA, nA);
-  const double viol2 = decide_sum(L.partRA + 0 * nA, nA);
-  const double dy = decide_sum(L.partRA + 1 * nA, nA);
-  const double dres2 = decide_sum(L.partRT, nT);
-  const double cross = decide_sum(L.partRA + 2 * nA, nA);
+  int a0, a1, t0, t1;
+  lp_range(L.ablk0, lp, nA, a0, a1);
+  lp_range(L.tblk0, lp, nT, t0, t1);
+  const int ca = a1 - a0, ct = t1 - t0;
+  const double Sx = decide_sum(L.partP + 0 * nT + t0, ct);
+  const double Sxa = decide_sum(L.partP + 1 * nT + t0, ct);
+  const double pobj_s = decide_sum(L.partP + 2 * nT + t0, ct);
+  const double dz = decide_sum(L.partP + 3 * nT + t0, ct);
+  const double Sy = decide_sum(L.partD + 0 * nA + a0, ca);
+  const double Sya = decide_sum(L.partD + 1 * nA + a0, ca);
+  const double viol2 = decide_sum(L.partRA + 0 * nA + a0, ca);
+  const double dy = decide_sum(L.partRA + 1 * nA + a0, ca);
+  const double dres2 = decide_sum(L.partRT + t0, ct);
+  const double cross = decide_sum(L.partRA + 2 * nA + a0, ca);
   __shared__ long long s_knew;
-  if (threadIdx.x == 0) s_knew = decide_logic(L, C, chunk, Sx, Sxa, pobj_s, dz, Sy, Sya, viol2, dy, dres2, cross);
+  if (threadIdx.x == 0)
+    s_knew = decide_logic(L, C, L.log + (size_t)lp * L.log_stride, chunk, Sx, Sxa, pobj_s, dz, Sy, Sya, viol2,
+                          dy, dres2, cross);
   __syncthreads();
   // Halpern weights of the next period, computed once (FP64 division is slow on
   // this part; every iterate update would otherwise divide per thread)
   const long long kn = s_knew;
+  double* cw = L.coef_w + (size_t)lp * L.coef_stride;
   for (int j = threadIdx.x; j < chunk; j += kDecideThreads) {
-    L.coef_w[2 * j] = 1.0 / (double)(kn + j + 2);
-    L.coef_w[2 * j + 1] = (double)(kn + j + 1) / (double)(kn + j + 2);
+    cw[2 * j] = 1.0 / (double)(kn + j + 2);
+    cw[2 * j + 1] = (double)(kn + j + 1) / (double)(kn + j + 2);
   }
 }
 
-__device__ long long decide_logic(const DevLP& L, Ctrl* C, int chunk, double Sx, double Sxa,
-                                  double pobj_s, double dz, double Sy, double Sya, double viol2,
+__device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, int chunk, double Sx,
+                                  double Sxa, double pobj_s, double dz, double Sy, double Sya, double viol2,
                                   double dy, double dres2, double cross) {
 
   const double sigma = C->sigma, lambda = C->lambda, bg = C->beta * C->gamma;
@@ -263,7 +301,7 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, int chunk, double Sx,
     C->rho_prev = rho;
   }
   if (C->nlog < C->log_cap) {
-    scuc_check_log& e = L.log[C->nlog];
+    scuc_check_log& e = log[C->nlog];
     e.iter = t; e.restart = restart; e.first = was_first;
     e.rp = rp; e.rd = rd; e.gap = gap; e.pobj = pobj; e.dobj = dobj; e.rho = rho;
     e.sigma = sigma; e.fp64 = C->fp64_phase; e.pad = 0;
@@ -298,12 +336,20 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, int chunk, double Sx,
   return C->k;
 }
 
-// restart: anchor <- current point (runs at the start of each period)
+// restart: anchor <- current point (runs at the start of each period);
+// blockIdx.y = LP of the batch
 __global__ void k_anchor(DevLP L) {
-  if (L.ctrl->done || !L.ctrl->restart_pending) return;
+  const int lp = blockIdx.y;
+  const Ctrl* C = L.ctrl + lp;
+  if (C->done || !C->restart_pending) return;
+  int a, b;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) L.x0[i] = L.x[i];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.m; i += stride) L.y0[i] = L.y[i];
+  lp_range(L.col0, lp, L.n, a, b);
+  for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += stride) L.x0[i] = L.x[i];
+  lp_range(L.row0, lp, L.m, a, b);
+  for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += stride) L.y0[i] = L.y[i];
 }
+
+}  // namespace
 
 }  // namespace scuc

@@ -4,6 +4,8 @@
 #include "lp_kernels.cuh"
 
 namespace scuc {
+namespace {  // internal linkage: each translation unit compiles its own copy
+
 
 // ----------------------------- transpose ---------------------------------
 __global__ void k_count_cols(const int* __restrict__ col, int64_t nnz, int* __restrict__ cnt) {
@@ -338,16 +340,21 @@ __global__ void k_power_norm_seed(int n, double* __restrict__ q, const PowerCtrl
 }
 
 // ------------------------ iterate init / output ---------------------------
+// blockIdx.y = LP of the batch
 __global__ void k_init_iterates(DevLP L, const double* __restrict__ xin, const double* __restrict__ yin) {
-  const double beta = L.ctrl->beta, gamma = L.ctrl->gamma;
+  const int lp = blockIdx.y;
+  const double beta = L.ctrl[lp].beta, gamma = L.ctrl[lp].gamma;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L.n; j += stride) {
+  int c0, c1, r0, r1;
+  lp_range(L.col0, lp, L.n, c0, c1);
+  lp_range(L.row0, lp, L.m, r0, r1);
+  for (int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c1; j += stride) {
     const double v = xin ? xin[j] / (beta * L.Dc[j]) : 0.0;
     const double x = clampd(v, L.xl[j], L.xu[j]);
     L.x[j] = x;
     L.x0[j] = x;
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.m; i += stride) {
+  for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += stride) {
     double v = yin ? yin[i] / (gamma * L.Dr[i]) : 0.0;
     if (!isfinite(L.lo[i]) && v > 0.0) v = 0.0;
     if (!isfinite(L.hi[i]) && v < 0.0) v = 0.0;
@@ -357,15 +364,20 @@ __global__ void k_init_iterates(DevLP L, const double* __restrict__ xin, const d
   }
 }
 
+// blockIdx.y = LP of the batch
 __global__ void k_finalize(DevLP L, double* __restrict__ xo, double* __restrict__ yo, double* __restrict__ zo) {
-  const double beta = L.ctrl->beta, gamma = L.ctrl->gamma;
+  const int lp = blockIdx.y;
+  const double beta = L.ctrl[lp].beta, gamma = L.ctrl[lp].gamma;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L.n; j += stride) {
+  int c0, c1, r0, r1;
+  lp_range(L.col0, lp, L.n, c0, c1);
+  lp_range(L.row0, lp, L.m, r0, r1);
+  for (int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c1; j += stride) {
     if (xo) xo[j] = beta * L.Dc[j] * L.xbar[j];
     if (zo) zo[j] = gamma * L.zbar[j] / L.Dc[j];
   }
   if (yo)
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.m; i += stride)
+    for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += stride)
       yo[i] = gamma * L.Dr[i] * L.ybar[i];
 }
 
@@ -383,5 +395,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_plain(const int* __restrict__ r
   PlainEpi epi{out};
   spmv_block<double>(rp, col, val, in, part, smem, epi);
 }
+
+}  // namespace
 
 }  // namespace scuc

@@ -209,3 +209,38 @@ class LP:
         for k, ln in (("col", nnz), ("val", nnz), ("c", n), ("xl", n), ("xu", n), ("lo", m), ("hi", m)):
             d[k] = d[k][:ln]
         return d
+
+
+def solve_batch(lps, outputs=None, autotune=True, **params):
+    """Solve the LPs together (scuc_lp_solve_batch).
+
+    ``outputs``: None (host solutions are returned), or a list with one
+    (x, y, z) tuple of torch CUDA float64 tensors (entries may be None) per
+    LP.  Returns (per-LP result dicts, batch info dict); with host outputs
+    each result dict carries x, y and z."""
+    p = default_params(**params)
+    cnt = len(lps)
+    hs = (C.c_void_p * max(cnt, 1))(*[lp.h for lp in lps])
+    infos = (L.SolveInfo * max(cnt, 1))()
+    bi = L.BatchInfo()
+    bi.autotune = 1 if autotune else 0
+    ptr3 = [(C.c_void_p * max(cnt, 1))() for _ in range(3)]
+    host = None
+    if outputs is None:
+        p.device_ptrs = 0
+        host = [(np.zeros(lp.n), np.zeros(lp.m), np.zeros(lp.n)) for lp in lps]
+        for i, (x, y, z) in enumerate(host):
+            ptr3[0][i], ptr3[1][i], ptr3[2][i] = x.ctypes.data, y.ctypes.data, z.ctypes.data
+    else:
+        p.device_ptrs = 1
+        for i, trip in enumerate(outputs):
+            for k, t in enumerate(trip):
+                ptr3[k][i] = None if t is None else t.data_ptr()
+    L.check(L.lib().scuc_lp_solve_batch(hs, cnt, C.byref(p), ptr3[0], ptr3[1], ptr3[2], infos, C.byref(bi)))
+    res = []
+    for i in range(cnt):
+        d = {"info": info_dict(infos[i])}
+        if host is not None:
+            d["x"], d["y"], d["z"] = host[i]
+        res.append(d)
+    return res, {f[0]: getattr(bi, f[0]) for f in L.BatchInfo._fields_}
