@@ -137,6 +137,36 @@ def cpu_baseline(inst, gpu_iters, power_iters):
             "s_per_iter": per_iter}
 
 
+def batched_variant(P):
+    """The 64 uneven relaxations of the batch family (200-3,000 buses, 0.15
+    units per bus, T in {24, 36}, seeds 1000-1063) to 1e-4 with FP32 matvecs:
+    one batched call against 64 solo solves on the same GPU (wall clock,
+    setup included on both sides)."""
+    import multiprocessing as mp
+    from scuc_gen.scuc import batch_configs, make_scuc
+    with mp.get_context("spawn").Pool(16) as pool:
+        insts = pool.map(make_scuc, batch_configs(64, 1000))
+    lps = [P.LP(i) for i in insts]
+    kw = dict(tol=1e-4, precision="mixed")
+    P.solve_batch(lps[:2], **kw)
+    t0 = time.perf_counter()
+    res, bi = P.solve_batch(lps, **kw)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    solo = [lp.solve(want=("x",), **kw) for lp in lps]
+    ts = time.perf_counter() - t0
+    its = [r["info"]["iters"] for r in res]
+    out = {"lps": len(lps), "nnz_total": int(sum(i.nnz for i in insts)), "batch_s": tb, "one_by_one_s": ts,
+           "speedup": ts / tb, "all_optimal": all(r["info"]["status"] == 0 for r in res),
+           "iters_min": min(its), "iters_max": max(its), "setup_ms": bi["setup_ms"], "tune_ms": bi["tune_ms"],
+           "iterations_ms": bi["solve_ms"], "shape_A": [bi["ept_A"], bi["run_A"]],
+           "shape_AT": [bi["ept_T"], bi["run_T"]], "launches": bi["launches"],
+           "solo_iters_sum": int(sum(r["info"]["iters"] for r in solo))}
+    for lp in lps:
+        lp.close()
+    return out
+
+
 def build_instance():
     from scuc_gen import make_preset
     return make_preset(WORKLOAD)
@@ -180,6 +210,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--start", default="warm", choices=["warm", "cold"],
                     help="warm: learned warm start (weights in paper_2510_10891_b300/weights)")
     ap.add_argument("--ncu-case", default=None,
@@ -379,6 +410,9 @@ def main():
         out["variants"] = v
         out["_fp64_iters"] = p64["iters"]
         out["_power_iters"] = p64["power_iters"]
+
+    if rank == 0 and not args.no_batch:
+        out.setdefault("variants", {})["batched_64"] = batched_variant(P)
 
     if not args.no_e2e:
         # through the C ABI from host buffers: create (H2D + device setup), solve, copy back
