@@ -28,6 +28,7 @@ __global__ void k_add_offset(int* __restrict__ dst, const int* __restrict__ src,
 template <typename VT>
 struct TuneEpi {
   VT* out;
+  __device__ void load(int) {}
   __device__ void row(int r, VT a) { out[r] = a; }
 };
 
@@ -60,6 +61,9 @@ struct Batch {
   double *y = nullptr, *y0 = nullptr, *ybar = nullptr, *qchk = nullptr, *dychk = nullptr;
   float *xt32 = nullptr, *y32 = nullptr;
   double *partP = nullptr, *partD = nullptr, *partRA = nullptr, *partRT = nullptr;
+  double* gsum = nullptr;
+  float* gsum32 = nullptr;
+  int epi_gx = 1;
   double *xo = nullptr, *yo = nullptr, *zo = nullptr;
   Ctrl* ctrl = nullptr;
   Ctrl* ctrl_h = nullptr;  // pinned, two slots of nlp
@@ -103,6 +107,9 @@ struct Batch {
     L.qchk = qchk; L.dychk = dychk;
     L.coef = coef; L.coef_w = coef;
     L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
+    L.gsum = gsum;
+    L.gsum32 = gsum32;
+    L.epi_gx = epi_gx;
     L.pA = pA; L.pT = pT;
     L.ctrl = ctrl; L.log = log;
     L.nlp = nlp;
@@ -114,29 +121,51 @@ struct Batch {
 };
 
 // Partition of the block-diagonal matrix: each LP's rows planned alone (no
-// streamed rows), then concatenated LP by LP with row and list offsets.
-void plan_batch(const std::vector<std::vector<int>>& rps, const std::vector<int>& off, const PartShape& shape,
-                std::vector<int4>* desc, std::vector<int>* list, std::vector<int>* blk_lp,
-                std::vector<int>* blk0) {
-  desc->clear();
-  list->clear();
+// chunked rows), then merged class by class with row and entry offsets; an
+// LP's rows of one class are padded to whole blocks, so no block spans two
+// LPs.  Blocks write their partial sums LP by LP (slot table), so each LP's
+// partials form one range for the decide kernel.
+void plan_batch(const std::vector<std::vector<int>>& rps, const std::vector<int>& off,
+                const std::vector<int64_t>& eoff, const PartShape& shape, PartPlan* plan,
+                std::vector<int>* blk_lp, std::vector<int>* blk0) {
+  const int nlp = (int)rps.size();
+  std::vector<PartPlan> one(nlp);
+  for (int b = 0; b < nlp; b++) plan_partition(rps[b], (int)rps[b].size() - 1, shape, false, &one[b]);
+  *plan = PartPlan{};
+  plan->chunk_ptr.assign(1, 0);
   blk_lp->clear();
-  blk0->clear();
-  std::vector<int4> d;
-  std::vector<int> l, lr;
-  for (size_t b = 0; b < rps.size(); b++) {
-    plan_partition(rps[b], (int)rps[b].size() - 1, shape, false, &d, &l, &lr);
-    blk0->push_back((int)desc->size());
-    const int loff = (int)list->size();
-    for (int4 e : d) {
-      if (e.x == kGroupListBlock) e.y += loff;
-      else e.y += off[b];
-      desc->push_back(e);
-      blk_lp->push_back((int)b);
+  for (int k = 0; k < 4; k++) {
+    const int per = kBlock >> (5 - k);
+    plan->cls_row[k] = (int)plan->listx.size();
+    plan->cls_blk[k] = (int)blk_lp->size();
+    for (int b = 0; b < nlp; b++) {
+      const int n0 = one[b].cls_row[k], n1 = one[b].cls_row[k + 1];
+      if (n1 == n0) continue;
+      for (int i = n0; i < n1; i++) {
+        int4 e = one[b].listx[i];
+        plan->listx.push_back(make_int4(e.x + off[b], e.y + (int)eoff[b], e.z + (int)eoff[b], 0));
+      }
+      const int nb = (n1 - n0 + per - 1) / per;
+      for (int q = (n1 - n0); q < nb * per; q++) plan->listx.push_back(make_int4(-1, 0, 0, 0));
+      for (int q = 0; q < nb; q++) blk_lp->push_back(b);
     }
-    for (int r : l) list->push_back(r + off[b]);
   }
-  blk0->push_back((int)desc->size());
+  plan->cls_row[4] = (int)plan->listx.size();
+  plan->cls_blk[4] = (int)blk_lp->size();
+  for (int b = 0; b < nlp; b++)
+    for (int4 d : one[b].desc) {
+      plan->desc.push_back(make_int4(d.x + off[b], d.y + (int)eoff[b], d.z + (int)eoff[b], d.w));
+      blk_lp->push_back(b);
+    }
+  // slots: blocks ordered by LP (stable)
+  const int nblk = (int)blk_lp->size();
+  std::vector<int> cnt(nlp + 1, 0);
+  for (int q : *blk_lp) cnt[q + 1]++;
+  for (int b = 0; b < nlp; b++) cnt[b + 1] += cnt[b];
+  *blk0 = cnt;
+  plan->slot.assign(nblk, 0);
+  std::vector<int> next(cnt.begin(), cnt.end() - 1);
+  for (int q = 0; q < nblk; q++) plan->slot[q] = next[(*blk_lp)[q]]++;
 }
 
 // Time one SpMV over the candidate partition (median of three launches).
@@ -164,8 +193,8 @@ int time_spmv(const int* rp, const int* col, const VT* val, const VT* in, VT* ou
 // Choose the shape of one matrix's partition (A or A^T of the batch) and
 // upload it: blk / blk0 get the per-block LP table and LP block offsets.
 int tune_partition(Batch& B, bool transpose, const std::vector<std::vector<int>>& rps,
-                   const std::vector<int>& off, bool autotune, Partition* P, int** blk, int** blk0,
-                   PartShape* chosen, int* ncand) {
+                   const std::vector<int>& off, const std::vector<int64_t>& eoff, bool autotune, Partition* P,
+                   int** blk, int** blk0, PartShape* chosen, int* ncand) {
   std::vector<PartShape> cands;
   if (autotune) {
     for (int ept : {8, 16, 32})
@@ -182,15 +211,15 @@ int tune_partition(Batch& B, bool transpose, const std::vector<std::vector<int>>
   const int rows = transpose ? B.n : B.m;
   const int* rp = transpose ? B.rpt : B.rp;
   const int* col = transpose ? B.colt : B.col;
-  std::vector<int4> desc;
-  std::vector<int> list, lp, b0;
+  PartPlan plan;
+  std::vector<int> lp, b0;
   float best = -1.f;
   PartShape best_sh = cands[0];
   if (cands.size() > 1) {
     for (const PartShape& sh : cands) {
-      plan_batch(rps, off, sh, &desc, &list, &lp, &b0);
+      plan_batch(rps, off, eoff, sh, &plan, &lp, &b0);
       Partition T;
-      SCUC_TRY(upload_partition(desc, list, std::vector<int>(), &T));
+      SCUC_TRY(upload_partition(plan, &T));
       float ms = 0.f;
       int rc = SCUC_OK;
       if (T.nblk == 0) {
@@ -213,8 +242,8 @@ int tune_partition(Batch& B, bool transpose, const std::vector<std::vector<int>>
     }
   }
   (void)rows;
-  plan_batch(rps, off, best_sh, &desc, &list, &lp, &b0);
-  SCUC_TRY(upload_partition(desc, list, std::vector<int>(), P));
+  plan_batch(rps, off, eoff, best_sh, &plan, &lp, &b0);
+  SCUC_TRY(upload_partition(plan, P));
   SCUC_TRY(B.alloc(blk, lp.size()));
   SCUC_TRY(B.alloc(blk0, b0.size()));
   if (!lp.empty()) SCUC_CUDA(cudaMemcpy(*blk, lp.data(), lp.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -229,10 +258,9 @@ int launch_batch_period(Batch& B, int check_every, int ga) {
   k_anchor<<<dim3(ga, B.nlp), kBlock, 0, s>>>(L);
   for (int j = 0; j < check_every; j++) {
     const bool chk = (j == check_every - 1);
-    if (B.pT.nblk) {
-      if (chk) k_primal<true><<<B.pT.nblk, kBlock, B.pT.smem, s>>>(L, j);
-      else k_primal<false><<<B.pT.nblk, kBlock, B.pT.smem, s>>>(L, j);
-    }
+    if (B.pT.nblk) k_primal_sum<<<B.pT.nblk, kBlock, B.pT.smem, s>>>(L);
+    if (chk) k_primal_epi<true><<<dim3(B.epi_gx, B.nlp), kBlock, 0, s>>>(L, j);
+    else k_primal_epi<false><<<dim3(B.epi_gx, B.nlp), kBlock, 0, s>>>(L, j);
     if (B.pA.nblk) {
       if (chk) k_dual<true><<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L, j);
       else k_dual<false><<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L, j);
@@ -246,7 +274,8 @@ int launch_batch_period(Batch& B, int check_every, int ga) {
 }
 
 int64_t period_launches(const Batch& B, int ce) {
-  return 2 + (int64_t)ce * ((B.pT.nblk ? 1 : 0) + (B.pA.nblk ? 1 : 0)) + (B.pA.nblk ? 1 : 0) + (B.pT.nblk ? 1 : 0);
+  return 2 + (int64_t)ce * ((B.pT.nblk ? 1 : 0) + (B.pA.nblk ? 1 : 0) + 1) + (B.pA.nblk ? 1 : 0) +
+         (B.pT.nblk ? 1 : 0);
 }
 
 }  // namespace
@@ -399,11 +428,16 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
   const auto tt0 = clk::now();
   PartShape shA, shT;
   int ncA = 0, ncT = 0;
-  SCUC_TRY(tune_partition(B, false, rps, B.row0_h, autotune, &B.pA, &B.blkA, &B.ablk0, &shA, &ncA));
-  SCUC_TRY(tune_partition(B, true, rpts, B.col0_h, autotune, &B.pT, &B.blkT, &B.tblk0, &shT, &ncT));
+  SCUC_TRY(tune_partition(B, false, rps, B.row0_h, B.nnz0_h, autotune, &B.pA, &B.blkA, &B.ablk0, &shA, &ncA));
+  SCUC_TRY(tune_partition(B, true, rpts, B.col0_h, B.nnz0_h, autotune, &B.pT, &B.blkT, &B.tblk0, &shT, &ncT));
   const double tune_ms = std::chrono::duration<double, std::milli>(clk::now() - tt0).count();
   if (autotune) launches += 4 * (int64_t)(ncA + ncT);
-  SCUC_TRY(B.alloc(&B.partP, 4 * (size_t)B.pT.nblk));
+  int maxn = 1;
+  for (int b = 0; b < nlp; b++) maxn = std::max(maxn, H[b]->n);
+  B.epi_gx = std::max(1, std::min(64, (maxn + kBlock - 1) / kBlock));
+  SCUC_TRY(B.alloc(&B.gsum, n));
+  SCUC_TRY(B.alloc(&B.gsum32, n));
+  SCUC_TRY(B.alloc(&B.partP, 4 * (size_t)B.epi_gx * nlp));
   SCUC_TRY(B.alloc(&B.partD, 2 * (size_t)B.pA.nblk));
   SCUC_TRY(B.alloc(&B.partRA, 3 * (size_t)B.pA.nblk));
   SCUC_TRY(B.alloc(&B.partRT, (size_t)B.pT.nblk));

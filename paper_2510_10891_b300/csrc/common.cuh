@@ -26,13 +26,16 @@ void set_error(const char* fmt, ...);
 
 constexpr int kBlock = 256;        // threads per SpMV block
 constexpr int kNnzCap = 2048;      // nonzeros staged in shared memory per staged block
-constexpr int kMaxRows = 256;      // rows per staged block
+constexpr int kMaxRows = 256;      // rows per staged block (<= kBlock: one epilogue row per thread)
 constexpr int kShortMax = 32;        // short rows: <= this many nonzeros
 constexpr int kGroupRowMax = 4096;   // list rows up to this many; longer rows get a block
 constexpr int kDecideThreads = 1024;
+#ifndef SCUC_ITER_MIN_BLOCKS
+#define SCUC_ITER_MIN_BLOCKS 1
+#endif
+constexpr int kIterMinBlocks = SCUC_ITER_MIN_BLOCKS;  // resident blocks per SM the iteration kernels ask for
+static_assert(kMaxRows <= 256, "a staged block's rows map to its threads");
 
-// block types of a partition entry
-constexpr int kStagedBlock = 0, kGroupListBlock = 1;
 
 // threads per row of a list row: about ept entries per thread, 4..32
 inline int group_size_for(int len, int ept = 16) {
@@ -42,39 +45,47 @@ inline int group_size_for(int len, int ept = 16) {
 }
 
 // tunable shape of a partition (plan_partition)
+#ifndef SCUC_DEFAULT_EPT
+#define SCUC_DEFAULT_EPT 16
+#endif
+#ifndef SCUC_DEFAULT_RUN
+#define SCUC_DEFAULT_RUN 32
+#endif
 struct PartShape {
-  int ept = 16;      // target entries per thread of list rows
-  int min_run = 32;  // shortest run of short rows that is staged in shared memory
+  int ept = SCUC_DEFAULT_EPT;      // target entries per thread of list rows
+  int min_run = SCUC_DEFAULT_RUN;  // shortest run of short rows that is staged in shared memory
 };
 
-// streamed long rows: tiles of kTile entries, kStages-deep shared-memory ring
-constexpr int kTile = 960;
-constexpr int kStages = 4;
-constexpr int kTileSlack = 8;                                   // alignment slack (entries)
-constexpr int kStageBytes = (kTile + kTileSlack) * 12;          // int index + FP64 value
-constexpr int kStreamSmem = 128 + kStages * kStageBytes;        // mbarriers + ring
-// the SpMV kernels keep static shared memory small so that the ring fits
-// under the 48 KB a launch may take without a function attribute
-static_assert(kStreamSmem + 1024 <= 48 * 1024, "streaming ring must fit the default shared memory");
-constexpr int kStagedSmem = kNnzCap * 12 + kBlock * 12;  // staging + row sums/ids
-constexpr long long kWaitBudgetCycles = 4000000000LL;           // ~2 s at 2 GHz
+constexpr int kChunk = 512;             // entries per chunk of a long row (one warp each)
+// staging (values + indices), row sums, row pointers of a staged run
+constexpr int kStagedSmem = kNnzCap * 12 + kBlock * 8 + (kMaxRows + 1) * 4;
 
-// Partition of a CSR matrix for the SpMV kernels.  Blocks [0, nstream) are
-// persistent CTAs that stream the long rows (long_rows[c], c = blockIdx,
-// blockIdx + nstream, ...) through shared memory with bulk copies; block
-// nstream + b runs desc[b] = {type, first, count, gsz}: staged blocks cover
-// rows [first, first + count) with gsz threads per row, list blocks cover
-// rows list[first .. first + count).  nblk = nstream + number of desc
-// entries (grid size and number of partial-sum slots).
+// Partition of a CSR matrix for the SpMV kernels (spmv.cuh).  Long rows
+// are cut into chunks; a chunk launch (nchunkblk blocks, one chunk per warp)
+// stores the chunk sums in cpart before the main launch.  The main launch
+// has nblk blocks:
+//  * list blocks [0, cls_blk[4]): class k = 0..3 (blocks [cls_blk[k],
+//    cls_blk[k+1])) reads rows with 32 >> k threads per row, kBlock / (32 >>
+//    k) consecutive entries of listx[cls_row[k] .. cls_row[k+1]) per block;
+//  * staged blocks [cls_blk[4], cls_blk[4] + nstaged): desc[b - cls_blk[4]];
+//  * long-row blocks: one thread per long row adds its chunk sums in order.
+// Block b writes its partial sums to slot[b] (nullptr: slot b).
 struct Partition {
   int nblk = 0;
-  int nstream = 0;
+  int cls_blk[5] = {0, 0, 0, 0, 0};
+  int cls_row[5] = {0, 0, 0, 0, 0};
+  int nstaged = 0;
   int nlong = 0;
-  int smem = kStagedSmem;        // dynamic shared memory of a launch
-  int4* desc = nullptr;
-  int* list = nullptr;
-  int* long_rows = nullptr;
-  int* err = nullptr;            // set to 1 when a bounded wait runs out
+  int nchunk = 0;
+  int nchunkblk = 0;
+  int smem = kStagedSmem;        // dynamic shared memory of a main launch
+  int4* listx = nullptr;         // list rows {row, first entry, end entry, 0}; row -1 pads a block
+  int4* desc = nullptr;          // staged runs {first row, first entry, end entry, (rows << 8) | gsz}
+  int2* chunks = nullptr;        // [nchunk] entry range [x, y) of each chunk, long row by long row
+  int* long_rows = nullptr;      // [nlong]
+  int* chunk_ptr = nullptr;      // [nlong + 1] first chunk of each long row
+  double* cpart = nullptr;       // [nchunk] chunk sums
+  int* slot = nullptr;           // [nblk] partial-sum slot of each block, or nullptr
 };
 
 // Device-resident solver state.  Parameters are written by the host before a

@@ -59,6 +59,7 @@ __device__ __forceinline__ double finite_mag(double lo, double hi) {
 struct RowEpi {
   const double *lo, *hi, *y;
   double acc[3];
+  __device__ void load(int) {}
   __device__ void row(int i, double a) {
     const double l = lo[i], h = hi[i];
     const double v = a - clamp_box(a, l, h);
@@ -75,6 +76,7 @@ struct RowEpi {
 struct ColEpi {
   const double *c, *xl, *xu, *x, *z;
   double acc[4];
+  __device__ void load(int) {}
   __device__ void row(int j, double g) {
     const double cj = c[j], zj = z[j];
     const double d = cj - g - zj;
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(const int* __restrict__ rp,
   extern __shared__ __align__(128) unsigned char smem[];
   RowEpi epi{lo, hi, y, {0.0, 0.0, 0.0}};
   spmv_block<double>(rp, col, val, x, part, smem, epi);
-  block_store<3>(epi.acc, partial, part.nblk);
+  block_store<3>(epi.acc, partial, part);
 }
 
 __global__ void __launch_bounds__(kBlock) k_kkt_cols(const int* __restrict__ rpt, const int* __restrict__ colt,
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_kkt_cols(const int* __restrict__ rpt
   extern __shared__ __align__(128) unsigned char smem[];
   ColEpi epi{c, xl, xu, x, z, {0.0, 0.0, 0.0, 0.0}};
   spmv_block<double>(rpt, colt, valt, y, part, smem, epi);
-  block_store<4>(epi.acc, partial, part.nblk);
+  block_store<4>(epi.acc, partial, part);
 }
 
 constexpr int kFinalThreads = 1024;
@@ -166,10 +168,11 @@ int Handle::kkt_noalloc(const double* xd, const double* yd, const double* zd, do
   cudaStream_t s = work;
   // every slot read by the final reduction is written by a block first, so
   // nothing left by an earlier call is read
+  double* scratch_t = scratch + 3 * (int64_t)pA.nblk;
+  if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, val, xd, pA);
   if (pA.nblk) k_kkt_rows<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, val, pA, xd, lo, hi, yd, scratch);
-  if (pT.nblk)
-    k_kkt_cols<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, valt, pT, yd, c, xl, xu, xd, zd,
-                                          scratch + 3 * (int64_t)pA.nblk);
+  if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, valt, yd, pT);
+  if (pT.nblk) k_kkt_cols<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, valt, pT, yd, c, xl, xu, xd, zd, scratch_t);
   k_kkt_final<<<1, kFinalThreads, 0, s>>>(scratch, pA.nblk, pT.nblk, out);
   SCUC_CUDA(cudaGetLastError());
   return leave();

@@ -45,22 +45,22 @@ static int grid_for(int64_t work, int block = kBlock) {
 }
 
 // Host plan of a partition (see Partition): rows with more than kGroupRowMax
-// nonzeros are streamed (long_rows) when allow_stream, else they go to
-// 32-thread list groups; rows of kShortMax+1..kGroupRowMax nonzeros get a
-// group of group_size_for(len, shape.ept) threads, kBlock/gsz rows of the
-// same group size per block; runs of at least shape.min_run consecutive
-// short rows are packed into staged blocks of <= kMaxRows rows / <= kNnzCap
-// nonzeros (threads per row = largest power of two with gsz * rows <=
-// kBlock), shorter runs go to 4-thread list groups.  Longest work first.
-void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_stream,
-                    std::vector<int4>* desc_out, std::vector<int>* list_out, std::vector<int>* long_out) {
-  std::vector<int> G[6];  // G[k]: rows with group size 1 << k (k = 2..5)
-  std::vector<int4> staged;
-  std::vector<int>& Lr = *long_out;
-  Lr.clear();
+// nonzeros are cut into chunks of kChunk entries when allow_long, else they
+// join the 32-thread list rows; rows of kShortMax+1..kGroupRowMax nonzeros
+// get a group of group_size_for(len, shape.ept) threads; runs of at least
+// shape.min_run consecutive short rows are packed into staged blocks of <=
+// kMaxRows rows / <= kNnzCap nonzeros (threads per row = largest power of
+// two with gsz * rows <= kBlock), shorter runs go to 4-thread list rows.
+// List classes run from 32 threads per row down to 4 (longest work first),
+// then the staged blocks, then the long rows.
+void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan) {
+  std::vector<int> G[4];  // G[k]: list rows with 32 >> k threads per row
+  *plan = PartPlan{};
+  plan->chunk_ptr.assign(1, 0);
+  auto cls = [](int gsz) { return gsz == 32 ? 0 : gsz == 16 ? 1 : gsz == 8 ? 2 : 3; };
   auto flush_run = [&](int a, int b) {  // short rows [a, b)
     if (b - a < shape.min_run) {
-      for (int r = a; r < b; r++) G[2].push_back(r);
+      for (int r = a; r < b; r++) G[3].push_back(r);
       return;
     }
     int r = a;
@@ -74,7 +74,7 @@ void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, b
       const int nr = r - start;
       int g = 1;
       while (g < 32 && g * 2 * nr <= kBlock) g *= 2;
-      staged.push_back(make_int4(kStagedBlock, start, nr, g));
+      plan->desc.push_back(make_int4(start, rp[start], rp[r], (nr << 8) | g));
     }
   };
   int run0 = 0;
@@ -83,65 +83,66 @@ void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, b
     if (len <= kShortMax) continue;
     flush_run(run0, r);
     run0 = r + 1;
-    if (len > kGroupRowMax && allow_stream) Lr.push_back(r);
-    else G[__builtin_ctz(group_size_for(len, shape.ept))].push_back(r);
+    if (len > kGroupRowMax && allow_long) {
+      plan->long_rows.push_back(r);
+      for (int e = rp[r]; e < rp[r + 1]; e += kChunk)
+        plan->chunks.push_back(make_int2(e, std::min(rp[r + 1], e + kChunk)));
+      plan->chunk_ptr.push_back((int)plan->chunks.size());
+    } else {
+      G[cls(len > kGroupRowMax ? 32 : group_size_for(len, shape.ept))].push_back(r);
+    }
   }
   flush_run(run0, m);
-  std::vector<int>& list = *list_out;
-  std::vector<int4>& desc = *desc_out;
-  list.clear();
-  desc.clear();
-  for (int k = 5; k >= 2; k--) {
-    const int gsz = 1 << k, per = kBlock / gsz;
-    const std::vector<int>& R = G[k];
-    for (size_t i = 0; i < R.size(); i += per) {
-      const int cnt = (int)std::min<size_t>(per, R.size() - i);
-      desc.push_back(make_int4(kGroupListBlock, (int)list.size(), cnt, gsz));
-      for (int q = 0; q < cnt; q++) list.push_back(R[i + q]);
-    }
-    if (k == 3) desc.insert(desc.end(), staged.begin(), staged.end());
+  for (int k = 0; k < 4; k++) {
+    plan->cls_row[k] = (int)plan->listx.size();
+    for (int r : G[k]) plan->listx.push_back(make_int4(r, rp[r], rp[r + 1], 0));
+    plan->cls_blk[k + 1] = plan->cls_blk[k] + (int)((G[k].size() + (kBlock >> (5 - k)) - 1) / (kBlock >> (5 - k)));
   }
+  plan->cls_row[4] = (int)plan->listx.size();
 }
 
 // device copies of a planned partition (freed by free_partition)
-int upload_partition(const std::vector<int4>& desc, const std::vector<int>& list, const std::vector<int>& Lr,
-                     Partition* P) {
-  P->nlong = (int)Lr.size();
-  P->nstream = std::min<int>(P->nlong, 2 * 148);  // persistent streaming CTAs, two per SM
-  P->smem = P->nlong ? std::max(kStagedSmem, kStreamSmem) : kStagedSmem;
-  P->nblk = P->nstream + (int)desc.size();
-  SCUC_TRY(dalloc(&P->desc, desc.size()));
-  SCUC_TRY(dalloc(&P->list, list.size()));
-  SCUC_TRY(dalloc(&P->long_rows, Lr.size()));
-  SCUC_TRY(dalloc(&P->err, 1));
-  SCUC_CUDA(cudaMemset(P->err, 0, sizeof(int)));
-  if (!Lr.empty())
-    SCUC_CUDA(cudaMemcpy(P->long_rows, Lr.data(), Lr.size() * sizeof(int), cudaMemcpyHostToDevice));
-  if (!desc.empty())
-    SCUC_CUDA(cudaMemcpy(P->desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  if (!list.empty())
-    SCUC_CUDA(cudaMemcpy(P->list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+int upload_partition(const PartPlan& plan, Partition* P) {
+  *P = Partition{};
+  for (int k = 0; k < 5; k++) {
+    P->cls_blk[k] = plan.cls_blk[k];
+    P->cls_row[k] = plan.cls_row[k];
+  }
+  P->nstaged = (int)plan.desc.size();
+  P->nlong = (int)plan.long_rows.size();
+  P->nchunk = (int)plan.chunks.size();
+  P->nchunkblk = (P->nchunk + kBlock / 32 - 1) / (kBlock / 32);
+  P->nblk = plan.cls_blk[4] + P->nstaged + (P->nlong + kBlock - 1) / kBlock;
+  SCUC_TRY(dalloc(&P->listx, plan.listx.size()));
+  SCUC_TRY(dalloc(&P->desc, plan.desc.size()));
+  SCUC_TRY(dalloc(&P->chunks, plan.chunks.size()));
+  SCUC_TRY(dalloc(&P->long_rows, plan.long_rows.size()));
+  SCUC_TRY(dalloc(&P->chunk_ptr, plan.long_rows.size() + 1));
+  SCUC_TRY(dalloc(&P->cpart, plan.chunks.size()));
+  if (!plan.slot.empty()) SCUC_TRY(dalloc(&P->slot, plan.slot.size()));
+  auto up = [](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  SCUC_CUDA(up(P->listx, plan.listx.data(), plan.listx.size() * sizeof(int4)));
+  SCUC_CUDA(up(P->desc, plan.desc.data(), plan.desc.size() * sizeof(int4)));
+  SCUC_CUDA(up(P->chunks, plan.chunks.data(), plan.chunks.size() * sizeof(int2)));
+  SCUC_CUDA(up(P->long_rows, plan.long_rows.data(), plan.long_rows.size() * sizeof(int)));
+  SCUC_CUDA(up(P->chunk_ptr, plan.chunk_ptr.data(), plan.chunk_ptr.size() * sizeof(int)));
+  if (P->slot) SCUC_CUDA(up(P->slot, plan.slot.data(), plan.slot.size() * sizeof(int)));
   return SCUC_OK;
 }
 
 void free_partition(Partition* P) {
-  for (void* q : {(void*)P->desc, (void*)P->list, (void*)P->long_rows, (void*)P->err})
+  for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
+                  (void*)P->cpart, (void*)P->slot})
     if (q) cudaFree(q);
-  P->desc = nullptr;
-  P->list = nullptr;
-  P->long_rows = nullptr;
-  P->err = nullptr;
+  *P = Partition{};
 }
 
-int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
-                    std::vector<int>* list_out) {
-  std::vector<int4> desc;
-  std::vector<int> list, Lr;
-  plan_partition(rp, m, PartShape{}, true, &desc, &list, &Lr);
-  SCUC_TRY(upload_partition(desc, list, Lr, P));
-  if (desc_out) *desc_out = desc;
-  if (list_out) *list_out = list;
-  return SCUC_OK;
+int build_partition(const std::vector<int>& rp, int m, Partition* P) {
+  PartPlan plan;
+  plan_partition(rp, m, PartShape{}, true, &plan);
+  return upload_partition(plan, P);
 }
 
 // exclusive scan of n ints into out[0..n] (out[n] = total), recursive
@@ -367,10 +368,12 @@ int Handle::setup_device(const std::vector<int>& rp32) {
   if (nnz) k_gather_t<<<grid_for(nnz), kBlock, 0, s>>>(permt, nnz, val, valt);
   SCUC_CUDA(cudaGetLastError());
 
-  SCUC_TRY(build_partition(rp32, m, &pA, nullptr, nullptr));
-  SCUC_TRY(build_partition(rpt_h, n, &pT, nullptr, nullptr));
+  SCUC_TRY(build_partition(rp32, m, &pA));
+  SCUC_TRY(build_partition(rpt_h, n, &pT));
   for (Partition* P : {&pA, &pT})
-    for (void* q : {(void*)P->desc, (void*)P->list, (void*)P->long_rows, (void*)P->err}) allocs.push_back(q);
+    for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
+                    (void*)P->cpart, (void*)P->slot})
+      if (q) allocs.push_back(q);
 
   // scaled data and iterates
   SCUC_TRY(alloc(&vs, nnz));
@@ -392,7 +395,10 @@ int Handle::setup_device(const std::vector<int>& rp32) {
   SCUC_TRY(alloc(&ybar, m));
   SCUC_TRY(alloc(&xt32, n));
   SCUC_TRY(alloc(&y32, m));
-  SCUC_TRY(alloc(&partP, 4 * (size_t)pT.nblk));
+  epi_gx = (int)std::max<int64_t>(1, std::min<int64_t>(148 * 8, ((int64_t)n + kBlock - 1) / kBlock));
+  SCUC_TRY(alloc(&gsum, n));
+  SCUC_TRY(alloc(&gsum32, n));
+  SCUC_TRY(alloc(&partP, 4 * (size_t)epi_gx));
   SCUC_TRY(alloc(&partD, 2 * (size_t)pA.nblk));
   SCUC_TRY(alloc(&partRA, 3 * (size_t)std::max(pA.nblk, kNormBlocks)));
   SCUC_TRY(alloc(&dychk, m));
@@ -434,6 +440,9 @@ DevLP Handle::dev() const {
   L.qchk = uv; L.dychk = dychk;  // uv: power-method scratch, free during iterations
   L.coef = coef; L.coef_w = coef;
   L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
+  L.gsum = gsum;
+  L.gsum32 = gsum32;
+  L.epi_gx = epi_gx;
   L.pA = pA; L.pT = pT;
   L.ctrl = ctrl; L.log = log_d;
   L.nlp = 1;
@@ -497,11 +506,13 @@ int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters
   PowerCtrl P{};
   for (int it = 0; it < p.power_max_iter; it += 16) {
     for (int j = 0; j < 16; j++) {
+      if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA);
       if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
+      if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, uv, pT);
       if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
       k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);
       k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, pctrl);
-      nlaunch += 2 + (pA.nblk ? 1 : 0) + (pT.nblk ? 1 : 0);
+      nlaunch += 2 + (pA.nblk ? 1 : 0) + (pT.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0) + (pT.nchunk ? 1 : 0);
     }
     SCUC_CUDA(cudaGetLastError());
     SCUC_CUDA(cudaMemcpyAsync(&P, pctrl, sizeof(PowerCtrl), cudaMemcpyDeviceToHost, s));
@@ -532,24 +543,27 @@ int Handle::launch_period(int check_every, bool profile) {
   for (int j = 0; j < check_every; j++) {
     const bool chk = (j == check_every - 1);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 0], s));
-    if (pT.nblk) {
-      if (chk) k_primal<true><<<pT.nblk, kBlock, pT.smem, s>>>(L, j);
-      else k_primal<false><<<pT.nblk, kBlock, pT.smem, s>>>(L, j);
-    }
+    if (pT.nchunk) k_chunks_iter<kChunksPrimal><<<pT.nchunkblk, kBlock, 0, s>>>(L);
+    if (pT.nblk) k_primal_sum<<<pT.nblk, kBlock, pT.smem, s>>>(L);
+    if (chk) k_primal_epi<true><<<epi_gx, kBlock, 0, s>>>(L, j);
+    else k_primal_epi<false><<<epi_gx, kBlock, 0, s>>>(L, j);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 1], s));
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 2], s));
+    if (pA.nchunk) k_chunks_iter<kChunksDual><<<pA.nchunkblk, kBlock, 0, s>>>(L);
     if (pA.nblk) {
       if (chk) k_dual<true><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
       else k_dual<false><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
     }
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 3], s));
   }
+  if (pA.nchunk) k_chunks_iter<kChunksResPrimal><<<pA.nchunkblk, kBlock, 0, s>>>(L);
   if (pA.nblk) k_res_primal<<<pA.nblk, kBlock, pA.smem, s>>>(L);
+  if (pT.nchunk) k_chunks_iter<kChunksResDual><<<pT.nchunkblk, kBlock, 0, s>>>(L);
   if (pT.nblk) k_res_dual<<<pT.nblk, kBlock, pT.smem, s>>>(L);
   k_decide<<<1, kDecideThreads, 0, s>>>(L, check_every);
   SCUC_CUDA(cudaGetLastError());
-  nlaunch += 2 + (int64_t)check_every * ((pT.nblk ? 1 : 0) + (pA.nblk ? 1 : 0)) + (pA.nblk ? 1 : 0) +
-             (pT.nblk ? 1 : 0);
+  const int la = (pA.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0), lt = (pT.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0);
+  nlaunch += 2 + (int64_t)check_every * (la + lt + 1) + la + lt;
   return SCUC_OK;
 }
 
@@ -728,7 +742,6 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   }
   last_nlog = std::min(C.nlog, log_cap);
   SCUC_CUDA(cudaStreamSynchronize(s));
-  SCUC_TRY(device_error());
   if (info) {
     memset(info, 0, sizeof(*info));
     info->status = timed_out && !C.done ? SCUC_ST_TIME_LIMIT : (C.status < 0 ? SCUC_ST_ITER_LIMIT : C.status);
@@ -751,33 +764,17 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   return leave();
 }
 
-// a bounded device-side wait ran out in a streaming SpMV
-int Handle::device_error() {
-  int e[2] = {0, 0};
-  SCUC_CUDA(cudaMemcpyAsync(&e[0], pA.err, sizeof(int), cudaMemcpyDeviceToHost, work));
-  SCUC_CUDA(cudaMemcpyAsync(&e[1], pT.err, sizeof(int), cudaMemcpyDeviceToHost, work));
-  SCUC_CUDA(cudaStreamSynchronize(work));
-  if (e[0] || e[1]) {
-    SCUC_CUDA(cudaMemsetAsync(pA.err, 0, sizeof(int), work));
-    SCUC_CUDA(cudaMemsetAsync(pT.err, 0, sizeof(int), work));
-    SCUC_CUDA(cudaStreamSynchronize(work));
-    set_error("a device-side wait for a bulk copy ran out of its time budget");
-    return SCUC_E_DEVICE_TIMEOUT;
-  }
-  return SCUC_OK;
-}
-
 int Handle::matvec(int transpose, const double* in, double* out) {
   SCUC_TRY(enter());
   cudaStream_t s = work;
-  if (!transpose) {
-    if (pA.nblk) k_spmv_plain<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, val, in, pA, out);
-  } else {
-    if (pT.nblk) k_spmv_plain<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, valt, in, pT, out);
-  }
+  const Partition& P = transpose ? pT : pA;
+  const int* r = transpose ? rpt : rp;
+  const int* c = transpose ? colt : col;
+  const double* v = transpose ? valt : val;
+  if (P.nchunk) k_chunk_sums<double><<<P.nchunkblk, kBlock, 0, s>>>(c, v, in, P);
+  if (P.nblk) k_spmv_plain<<<P.nblk, kBlock, P.smem, s>>>(r, c, v, in, P, out);
   SCUC_CUDA(cudaGetLastError());
   SCUC_CUDA(cudaStreamSynchronize(s));
-  SCUC_TRY(device_error());
   return leave();
 }
 

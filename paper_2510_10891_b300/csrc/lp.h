@@ -8,12 +8,17 @@ namespace scuc {
 
 struct DevLP;  // device view of a handle (lp_kernels.cuh)
 
-int build_partition(const std::vector<int>& rp, int m, Partition* P, std::vector<int4>* desc_out,
-                    std::vector<int>* list_out);
-void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_stream,
-                    std::vector<int4>* desc_out, std::vector<int>* list_out, std::vector<int>* long_out);
-int upload_partition(const std::vector<int4>& desc, const std::vector<int>& list, const std::vector<int>& Lr,
-                     Partition* P);
+// host plan of a Partition
+struct PartPlan {
+  std::vector<int4> listx, desc;
+  std::vector<int> long_rows, chunk_ptr, slot;
+  std::vector<int2> chunks;
+  int cls_blk[5] = {0, 0, 0, 0, 0};
+  int cls_row[5] = {0, 0, 0, 0, 0};
+};
+int build_partition(const std::vector<int>& rp, int m, Partition* P);
+void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan);
+int upload_partition(const PartPlan& plan, Partition* P);
 void free_partition(Partition* P);
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s);
 int dev_alloc_bytes(void** p, size_t bytes);
@@ -41,6 +46,9 @@ struct Handle {
   double* dychk = nullptr;
   double *qv = nullptr, *uv = nullptr, *wv = nullptr;
   double *partP = nullptr, *partD = nullptr, *partRA = nullptr, *partRT = nullptr;
+  double* gsum = nullptr;  // A^T y of the primal step (FP64 phases)
+  float* gsum32 = nullptr;  // ... (FP32 phases)
+  int epi_gx = 1;          // blocks of the primal epilogue
   Ctrl* ctrl = nullptr;
   Ctrl* ctrl_h = nullptr;
   PowerCtrl* pctrl = nullptr;
@@ -75,7 +83,6 @@ struct Handle {
             double* yo, double* zo, scuc_solve_info* info, double reject_kkt = 0.0);
   int* pt_flag = nullptr;  // index checks of scuc_ws_assemble / scuc_ws_targets
   int matvec(int transpose, const double* in, double* out);
-  int device_error();
   int kkt_noalloc(const double* x, const double* y, const double* z, double* out);
   int fix_and_propagate(const scuc_map& map, const uint8_t* is_int, const double* x, const scuc_fix_params& p,
                         int8_t* fix_out, Handle** reduced, int32_t* col_map, int32_t* row_map, scuc_fix_info* info);

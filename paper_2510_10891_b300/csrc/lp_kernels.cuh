@@ -20,8 +20,11 @@ struct DevLP {
   double *qchk, *dychk;        // A x_t and y_bar - y at a check iteration
   const double* coef;          // Halpern weights {1/(k+2), (k+1)/(k+2)} per period slot
   double* coef_w;              // same buffer, written by the decide kernel
+  double* gsum;                // A^T y of the primal step in FP64 phases
+  float* gsum32;               // ... in FP32 phases (LPs of a batch may be in different phases)
   // partial sums
   double *partP, *partD, *partRA, *partRT;
+  int epi_gx;                  // blocks per LP of the primal epilogue (partP: epi_gx * nlp slots)
   Partition pA, pT;
   Ctrl* ctrl;
   scuc_check_log* log;
@@ -55,6 +58,32 @@ __device__ __forceinline__ double clampd(double v, double l, double u) {
 namespace {
 
 // ---------------------------------------------------------------------------
+// chunk launches of the long rows (one LP; batches have no long rows)
+// ---------------------------------------------------------------------------
+constexpr int kChunksPrimal = 0, kChunksDual = 1, kChunksResPrimal = 2, kChunksResDual = 3;
+
+// Chunk sums for the next main launch: A^T y (primal step) or A x_t (dual
+// step) in the precision of the current phase, A x_bar / A^T y_bar (checks)
+// in FP64.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_chunks_iter(DevLP L) {
+  const Ctrl* ctrl = L.ctrl;
+  if (ctrl->done) return;
+  const bool fp64 = ctrl->fp64_phase != 0;
+  if (MODE == kChunksPrimal) {
+    if (fp64) chunk_warp<double>(L.colt, L.vst, L.y, L.pT);
+    else chunk_warp<float>(L.colt, L.vst32, L.y32, L.pT);
+  } else if (MODE == kChunksDual) {
+    if (fp64) chunk_warp<double>(L.col, L.vs, L.xt, L.pA);
+    else chunk_warp<float>(L.col, L.vs32, L.xt32, L.pA);
+  } else if (MODE == kChunksResPrimal) {
+    chunk_warp<double>(L.col, L.vs, L.xbar, L.pA);
+  } else {
+    chunk_warp<double>(L.colt, L.vst, L.ybar, L.pT);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // primal step over A^T y: x_bar = Pi_K(x + sigma (g - c)), reflection, Halpern
 // ---------------------------------------------------------------------------
 template <bool CHECK>
@@ -63,51 +92,79 @@ struct PrimalEpi {
   double sigma, wa, wb;
   bool fp64;
   double acc[4];
+  double xj, cj, xlj, xuj, x0j;  // the column's operands, loaded before its sum
+  __device__ void load(int j) {
+    xj = L.x[j];
+    cj = L.c[j];
+    xlj = L.xl[j];
+    xuj = L.xu[j];
+    x0j = L.x0[j];
+  }
   __device__ void row(int j, double g) {
-    const double xj = L.x[j];
-    const double v = xj + sigma * (g - L.c[j]);
-    const double xb = clampd(v, L.xl[j], L.xu[j]);
+    const double v = xj + sigma * (g - cj);
+    const double xb = clampd(v, xlj, xuj);
     const double xt = 2.0 * xb - xj;
-    const double x0j = L.x0[j];
     const double xn = wa * x0j + wb * xt;
     L.x[j] = xn;
     if (fp64) L.xt[j] = xt;
     else L.xt32[j] = (float)xt;
     if (CHECK) {
       double zb = (xb - v) / sigma;
-      if (zb > 0.0 && !isfinite(L.xl[j])) zb = 0.0;
-      if (zb < 0.0 && !isfinite(L.xu[j])) zb = 0.0;
+      if (zb > 0.0 && !isfinite(xlj)) zb = 0.0;
+      if (zb < 0.0 && !isfinite(xuj)) zb = 0.0;
       L.xbar[j] = xb;
       L.zbar[j] = zb;
       acc[0] += (xb - xj) * (xb - xj);
       acc[1] += (xn - x0j) * (xn - x0j);
-      acc[2] += L.c[j] * xb;
-      if (zb > 0.0) acc[3] += L.xl[j] * zb;
-      else if (zb < 0.0) acc[3] += L.xu[j] * zb;
+      acc[2] += cj * xb;
+      if (zb > 0.0) acc[3] += xlj * zb;
+      else if (zb < 0.0) acc[3] += xuj * zb;
     }
   }
 };
 
-template <bool CHECK>
-__global__ void __launch_bounds__(kBlock) k_primal(DevLP L, int j) {
+// g = A^T y (the primal step's product), stored for the elementwise epilogue
+template <typename VT>
+struct GStoreEpi {
+  VT* g;
+  __device__ void load(int) {}
+  __device__ void row(int r, VT a) { g[r] = a; }
+};
+
+__global__ void __launch_bounds__(kBlock) k_primal_sum(DevLP L) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int lp = L.blkT ? L.blkT[blockIdx.x] : 0;
+  const BlockPlan bp = spmv_plan(L.pT);  // issued together with the control loads
+  const Ctrl* ctrl = L.ctrl + (L.blkT ? L.blkT[blockIdx.x] : 0);
+  if (ctrl->done) return;
+  if (ctrl->fp64_phase) {
+    GStoreEpi<double> e{L.gsum};
+    spmv_run<double, GStoreEpi<double>, true>(bp, L.rpt, L.colt, L.vst, L.y, L.pT, smem, e);
+  } else {
+    GStoreEpi<float> e{L.gsum32};
+    spmv_run<float, GStoreEpi<float>, true>(bp, L.rpt, L.colt, L.vst32, L.y32, L.pT, smem, e);
+  }
+}
+
+// Primal step, elementwise over the columns of LP blockIdx.y (blockIdx.x of
+// epi_gx blocks strides over them): contiguous loads, full warps for the
+// FP64 arithmetic.
+template <bool CHECK>
+__global__ void __launch_bounds__(kBlock) k_primal_epi(DevLP L, int j) {
+  const int lp = blockIdx.y;
   const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
   const double* cf = L.coef + (size_t)lp * L.coef_stride;
   PrimalEpi<CHECK> epi{L, ctrl->sigma, cf[2 * j], cf[2 * j + 1], ctrl->fp64_phase != 0,
-                       {0.0, 0.0, 0.0, 0.0}};
-  if (epi.fp64) {
-    spmv_block<double>(L.rpt, L.colt, L.vst, L.y, L.pT, smem, epi);
-  } else {
-    // FP32 matvec, FP32 accumulation; epilogue in FP64
-    struct Wrap {
-      PrimalEpi<CHECK>& e;
-      __device__ void row(int r, float a) { e.row(r, (double)a); }
-    } w{epi};
-    spmv_block<float>(L.rpt, L.colt, L.vst32, L.y32, L.pT, smem, w);
+                       {0.0, 0.0, 0.0, 0.0}, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const float* g32 = L.gsum32;
+  int c0, c1;
+  lp_range(L.col0, lp, L.n, c0, c1);
+  const int stride = gridDim.x * kBlock;
+  for (int c = c0 + (int)blockIdx.x * kBlock + (int)threadIdx.x; c < c1; c += stride) {
+    epi.load(c);
+    epi.row(c, epi.fp64 ? L.gsum[c] : (double)g32[c]);
   }
-  if (CHECK) block_store<4>(epi.acc, L.partP, L.pT.nblk);
+  if (CHECK) block_store_slot<4>(epi.acc, L.partP, L.epi_gx * L.nlp, lp * L.epi_gx + (int)blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -120,11 +177,16 @@ struct DualEpi {
   double s, wa, wb;
   bool fp64;
   double acc[2];
+  double yi, loi, hii, y0i;  // the row's operands, loaded before its sum
+  __device__ void load(int i) {
+    yi = L.y[i];
+    loi = L.lo[i];
+    hii = L.hi[i];
+    y0i = L.y0[i];
+  }
   __device__ void row(int i, double q) {
-    const double yi = L.y[i];
     const double r = yi - s * q;
-    const double yb = fmax(r + s * L.lo[i], 0.0) + fmin(r + s * L.hi[i], 0.0);
-    const double y0i = L.y0[i];
+    const double yb = fmax(r + s * loi, 0.0) + fmin(r + s * hii, 0.0);
     const double yn = wa * y0i + wb * (2.0 * yb - yi);
     L.y[i] = yn;
     if (!fp64) L.y32[i] = (float)yn;
@@ -139,24 +201,27 @@ struct DualEpi {
 };
 
 template <bool CHECK>
-__global__ void __launch_bounds__(kBlock) k_dual(DevLP L, int j) {
+__global__ void __launch_bounds__(kBlock, kIterMinBlocks) k_dual(DevLP L, int j) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const BlockPlan bp = spmv_plan(L.pA);  // issued together with the control loads
   const int lp = L.blkA ? L.blkA[blockIdx.x] : 0;
   const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
   const double* cf = L.coef + (size_t)lp * L.coef_stride;
   DualEpi<CHECK> epi{L, ctrl->s_step, cf[2 * j], cf[2 * j + 1], ctrl->fp64_phase != 0,
-                     {0.0, 0.0}};
+                     {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
+  if (bp.er >= 0) epi.load(bp.er);
   if (epi.fp64) {
-    spmv_block<double>(L.rp, L.col, L.vs, L.xt, L.pA, smem, epi);
+    spmv_run<double>(bp, L.rp, L.col, L.vs, L.xt, L.pA, smem, epi);
   } else {
     struct Wrap {
       DualEpi<CHECK>& e;
+      __device__ void load(int r) { e.load(r); }
       __device__ void row(int r, float a) { e.row(r, (double)a); }
     } w{epi};
-    spmv_block<float>(L.rp, L.col, L.vs32, L.xt32, L.pA, smem, w);
+    spmv_run<float>(bp, L.rp, L.col, L.vs32, L.xt32, L.pA, smem, w);
   }
-  if (CHECK) block_store<2>(epi.acc, L.partD, L.pA.nblk);
+  if (CHECK) block_store<2>(epi.acc, L.partD, L.pA);
 }
 
 // ---------------------------------------------------------------------------
@@ -166,6 +231,7 @@ struct ResPrimalEpi {  // A x_bar: primal violation (unscaled), y-part of dobj, 
   const DevLP& L;
   double beta;
   double acc[3];
+  __device__ void load(int) {}
   __device__ void row(int i, double a) {
     const double lo = L.lo[i], hi = L.hi[i];
     const double viol = (a - clampd(a, lo, hi)) * beta / L.Dr[i];
@@ -183,13 +249,14 @@ __global__ void __launch_bounds__(kBlock) k_res_primal(DevLP L) {
   if (ctrl->done) return;
   ResPrimalEpi epi{L, ctrl->beta, {0.0, 0.0, 0.0}};
   spmv_block<double>(L.rp, L.col, L.vs, L.xbar, L.pA, smem, epi);
-  block_store<3>(epi.acc, L.partRA, L.pA.nblk);
+  block_store<3>(epi.acc, L.partRA, L.pA);
 }
 
 struct ResDualEpi {  // A^T y_bar: dual residual (unscaled)
   const DevLP& L;
   double gamma;
   double acc[1];
+  __device__ void load(int) {}
   __device__ void row(int j, double g) {
     const double d = gamma * (L.c[j] - g - L.zbar[j]) / L.Dc[j];
     acc[0] += d * d;
@@ -202,7 +269,7 @@ __global__ void __launch_bounds__(kBlock) k_res_dual(DevLP L) {
   if (ctrl->done) return;
   ResDualEpi epi{L, ctrl->gamma, {0.0}};
   spmv_block<double>(L.rpt, L.colt, L.vst, L.ybar, L.pT, smem, epi);
-  block_store<1>(epi.acc, L.partRT, L.pT.nblk);
+  block_store<1>(epi.acc, L.partRT, L.pT);
 }
 
 // fixed-order sum of one partial array by a single block
@@ -232,15 +299,15 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   const int lp = blockIdx.x;
   Ctrl* C = L.ctrl + lp;
   if (C->done) return;
-  const int nA = L.pA.nblk, nT = L.pT.nblk;
+  const int nA = L.pA.nblk, nT = L.pT.nblk, nP = L.epi_gx * L.nlp, p0 = lp * L.epi_gx;
   int a0, a1, t0, t1;
   lp_range(L.ablk0, lp, nA, a0, a1);
   lp_range(L.tblk0, lp, nT, t0, t1);
   const int ca = a1 - a0, ct = t1 - t0;
-  const double Sx = decide_sum(L.partP + 0 * nT + t0, ct);
-  const double Sxa = decide_sum(L.partP + 1 * nT + t0, ct);
-  const double pobj_s = decide_sum(L.partP + 2 * nT + t0, ct);
-  const double dz = decide_sum(L.partP + 3 * nT + t0, ct);
+  const double Sx = decide_sum(L.partP + 0 * nP + p0, L.epi_gx);
+  const double Sxa = decide_sum(L.partP + 1 * nP + p0, L.epi_gx);
+  const double pobj_s = decide_sum(L.partP + 2 * nP + p0, L.epi_gx);
+  const double dz = decide_sum(L.partP + 3 * nP + p0, L.epi_gx);
   const double Sy = decide_sum(L.partD + 0 * nA + a0, ca);
   const double Sya = decide_sum(L.partD + 1 * nA + a0, ca);
   const double viol2 = decide_sum(L.partRA + 0 * nA + a0, ca);

@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_power_seed_norm(const double
 struct StoreEpi {  // out[r] = acc, and sum of squares
   double* out;
   double acc[1];
+  __device__ void load(int) {}
   __device__ void row(int r, double a) {
     out[r] = a;
     acc[0] += a * a;
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_power_spmv(const int* __restrict__ r
   if (P->done) return;
   StoreEpi epi{out, {0.0}};
   spmv_block<double>(rp, col, val, in, part, smem, epi);
-  block_store<1>(epi.acc, psum, part.nblk);
+  block_store<1>(epi.acc, psum, part);
 }
 
 __global__ void __launch_bounds__(kDecideThreads) k_power_decide(const double* pu, int nA, const double* pw,
@@ -384,6 +385,7 @@ __global__ void k_finalize(DevLP L, double* __restrict__ xo, double* __restrict_
 // unscaled product (matvec entry point)
 struct PlainEpi {
   double* out;
+  __device__ void load(int) {}
   __device__ void row(int r, double a) { out[r] = a; }
 };
 
