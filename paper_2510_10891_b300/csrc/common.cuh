@@ -30,10 +30,9 @@ constexpr int kMaxRows = 256;      // rows per staged block (<= kBlock: one epil
 constexpr int kShortMax = 32;        // short rows: <= this many nonzeros
 constexpr int kGroupRowMax = 4096;   // list rows up to this many; longer rows get a block
 constexpr int kDecideThreads = 1024;
-#ifndef SCUC_ITER_MIN_BLOCKS
-#define SCUC_ITER_MIN_BLOCKS 1
-#endif
-constexpr int kIterMinBlocks = SCUC_ITER_MIN_BLOCKS;  // resident blocks per SM the iteration kernels ask for
+// resident blocks per SM the dual-step kernel asks for (register cap 40:
+// measured faster than 64 registers at half the occupancy)
+constexpr int kDualMinBlocks = 6;
 static_assert(kMaxRows <= 256, "a staged block's rows map to its threads");
 
 

@@ -133,7 +133,7 @@ struct GStoreEpi {
 
 __global__ void __launch_bounds__(kBlock) k_primal_sum(DevLP L) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const BlockPlan bp = spmv_plan(L.pT);  // issued together with the control loads
+  const BlockPlan bp = spmv_plan<false>(L.pT);  // issued together with the control loads
   const Ctrl* ctrl = L.ctrl + (L.blkT ? L.blkT[blockIdx.x] : 0);
   if (ctrl->done) return;
   if (ctrl->fp64_phase) {
@@ -201,9 +201,9 @@ struct DualEpi {
 };
 
 template <bool CHECK>
-__global__ void __launch_bounds__(kBlock, kIterMinBlocks) k_dual(DevLP L, int j) {
+__global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_dual(DevLP L, int j) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const BlockPlan bp = spmv_plan(L.pA);  // issued together with the control loads
+  const BlockPlan bp = spmv_plan<true>(L.pA);  // issued together with the control loads
   const int lp = L.blkA ? L.blkA[blockIdx.x] : 0;
   const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
