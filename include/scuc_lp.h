@@ -94,9 +94,12 @@ typedef struct {
   double restart_suff;    /* 0.2 */
   double restart_nec;     /* 0.8 */
   double restart_long;    /* 0.2 */
-  double polish_factor;   /* 10: MIXED switches to FP64 at kkt <= factor*tol */
+  double polish_factor;   /* 1: MIXED switches to FP64 matvecs at kkt <=
+                             factor*tol (1: only on a stall -- FP32 matvecs
+                             reach 1e-4 on the 13k-bus LP in as many
+                             iterations as FP64; 10 polishes the last decade) */
   int32_t polish_stall;   /* 20: ... or after this many checks without a
-                             10 % improvement of the best KKT in FP32       */
+                             10% improvement of the best KKT measure       */
   int32_t use_graph;      /* 1: replay each check period as a CUDA graph    */
   int32_t profile;        /* 1: time the two SpMV kernels with CUDA events  */
   int32_t device_ptrs;    /* 1: x0/y0 and x/y/z_out of scuc_lp_solve are

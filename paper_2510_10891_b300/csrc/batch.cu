@@ -252,18 +252,18 @@ int tune_partition(Batch& B, bool transpose, const std::vector<std::vector<int>>
   return SCUC_OK;
 }
 
-int launch_batch_period(Batch& B, int check_every, int ga) {
-  cudaStream_t s = B.s;
+// One period over all LPs (runtime precision: each LP's own phase).
+int launch_batch_period(Batch& B, cudaStream_t s, int check_every, int ga) {
   const DevLP L = B.dev();
   k_anchor<<<dim3(ga, B.nlp), kBlock, 0, s>>>(L);
   for (int j = 0; j < check_every; j++) {
     const bool chk = (j == check_every - 1);
-    if (B.pT.nblk) k_primal_sum<<<B.pT.nblk, kBlock, B.pT.smem, s>>>(L);
-    if (chk) k_primal_epi<true><<<dim3(B.epi_gx, B.nlp), kBlock, 0, s>>>(L, j);
-    else k_primal_epi<false><<<dim3(B.epi_gx, B.nlp), kBlock, 0, s>>>(L, j);
+    if (B.pT.nblk) k_primal_sum<kPrecRuntime><<<B.pT.nblk, kBlock, B.pT.smem, s>>>(L);
+    if (chk) k_primal_epi<true, kPrecRuntime><<<dim3(B.epi_gx, B.nlp), kBlock, 0, s>>>(L, j);
+    else k_primal_epi<false, kPrecRuntime><<<dim3(B.epi_gx, B.nlp), kBlock, 0, s>>>(L, j);
     if (B.pA.nblk) {
-      if (chk) k_dual<true><<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L, j);
-      else k_dual<false><<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L, j);
+      if (chk) k_dual<true, kPrecRuntime><<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L, j);
+      else k_dual<false, kPrecRuntime><<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L, j);
     }
   }
   if (B.pA.nblk) k_res_primal<<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L);
@@ -276,6 +276,35 @@ int launch_batch_period(Batch& B, int check_every, int ga) {
 int64_t period_launches(const Batch& B, int ce) {
   return 2 + (int64_t)ce * ((B.pT.nblk ? 1 : 0) + (B.pA.nblk ? 1 : 0) + 1) + (B.pA.nblk ? 1 : 0) +
          (B.pT.nblk ? 1 : 0);
+}
+
+// The batch's iteration as one graph: WHILE (some LP runs) { period; conditions }.
+int build_batch_graph(Batch& B, int check_every, int ga) {
+  cudaGraph_t g = nullptr;
+  SCUC_CUDA(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+  } guard{g};
+  cudaGraphConditionalHandle hloop;
+  SCUC_CUDA(cudaGraphConditionalHandleCreate(&hloop, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hloop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  SCUC_CUDA(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp));
+  SCUC_CUDA(cudaStreamBeginCaptureToGraph(B.s, wp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+  int rc = launch_batch_period(B, B.s, check_every, ga);
+  if (rc == SCUC_OK) k_loop_cond<<<1, kDecideThreads, 0, B.s>>>(B.dev(), hloop, hloop, 0);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(B.s, &out);
+  SCUC_TRY(rc);
+  SCUC_CUDA(e);
+  SCUC_CUDA(cudaGraphInstantiate(&B.graph, g, 0));
+  return SCUC_OK;
 }
 
 }  // namespace
@@ -479,59 +508,66 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
       coef_h[(size_t)b * B.coef_stride + 2 * j + 1] = (double)(j + 1) / (double)(j + 2);
     }
   }
-  SCUC_CUDA(cudaMemcpyAsync(B.ctrl, C.data(), nlp * sizeof(Ctrl), cudaMemcpyHostToDevice, s));
   SCUC_CUDA(cudaMemcpyAsync(B.coef, coef_h.data(), coef_h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   int maxdim = 1;
   for (int b = 0; b < nlp; b++) maxdim = std::max(maxdim, std::max(H[b]->m, H[b]->n));
   const int ga = std::max(1, std::min(64, (maxdim + kBlock - 1) / kBlock));
   const DevLP L = B.dev();
-  k_init_iterates<<<dim3(ga, nlp), kBlock, 0, s>>>(L, nullptr, nullptr);
-  launches++;
-  SCUC_CUDA(cudaGetLastError());
   SCUC_CUDA(cudaStreamSynchronize(s));
   const auto t1 = clk::now();
 
-  // 5. iterations: one graph per check period over all LPs, two in flight
+  // 5. iterations: one graph launch (the device loops until every LP has
+  // stopped), or one period at a time from the host, two in flight
   const int64_t nper = C[0].max_iter / ce;
   const bool use_graph = p.use_graph != 0;
   const int64_t per_launch = period_launches(B, ce);
-  if (use_graph) {
-    cudaGraph_t g;
-    SCUC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_batch_period(B, ce, ga);
-    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
-    if (rc != SCUC_OK) return rc;
-    SCUC_CUDA(e2);
-    SCUC_CUDA(cudaGraphInstantiate(&B.graph, g, 0));
-    cudaGraphDestroy(g);
-  }
-  int64_t launched = 0, seen = 0, periods = 0;
+  int64_t periods = 0;
   int timed_out = 0;
-  while (seen < nper) {
-    while (launched < nper && launched - seen < 2) {
-      if (use_graph) SCUC_CUDA(cudaGraphLaunch(B.graph, s));
-      else SCUC_TRY(launch_batch_period(B, ce, ga));
-      launches += per_launch;
-      SCUC_CUDA(cudaMemcpyAsync(B.ctrl_h + (size_t)(launched & 1) * nlp, B.ctrl, nlp * sizeof(Ctrl),
-                                cudaMemcpyDeviceToHost, s));
-      SCUC_CUDA(cudaEventRecord(B.ev_slot[launched & 1], s));
-      launched++;
-    }
-    SCUC_CUDA(cudaEventSynchronize(B.ev_slot[seen & 1]));
-    const Ctrl* hc = B.ctrl_h + (size_t)(seen & 1) * nlp;
-    seen++;
-    periods++;
-    bool all = true;
-    for (int b = 0; b < nlp && all; b++) all = hc[b].done != 0;
-    if (all) break;
-    if (std::chrono::duration<double>(clk::now() - t0).count() > p.time_limit_s) {
-      timed_out = 1;
-      break;
-    }
+  for (int b = 0; b < nlp; b++) {
+    C[b].t_start_ns = 0;
+    C[b].time_limit_ns = (p.time_limit_s > 0.0 && p.time_limit_s < 1e9) ? (uint64_t)(p.time_limit_s * 1e9) : 0;
   }
-  SCUC_CUDA(cudaStreamSynchronize(s));
-  SCUC_CUDA(cudaMemcpyAsync(C.data(), B.ctrl, nlp * sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-  SCUC_CUDA(cudaStreamSynchronize(s));
+  SCUC_CUDA(cudaMemcpyAsync(B.ctrl, C.data(), nlp * sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  k_init_iterates<<<dim3(ga, nlp), kBlock, 0, s>>>(L, nullptr, nullptr);
+  launches++;
+  SCUC_CUDA(cudaGetLastError());
+  if (use_graph) {
+    SCUC_TRY(build_batch_graph(B, ce, ga));
+    SCUC_CUDA(cudaGraphLaunch(B.graph, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    SCUC_CUDA(cudaMemcpyAsync(C.data(), B.ctrl, nlp * sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    int64_t tmax = 0;
+    for (int b = 0; b < nlp; b++) tmax = std::max<int64_t>(tmax, C[b].t);
+    periods = (tmax + ce - 1) / ce;
+    launches += periods * (per_launch + 1);
+  } else {
+    int64_t launched = 0, seen = 0;
+    while (seen < nper) {
+      while (launched < nper && launched - seen < 2) {
+        SCUC_TRY(launch_batch_period(B, s, ce, ga));
+        launches += per_launch;
+        SCUC_CUDA(cudaMemcpyAsync(B.ctrl_h + (size_t)(launched & 1) * nlp, B.ctrl, nlp * sizeof(Ctrl),
+                                  cudaMemcpyDeviceToHost, s));
+        SCUC_CUDA(cudaEventRecord(B.ev_slot[launched & 1], s));
+        launched++;
+      }
+      SCUC_CUDA(cudaEventSynchronize(B.ev_slot[seen & 1]));
+      const Ctrl* hc = B.ctrl_h + (size_t)(seen & 1) * nlp;
+      seen++;
+      periods++;
+      bool all = true;
+      for (int b = 0; b < nlp && all; b++) all = hc[b].done != 0;
+      if (all) break;
+      if (std::chrono::duration<double>(clk::now() - t0).count() > p.time_limit_s) {
+        timed_out = 1;
+        break;
+      }
+    }
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    SCUC_CUDA(cudaMemcpyAsync(C.data(), B.ctrl, nlp * sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+  }
   const auto t2 = clk::now();
 
   // 6. unscaled outputs, logs, per-LP information

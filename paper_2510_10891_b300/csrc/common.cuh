@@ -101,6 +101,8 @@ struct Ctrl {
   int32_t restarts, nlog, fp64_phase, stall;
   double kkt, rp, rd, gap, pobj, dobj;
   double reject_kkt;  // > 0: stop with SCUC_ST_FALLBACK_COLD if the first check has kkt >= this
+  uint64_t t_start_ns;     // device clock at the start of the iterations
+  uint64_t time_limit_ns;  // > 0: stop with SCUC_ST_TIME_LIMIT after this long (checked at checks)
 };
 
 struct PowerCtrl {

@@ -183,6 +183,7 @@ Handle::~Handle() {
   if (ev_work) cudaEventDestroy(ev_work);
   for (auto& e : ev_slot)
     if (e) cudaEventDestroy(e);
+  if (aux) cudaStreamDestroy(aux);
   if (work) cudaStreamDestroy(work);
 }
 
@@ -536,34 +537,121 @@ int Handle::ensure_log(int cap) {
 
 // One check period: anchor, check_every-1 plain iterations, a check iteration,
 // the two FP64 residual SpMVs and the decide kernel.
-int Handle::launch_period(int check_every, bool profile) {
-  cudaStream_t s = work;
+// The check_every iterations of one period in one precision (PREC) on stream
+// s; with profile, events around the two half-steps of every iteration.
+template <int PREC>
+int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
   const DevLP L = dev();
-  k_anchor<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L);
   for (int j = 0; j < check_every; j++) {
     const bool chk = (j == check_every - 1);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 0], s));
-    if (pT.nchunk) k_chunks_iter<kChunksPrimal><<<pT.nchunkblk, kBlock, 0, s>>>(L);
-    if (pT.nblk) k_primal_sum<<<pT.nblk, kBlock, pT.smem, s>>>(L);
-    if (chk) k_primal_epi<true><<<epi_gx, kBlock, 0, s>>>(L, j);
-    else k_primal_epi<false><<<epi_gx, kBlock, 0, s>>>(L, j);
+    if (pT.nchunk) k_chunks_iter<kChunksPrimal, PREC><<<pT.nchunkblk, kBlock, 0, s>>>(L);
+    if (pT.nblk) k_primal_sum<PREC><<<pT.nblk, kBlock, pT.smem, s>>>(L);
+    if (chk) k_primal_epi<true, PREC><<<epi_gx, kBlock, 0, s>>>(L, j);
+    else k_primal_epi<false, PREC><<<epi_gx, kBlock, 0, s>>>(L, j);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 1], s));
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 2], s));
-    if (pA.nchunk) k_chunks_iter<kChunksDual><<<pA.nchunkblk, kBlock, 0, s>>>(L);
+    if (pA.nchunk) k_chunks_iter<kChunksDual, PREC><<<pA.nchunkblk, kBlock, 0, s>>>(L);
     if (pA.nblk) {
-      if (chk) k_dual<true><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
-      else k_dual<false><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
+      if (chk) k_dual<true, PREC><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
+      else k_dual<false, PREC><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
     }
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 3], s));
   }
-  if (pA.nchunk) k_chunks_iter<kChunksResPrimal><<<pA.nchunkblk, kBlock, 0, s>>>(L);
+  SCUC_CUDA(cudaGetLastError());
+  return SCUC_OK;
+}
+
+// kernels of one period: anchor, iterations, residual SpMVs, decide
+int64_t Handle::period_kernels(int check_every) const {
+  const int la = (pA.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0), lt = (pT.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0);
+  return 2 + (int64_t)check_every * (la + lt + 1) + la + lt;
+}
+
+// check SpMVs (FP64) and the decide kernel of a period
+int Handle::launch_checks(cudaStream_t s, int check_every) {
+  const DevLP L = dev();
+  if (pA.nchunk) k_chunks_iter<kChunksResPrimal, kPrecF64><<<pA.nchunkblk, kBlock, 0, s>>>(L);
   if (pA.nblk) k_res_primal<<<pA.nblk, kBlock, pA.smem, s>>>(L);
-  if (pT.nchunk) k_chunks_iter<kChunksResDual><<<pT.nchunkblk, kBlock, 0, s>>>(L);
+  if (pT.nchunk) k_chunks_iter<kChunksResDual, kPrecF64><<<pT.nchunkblk, kBlock, 0, s>>>(L);
   if (pT.nblk) k_res_dual<<<pT.nblk, kBlock, pT.smem, s>>>(L);
   k_decide<<<1, kDecideThreads, 0, s>>>(L, check_every);
   SCUC_CUDA(cudaGetLastError());
-  const int la = (pA.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0), lt = (pT.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0);
-  nlaunch += 2 + (int64_t)check_every * (la + lt + 1) + la + lt;
+  return SCUC_OK;
+}
+
+// One period launched from the host in the phase the host last saw.
+int Handle::launch_period(int check_every, bool profile, bool fp64) {
+  cudaStream_t s = work;
+  k_anchor<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(dev());
+  if (fp64) SCUC_TRY(launch_iterations<kPrecF64>(s, check_every, profile));
+  else SCUC_TRY(launch_iterations<kPrecF32>(s, check_every, profile));
+  SCUC_TRY(launch_checks(s, check_every));
+  nlaunch += period_kernels(check_every);
+  return SCUC_OK;
+}
+
+// The whole iteration as one graph: WHILE (not stopped) { anchor; IF (FP64
+// phase) FP64 iterations ELSE FP32 iterations; checks; decide; conditions }.
+// The decide kernel's state picks the branch and ends the loop on the
+// device, so a solve is one graph launch with no host round trip.
+int Handle::build_solve_graph(int check_every, int phase64) {
+  if (!aux) SCUC_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  SCUC_CUDA(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+  } guard{g};
+  cudaGraphConditionalHandle hloop, hphase;
+  SCUC_CUDA(cudaGraphConditionalHandleCreate(&hloop, g, 1, cudaGraphCondAssignDefault));
+  SCUC_CUDA(cudaGraphConditionalHandleCreate(&hphase, g, phase64 ? 1 : 0, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hloop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  SCUC_CUDA(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  const DevLP L = dev();
+  cudaStream_t s = work;
+  SCUC_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  k_anchor<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(L);
+  // the precision branch, inserted into the capture
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t capg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &capg, &deps, nullptr, &ndeps);
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hphase;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 2;
+  cudaGraphNode_t inode = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip);
+  if (e == cudaSuccess)
+    e = cudaStreamUpdateCaptureDependencies(s, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  int rc = e == cudaSuccess ? launch_checks(s, check_every) : SCUC_OK;
+  if (e == cudaSuccess && rc == SCUC_OK) k_loop_cond<<<1, kDecideThreads, 0, s>>>(L, hloop, hphase, 1);
+  cudaGraph_t cap_out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s, &cap_out);
+  SCUC_CUDA(e);
+  SCUC_TRY(rc);
+  SCUC_CUDA(e2);
+  // the two branches: [0] FP64 phase, [1] FP32 phase
+  for (int br = 0; br < 2; br++) {
+    SCUC_CUDA(cudaStreamBeginCaptureToGraph(aux, ip.conditional.phGraph_out[br], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+    rc = br == 0 ? launch_iterations<kPrecF64>(aux, check_every, false)
+                 : launch_iterations<kPrecF32>(aux, check_every, false);
+    cudaGraph_t bout = nullptr;
+    const cudaError_t e3 = cudaStreamEndCapture(aux, &bout);
+    SCUC_TRY(rc);
+    SCUC_CUDA(e3);
+  }
+  SCUC_CUDA(cudaGraphInstantiate(&graph_exec, g, 0));
   return SCUC_OK;
 }
 
@@ -634,6 +722,8 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.rho0 = 0; C.rho_prev = 0; C.best_kkt = INFINITY;
   C.first_check = 1; C.done = 0; C.status = -1; C.restart_pending = 0;
   C.reject_kkt = reject_kkt;
+  C.t_start_ns = 0;
+  C.time_limit_ns = (p.time_limit_s > 0.0 && p.time_limit_s < 1e9) ? (uint64_t)(p.time_limit_s * 1e9) : 0;
   C.restarts = 0; C.nlog = 0; C.fp64_phase = mixed ? 0 : 1; C.stall = 0;
   SCUC_CUDA(cudaMemcpyAsync(ctrl, &C, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
   if (p.check_every > coef_cap) {
@@ -653,9 +743,11 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   SCUC_CUDA(cudaStreamSynchronize(s));
   const auto t1 = clk::now();
 
-  // iteration: periods of check_every iterations, two in flight
+  // iteration: one graph launch for the whole loop (the device decides the
+  // precision of every period and when to stop), or, when profiling or
+  // without graphs, one period at a time from the host
   const int64_t nper = C.max_iter / ce;
-  bool use_graph = p.use_graph && !p.profile;
+  const bool use_graph = p.use_graph && !p.profile;
   if (p.profile && (int)prof_ev.size() < 4 * p.check_every) {
     while ((int)prof_ev.size() < 4 * p.check_every) {
       cudaEvent_t e;
@@ -663,62 +755,48 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
       prof_ev.push_back(e);
     }
   }
-  const void* key[4] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
-                        (const void*)coef};
-  if (use_graph && (!graph_exec || memcmp(key, graph_key, sizeof(key)) != 0)) {
-    if (graph_exec) { cudaGraphExecDestroy(graph_exec); graph_exec = nullptr; }
-    cudaGraph_t g;
-    SCUC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const int64_t before = nlaunch;
-    int rc = launch_period(p.check_every, false);
-    nlaunch = before;  // captured, not launched
-    cudaError_t ce2 = cudaStreamEndCapture(s, &g);
-    if (rc != SCUC_OK) return rc;
-    SCUC_CUDA(ce2);
-    size_t nodes = 0;
-    SCUC_CUDA(cudaGraphGetNodes(g, nullptr, &nodes));
-    graph_nodes = (int64_t)nodes;
-    SCUC_CUDA(cudaGraphInstantiate(&graph_exec, g, 0));
-    cudaGraphDestroy(g);
-    memcpy(graph_key, key, sizeof(key));
-  }
   double ms_p = 0.0, ms_d = 0.0, ms_p32 = 0.0, ms_d32 = 0.0;
   int64_t n_p = 0, n_d = 0, n_p32 = 0, n_d32 = 0;
-  int phase64 = mixed ? 0 : 1;  // phase the next launched period runs in (profile mode)
   int timed_out = 0;
-  int64_t launched = 0, seen = 0;
-  const int inflight = p.profile ? 1 : 2;
-  while (seen < nper) {
-    while (launched < nper && launched - seen < inflight) {
-      if (use_graph) {
-        SCUC_CUDA(cudaGraphLaunch(graph_exec, s));
-        nlaunch += graph_nodes;
-      } else {
-        SCUC_TRY(launch_period(p.check_every, p.profile != 0));
+  if (use_graph) {
+    const void* key[5] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
+                          (const void*)coef, (const void*)(intptr_t)(mixed ? 0 : 1)};
+    if (!graph_exec || memcmp(key, graph_key, sizeof(key)) != 0) {
+      if (graph_exec) {
+        cudaGraphExecDestroy(graph_exec);
+        graph_exec = nullptr;
       }
-      SCUC_CUDA(cudaMemcpyAsync(ctrl_h + (launched & 1), ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-      SCUC_CUDA(cudaEventRecord(ev_slot[launched & 1], s));
-      launched++;
+      SCUC_TRY(build_solve_graph(p.check_every, mixed ? 0 : 1));
+      memcpy(graph_key, key, sizeof(key));
     }
-    // wait for the oldest period in flight (its state copy has landed)
-    SCUC_CUDA(cudaEventSynchronize(ev_slot[seen & 1]));
-    if (p.profile) {
-      for (int j = 0; j < p.check_every; j++) {
-        float a = 0.f, b = 0.f;
-        SCUC_CUDA(cudaEventElapsedTime(&a, prof_ev[4 * j + 0], prof_ev[4 * j + 1]));
-        SCUC_CUDA(cudaEventElapsedTime(&b, prof_ev[4 * j + 2], prof_ev[4 * j + 3]));
-        ms_p += a; ms_d += b;
-        if (!phase64) { ms_p32 += a; ms_d32 += b; }
+    SCUC_CUDA(cudaGraphLaunch(graph_exec, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    SCUC_CUDA(cudaMemcpyAsync(&C, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    nlaunch += ((C.t + ce - 1) / ce) * (period_kernels(p.check_every) + 1);
+  } else {
+    int phase64 = mixed ? 0 : 1;  // phase of the next period (the host waits for every period)
+    for (int64_t per = 0; per < nper; per++) {
+      SCUC_TRY(launch_period(p.check_every, p.profile != 0, phase64 != 0));
+      SCUC_CUDA(cudaMemcpyAsync(ctrl_h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+      SCUC_CUDA(cudaEventRecord(ev_slot[0], s));
+      SCUC_CUDA(cudaEventSynchronize(ev_slot[0]));
+      if (p.profile) {
+        for (int j = 0; j < p.check_every; j++) {
+          float a = 0.f, b = 0.f;
+          SCUC_CUDA(cudaEventElapsedTime(&a, prof_ev[4 * j + 0], prof_ev[4 * j + 1]));
+          SCUC_CUDA(cudaEventElapsedTime(&b, prof_ev[4 * j + 2], prof_ev[4 * j + 3]));
+          ms_p += a; ms_d += b;
+          if (!phase64) { ms_p32 += a; ms_d32 += b; }
+        }
+        n_p += p.check_every; n_d += p.check_every;
+        if (!phase64) { n_p32 += p.check_every; n_d32 += p.check_every; }
       }
-      n_p += p.check_every; n_d += p.check_every;
-      if (!phase64) { n_p32 += p.check_every; n_d32 += p.check_every; }
+      phase64 = ctrl_h[0].fp64_phase;
+      if (ctrl_h[0].done) break;
+      const double el = std::chrono::duration<double>(clk::now() - t0).count();
+      if (el > p.time_limit_s) { timed_out = 1; break; }
     }
-    const Ctrl& h = ctrl_h[seen & 1];
-    phase64 = h.fp64_phase;
-    seen++;
-    if (h.done) break;
-    const double el = std::chrono::duration<double>(clk::now() - t0).count();
-    if (el > p.time_limit_s) { timed_out = 1; break; }
   }
   SCUC_CUDA(cudaStreamSynchronize(s));
   SCUC_CUDA(cudaMemcpyAsync(&C, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
@@ -805,7 +883,7 @@ void scuc_default_params(scuc_solve_params* p) {
   p->restart_suff = 0.2;
   p->restart_nec = 0.8;
   p->restart_long = 0.2;
-  p->polish_factor = 10.0;
+  p->polish_factor = 1.0;
   p->polish_stall = 20;
   p->use_graph = 1;
   p->profile = 0;

@@ -55,7 +55,9 @@ struct Handle {
   scuc_check_log* log_d = nullptr;
   int log_cap = 0, last_nlog = 0;
   cudaGraphExec_t graph_exec = nullptr;
-  const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // check_every, FP32 values, log, coef
+  const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // check_every, FP32 values, log,
+                                                                               // coef, initial phase
+  cudaStream_t aux = nullptr;  // capture stream of the graph's conditional bodies
   double* coef = nullptr;
   int64_t nlaunch = 0, graph_nodes = 0;  // kernels launched by this handle; nodes of the period graph
   int coef_cap = 0;
@@ -78,7 +80,12 @@ struct Handle {
   int setup_scaling(int use_scaling, bool need_f32);
   int power_method(const scuc_solve_params& p, double* lam, int* iters);
   int ensure_log(int cap);
-  int launch_period(int check_every, bool profile);
+  template <int PREC>
+  int launch_iterations(cudaStream_t s, int check_every, bool profile);
+  int launch_checks(cudaStream_t s, int check_every);
+  int64_t period_kernels(int check_every) const;
+  int launch_period(int check_every, bool profile, bool fp64);
+  int build_solve_graph(int check_every, int phase64);
   int solve(const scuc_solve_params& p, const double* x0, const double* y0, double* xo,
             double* yo, double* zo, scuc_solve_info* info, double reject_kkt = 0.0);
   int* pt_flag = nullptr;  // index checks of scuc_ws_assemble / scuc_ws_targets

@@ -49,6 +49,12 @@ __device__ __forceinline__ void lp_range(const int* off, int lp, int total, int&
   }
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ double clampd(double v, double l, double u) {
   return v < l ? l : (v > u ? u : v);
 }
@@ -57,26 +63,36 @@ __device__ __forceinline__ double clampd(double v, double l, double u) {
 // that launches them compiles its own copy.
 namespace {
 
+// Precision of the products in an iteration kernel: kPrecRuntime reads each
+// LP's phase from its control block (batches, whose LPs switch at different
+// times); kPrecF32 / kPrecF64 are compiled for one phase (one LP, whose phase
+// picks the kernels: a graph conditional, or the host between periods), so
+// each gets its own register allocation.
+constexpr int kPrecRuntime = 0, kPrecF32 = 1, kPrecF64 = 2;
+
+__device__ __forceinline__ bool phase64(const Ctrl* c, int prec) {
+  return prec == kPrecRuntime ? c->fp64_phase != 0 : prec == kPrecF64;
+}
+
 // ---------------------------------------------------------------------------
 // chunk launches of the long rows (one LP; batches have no long rows)
 // ---------------------------------------------------------------------------
 constexpr int kChunksPrimal = 0, kChunksDual = 1, kChunksResPrimal = 2, kChunksResDual = 3;
 
 // Chunk sums for the next main launch: A^T y (primal step) or A x_t (dual
-// step) in the precision of the current phase, A x_bar / A^T y_bar (checks)
-// in FP64.
-template <int MODE>
+// step) in the phase's precision, A x_bar / A^T y_bar (checks) in FP64.
+template <int KIND, int PREC>
 __global__ void __launch_bounds__(kBlock) k_chunks_iter(DevLP L) {
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
-  const bool fp64 = ctrl->fp64_phase != 0;
-  if (MODE == kChunksPrimal) {
+  const bool fp64 = phase64(ctrl, PREC);
+  if (KIND == kChunksPrimal) {
     if (fp64) chunk_warp<double>(L.colt, L.vst, L.y, L.pT);
     else chunk_warp<float>(L.colt, L.vst32, L.y32, L.pT);
-  } else if (MODE == kChunksDual) {
+  } else if (KIND == kChunksDual) {
     if (fp64) chunk_warp<double>(L.col, L.vs, L.xt, L.pA);
     else chunk_warp<float>(L.col, L.vs32, L.xt32, L.pA);
-  } else if (MODE == kChunksResPrimal) {
+  } else if (KIND == kChunksResPrimal) {
     chunk_warp<double>(L.col, L.vs, L.xbar, L.pA);
   } else {
     chunk_warp<double>(L.colt, L.vst, L.ybar, L.pT);
@@ -131,12 +147,13 @@ struct GStoreEpi {
   __device__ void row(int r, VT a) { g[r] = a; }
 };
 
+template <int PREC>
 __global__ void __launch_bounds__(kBlock) k_primal_sum(DevLP L) {
   extern __shared__ __align__(128) unsigned char smem[];
   const BlockPlan bp = spmv_plan<false>(L.pT);  // issued together with the control loads
   const Ctrl* ctrl = L.ctrl + (L.blkT ? L.blkT[blockIdx.x] : 0);
   if (ctrl->done) return;
-  if (ctrl->fp64_phase) {
+  if (phase64(ctrl, PREC)) {
     GStoreEpi<double> e{L.gsum};
     spmv_run<double, GStoreEpi<double>, true>(bp, L.rpt, L.colt, L.vst, L.y, L.pT, smem, e);
   } else {
@@ -148,13 +165,13 @@ __global__ void __launch_bounds__(kBlock) k_primal_sum(DevLP L) {
 // Primal step, elementwise over the columns of LP blockIdx.y (blockIdx.x of
 // epi_gx blocks strides over them): contiguous loads, full warps for the
 // FP64 arithmetic.
-template <bool CHECK>
+template <bool CHECK, int PREC>
 __global__ void __launch_bounds__(kBlock) k_primal_epi(DevLP L, int j) {
   const int lp = blockIdx.y;
   const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
   const double* cf = L.coef + (size_t)lp * L.coef_stride;
-  PrimalEpi<CHECK> epi{L, ctrl->sigma, cf[2 * j], cf[2 * j + 1], ctrl->fp64_phase != 0,
+  PrimalEpi<CHECK> epi{L, ctrl->sigma, cf[2 * j], cf[2 * j + 1], phase64(ctrl, PREC),
                        {0.0, 0.0, 0.0, 0.0}, 0.0, 0.0, 0.0, 0.0, 0.0};
   const float* g32 = L.gsum32;
   int c0, c1;
@@ -200,7 +217,7 @@ struct DualEpi {
   }
 };
 
-template <bool CHECK>
+template <bool CHECK, int PREC>
 __global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_dual(DevLP L, int j) {
   extern __shared__ __align__(128) unsigned char smem[];
   const BlockPlan bp = spmv_plan<true>(L.pA);  // issued together with the control loads
@@ -208,7 +225,7 @@ __global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_dual(DevLP L, int j)
   const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
   const double* cf = L.coef + (size_t)lp * L.coef_stride;
-  DualEpi<CHECK> epi{L, ctrl->s_step, cf[2 * j], cf[2 * j + 1], ctrl->fp64_phase != 0,
+  DualEpi<CHECK> epi{L, ctrl->s_step, cf[2 * j], cf[2 * j + 1], phase64(ctrl, PREC),
                      {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
   if (bp.er >= 0) epi.load(bp.er);
   if (epi.fp64) {
@@ -396,11 +413,30 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, 
   C->t = t;
   C->s_step = 1.0 / (C->lambda * C->sigma);
   if (status < 0 && t >= C->max_iter) status = SCUC_ST_ITER_LIMIT;
+  if (status < 0 && C->time_limit_ns > 0 && globaltimer_ns() - C->t_start_ns > C->time_limit_ns)
+    status = SCUC_ST_TIME_LIMIT;
   if (status >= 0) {
     C->status = status;
     C->done = 1;
   }
   return C->k;
+}
+
+// Conditions of a solve graph (one launch per solve): the loop continues
+// while some LP has not stopped; the precision branch follows LP 0 (graphs of
+// one LP).  One block, after the decide kernel.
+__global__ void __launch_bounds__(kDecideThreads) k_loop_cond(DevLP L, cudaGraphConditionalHandle loop,
+                                                             cudaGraphConditionalHandle phase, int set_phase) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int lp = threadIdx.x; lp < L.nlp; lp += kDecideThreads)
+    if (!L.ctrl[lp].done) atomicOr(&s_any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cudaGraphSetConditional(loop, s_any ? 1u : 0u);
+    if (set_phase) cudaGraphSetConditional(phase, L.ctrl[0].fp64_phase ? 1u : 0u);
+  }
 }
 
 // restart: anchor <- current point (runs at the start of each period);

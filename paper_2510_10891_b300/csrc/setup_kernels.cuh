@@ -344,6 +344,7 @@ __global__ void k_power_norm_seed(int n, double* __restrict__ q, const PowerCtrl
 // blockIdx.y = LP of the batch
 __global__ void k_init_iterates(DevLP L, const double* __restrict__ xin, const double* __restrict__ yin) {
   const int lp = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) L.ctrl[lp].t_start_ns = globaltimer_ns();
   const double beta = L.ctrl[lp].beta, gamma = L.ctrl[lp].gamma;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int c0, c1, r0, r1;

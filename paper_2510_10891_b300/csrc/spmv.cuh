@@ -122,35 +122,35 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 // Partial sum of val[e] * x[col[e]] for e = a + li, a + li + nl, ... < z:
 // consecutive lanes take consecutive entries, so one warp-wide gather touches
 // neighbouring columns (rows of these matrices list their columns in
-// increasing order, mostly a few apart); U independent accumulators,
-// combined in a fixed tree.  U = entries in flight per thread: eight for
-// FP32 values, four for FP64 (measured on the 13k-bus A^T: FP32 -9 % time
-// with eight, FP64 +16 %).
+// increasing order, mostly a few apart).  U entries in flight per thread
+// (eight for FP32 values, four for FP64: measured on the 13k-bus A^T), two
+// accumulators (the loads, not the FMAs, are the latency to hide; two keep
+// the register count low enough for full occupancy), combined in a fixed
+// order.
 template <typename VT>
 __device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* __restrict__ val,
                                         const VT* __restrict__ x, int a, int z, int li, int nl) {
   constexpr int U = sizeof(VT) == 4 ? 8 : 4;
-  VT s[U];
-#pragma unroll
-  for (int u = 0; u < U; u++) s[u] = VT(0);
+  VT s0 = VT(0), s1 = VT(0);
   int e = a + li;
   for (; e + (U - 1) * nl < z; e += U * nl) {
     int c[U];
-    VT v[U];
+    VT v[U], g[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       c[u] = ldcs(col + e + u * nl);
       v[u] = ldcs(val + e + u * nl);
     }
 #pragma unroll
-    for (int u = 0; u < U; u++) s[u] = fma_t(v[u], ldg(x + c[u]), s[u]);
+    for (int u = 0; u < U; u++) g[u] = ldg(x + c[u]);
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      s0 = fma_t(v[u], g[u], s0);
+      s1 = fma_t(v[u + 1], g[u + 1], s1);
+    }
   }
-  for (; e < z; e += nl) s[0] = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s[0]);
-#pragma unroll
-  for (int w = U / 2; w > 0; w >>= 1)
-#pragma unroll
-    for (int u = 0; u < w; u++) s[u] += s[u + w];
-  return s[0];
+  for (; e < z; e += nl) s0 = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s0);
+  return s0 + s1;
 }
 
 // One warp per chunk of a long row (chunk launch): chunk w = blockIdx.x *
