@@ -122,35 +122,67 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 // Partial sum of val[e] * x[col[e]] for e = a + li, a + li + nl, ... < z:
 // consecutive lanes take consecutive entries, so one warp-wide gather touches
 // neighbouring columns (rows of these matrices list their columns in
-// increasing order, mostly a few apart).  U entries in flight per thread
-// (eight for FP32 values, four for FP64: measured on the 13k-bus A^T), two
-// accumulators (the loads, not the FMAs, are the latency to hide; two keep
-// the register count low enough for full occupancy), combined in a fixed
-// order.
-template <typename VT>
+// increasing order, mostly a few apart).  U entries in flight per thread and
+// NA accumulators, combined in a fixed tree: eight and eight for FP32
+// values, four and two for FP64 (measured on the 13k-bus A^T).  The group
+// size nl is a compile-time constant, so the U loads of a round address
+// their entries with immediate offsets from one pointer.
+template <typename VT, int nl>
 __device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* __restrict__ val,
-                                        const VT* __restrict__ x, int a, int z, int li, int nl) {
+                                        const VT* __restrict__ x, int a, int z, int li) {
   constexpr int U = sizeof(VT) == 4 ? 8 : 4;
-  VT s0 = VT(0), s1 = VT(0);
+  constexpr int NA = sizeof(VT) == 4 ? 8 : 2;
+  VT s[NA];
+#pragma unroll
+  for (int q = 0; q < NA; q++) s[q] = VT(0);
   int e = a + li;
   for (; e + (U - 1) * nl < z; e += U * nl) {
     int c[U];
-    VT v[U], g[U];
+    VT v[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       c[u] = ldcs(col + e + u * nl);
       v[u] = ldcs(val + e + u * nl);
     }
 #pragma unroll
-    for (int u = 0; u < U; u++) g[u] = ldg(x + c[u]);
-#pragma unroll
-    for (int u = 0; u < U; u += 2) {
-      s0 = fma_t(v[u], g[u], s0);
-      s1 = fma_t(v[u + 1], g[u + 1], s1);
-    }
+    for (int u = 0; u < U; u++) s[u % NA] = fma_t(v[u], ldg(x + c[u]), s[u % NA]);
   }
-  for (; e < z; e += nl) s0 = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s0);
-  return s0 + s1;
+  for (; e < z; e += nl) s[0] = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s[0]);
+#pragma unroll
+  for (int w = NA / 2; w > 0; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; q++) s[q] += s[q + w];
+  return s[0];
+}
+
+// The same with the group size known only at run time (measured faster for
+// FP64 values on the 13k-bus A^T; the compile-time form is faster for FP32).
+template <typename VT>
+__device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT* __restrict__ val,
+                                           const VT* __restrict__ x, int a, int z, int li, int nl) {
+  constexpr int U = sizeof(VT) == 4 ? 8 : 4;
+  constexpr int NA = sizeof(VT) == 4 ? 8 : 2;
+  VT s[NA];
+#pragma unroll
+  for (int q = 0; q < NA; q++) s[q] = VT(0);
+  int e = a + li;
+  for (; e + (U - 1) * nl < z; e += U * nl) {
+    int c[U];
+    VT v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      c[u] = ldcs(col + e + u * nl);
+      v[u] = ldcs(val + e + u * nl);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) s[u % NA] = fma_t(v[u], ldg(x + c[u]), s[u % NA]);
+  }
+  for (; e < z; e += nl) s[0] = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s[0]);
+#pragma unroll
+  for (int w = NA / 2; w > 0; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; q++) s[q] += s[q + w];
+  return s[0];
 }
 
 // One warp per chunk of a long row (chunk launch): chunk w = blockIdx.x *
@@ -259,7 +291,19 @@ __device__ __forceinline__ void spmv_run(const BlockPlan& bp, const int* __restr
   if (bp.kind == 0) {
     const int gsz = bp.gsz;
     const int g = tid / gsz, li = tid - g * gsz;
-    VT acc = bp.rec.x >= 0 ? group_dot(col, val, x, bp.rec.y, bp.rec.z, li, gsz) : VT(0);
+    VT acc = VT(0);
+    if (bp.rec.x >= 0) {
+      if (sizeof(VT) == 8) {
+        acc = group_dot_rt<VT>(col, val, x, bp.rec.y, bp.rec.z, li, gsz);
+      } else {
+        switch (gsz) {
+          case 32: acc = group_dot<VT, 32>(col, val, x, bp.rec.y, bp.rec.z, li); break;
+          case 16: acc = group_dot<VT, 16>(col, val, x, bp.rec.y, bp.rec.z, li); break;
+          case 8: acc = group_dot<VT, 8>(col, val, x, bp.rec.y, bp.rec.z, li); break;
+          default: acc = group_dot<VT, 4>(col, val, x, bp.rec.y, bp.rec.z, li); break;
+        }
+      }
+    }
     for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, gsz);
     if (DIRECT) {
       if (li == 0 && bp.rec.x >= 0) epi.row(bp.rec.x, acc);
