@@ -197,7 +197,7 @@ int tune_partition(Batch& B, bool transpose, const std::vector<std::vector<int>>
                    int** blk, int** blk0, PartShape* chosen, int* ncand) {
   std::vector<PartShape> cands;
   if (autotune) {
-    for (int ept : {8, 16, 32})
+    for (int ept : {8, 12, 16})
       for (int run : {16, 64}) {
         PartShape sh;
         sh.ept = ept;

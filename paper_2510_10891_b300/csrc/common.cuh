@@ -44,15 +44,11 @@ inline int group_size_for(int len, int ept = 16) {
 }
 
 // tunable shape of a partition (plan_partition)
-#ifndef SCUC_DEFAULT_EPT
-#define SCUC_DEFAULT_EPT 16
-#endif
-#ifndef SCUC_DEFAULT_RUN
-#define SCUC_DEFAULT_RUN 32
-#endif
+// Defaults measured on the 13k-bus LP (FP32 A^T product: 0.319 ms at 12
+// entries per thread, 0.331 at 16, 0.441 at 24; 6-10 within 1 %).
 struct PartShape {
-  int ept = SCUC_DEFAULT_EPT;      // target entries per thread of list rows
-  int min_run = SCUC_DEFAULT_RUN;  // shortest run of short rows that is staged in shared memory
+  int ept = 12;      // target entries per thread of list rows
+  int min_run = 32;  // shortest run of short rows that is staged in shared memory
 };
 
 constexpr int kChunk = 512;             // entries per chunk of a long row (one warp each)
