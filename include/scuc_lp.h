@@ -281,6 +281,10 @@ typedef struct {
   int64_t n_fixed_cols;    /* columns with xl == xu after propagation        */
   double obj_const;        /* c^T x of the removed (fixed) columns           */
   double ms;               /* wall time of the call                          */
+  double ms_propagate;     /* of which Round, Algorithm 1 and propagation     */
+  double ms_reduce;        /* ... the reduced CSR and maps                    */
+  double ms_setup;         /* ... the reduced LP's device setup (transpose,
+                              partitions, buffers)                          */
 } scuc_fix_info;
 
 void scuc_default_fix_params(scuc_fix_params* p);

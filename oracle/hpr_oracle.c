@@ -476,22 +476,37 @@ int64_t orc_fix(int32_t G, int32_t T, const double* u, const double* v, const do
 /* ---------------------------------------------------------------------- */
 /* Activity range of one row over the bounds: finite parts and the number of
  * infinite contributions, summed in entry order.                          */
+/* Sums over the entries of one row are taken in a fixed order that a warp
+ * of 32 lanes can reproduce: entry k0 + q goes to partial sum q mod 32
+ * (each partial in entry order), then partials are combined by halving,
+ * p[l] += p[l + w] for w = 16, 8, 4, 2, 1.  (The definitions fix no order;
+ * this one is shared with the GPU so both take the same rounding.) */
+#define ORC_LANES 32
+static double lanes_total(double* p) {
+  for (int w = ORC_LANES / 2; w > 0; w >>= 1)
+    for (int l = 0; l < w; l++) p[l] += p[l + w];
+  return p[0];
+}
+
+/* activity range of row entries [k0, k1): min and max of sum a_k x_k over
+ * the bounds, with the infinite contributions counted apart */
 static void row_activity(int64_t k0, int64_t k1, const int32_t* col, const double* val,
                          const double* xl, const double* xu, double* mn, double* mx,
                          int32_t* cmn, int32_t* cmx) {
-  double a_mn = 0.0, a_mx = 0.0;
+  double p_mn[ORC_LANES] = {0}, p_mx[ORC_LANES] = {0};
   int32_t c_mn = 0, c_mx = 0;
   for (int64_t k = k0; k < k1; k++) {
+    const int q = (int)((k - k0) % ORC_LANES);
     double a = val[k];
     double lmin = a > 0.0 ? xl[col[k]] : xu[col[k]];
     double lmax = a > 0.0 ? xu[col[k]] : xl[col[k]];
     if (isinf(lmin)) c_mn++;
-    else a_mn += a * lmin;
+    else p_mn[q] += a * lmin;
     if (isinf(lmax)) c_mx++;
-    else a_mx += a * lmax;
+    else p_mx[q] += a * lmax;
   }
-  *mn = a_mn;
-  *mx = a_mx;
+  *mn = lanes_total(p_mn);
+  *mx = lanes_total(p_mx);
   *cmn = c_mn;
   *cmx = c_mx;
 }
@@ -516,8 +531,9 @@ int32_t orc_propagate(int32_t m, int32_t n, const int64_t* rp, const int32_t* co
         const double a = val[k];
         const double lmin = a > 0.0 ? xl[j] : xu[j];
         const double lmax = a > 0.0 ? xu[j] : xl[j];
-        /* from the row's upper bound: a x_j <= hi - (min activity of the rest) */
-        if (isfinite(hi[i])) {
+        /* from the row's upper bound: a x_j <= hi - (min activity of the rest);
+         * a row whose maximum activity cannot exceed hi implies nothing */
+        if (isfinite(hi[i]) && !(cmx == 0 && mx <= hi[i])) {
           int ok = isinf(lmin) ? (cmn == 1) : (cmn == 0);
           if (ok) {
             double rest = isinf(lmin) ? mn : mn - a * lmin;
@@ -526,8 +542,9 @@ int32_t orc_propagate(int32_t m, int32_t n, const int64_t* rp, const int32_t* co
             else { if (b > nlo[j]) nlo[j] = b; }
           }
         }
-        /* from the row's lower bound: a x_j >= lo - (max activity of the rest) */
-        if (isfinite(lo[i])) {
+        /* from the row's lower bound: a x_j >= lo - (max activity of the rest);
+         * a row whose minimum activity cannot fall below lo implies nothing */
+        if (isfinite(lo[i]) && !(cmn == 0 && mn >= lo[i])) {
           int ok = isinf(lmax) ? (cmx == 1) : (cmx == 0);
           if (ok) {
             double rest = isinf(lmax) ? mx : mx - a * lmax;
@@ -590,31 +607,34 @@ int orc_reduce(int32_t m, int32_t n, const int64_t* rp, const int32_t* col, cons
   rp_r[0] = 0;
   for (int32_t i = 0; i < m; i++) {
     /* fold the fixed columns into the row bounds */
-    double shift = 0.0;
+    double p_sh[ORC_LANES] = {0};
     int64_t kept = 0;
     for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-      if (newcol[col[k]] < 0) shift += val[k] * xl[col[k]];
+      if (newcol[col[k]] < 0) p_sh[(k - rp[i]) % ORC_LANES] += val[k] * xl[col[k]];
       else kept++;
     }
+    const double shift = lanes_total(p_sh);
     double l = lo[i] - shift, u = hi[i] - shift;
     if (kept == 0) {
       if (l > 1e-6 * fmax(1.0, fabs(l)) || u < -1e-6 * fmax(1.0, fabs(u))) bad = 1;
       continue;
     }
     /* activity range over the free columns */
-    double mn = 0.0, mx = 0.0;
+    double p_mn[ORC_LANES] = {0}, p_mx[ORC_LANES] = {0};
     int32_t cmn = 0, cmx = 0;
     for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
       const int32_t j = col[k];
       if (newcol[j] < 0) continue;
+      const int q = (int)((k - rp[i]) % ORC_LANES);
       const double a = val[k];
       const double lmin = a > 0.0 ? xl[j] : xu[j];
       const double lmax = a > 0.0 ? xu[j] : xl[j];
       if (isinf(lmin)) cmn++;
-      else mn += a * lmin;
+      else p_mn[q] += a * lmin;
       if (isinf(lmax)) cmx++;
-      else mx += a * lmax;
+      else p_mx[q] += a * lmax;
     }
+    const double mn = lanes_total(p_mn), mx = lanes_total(p_mx);
     int lo_red = !isfinite(l) || (cmn == 0 && mn >= l);
     int hi_red = !isfinite(u) || (cmx == 0 && mx <= u);
     if (lo_red && hi_red) continue;

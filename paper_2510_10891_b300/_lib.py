@@ -66,7 +66,8 @@ class FixParams(C.Structure):
 class FixInfo(C.Structure):
     _fields_ = [("nfixed", C.c_int64), ("passes", C.c_int32), ("infeasible", C.c_int32),
                 ("m_red", C.c_int32), ("n_red", C.c_int32), ("nnz_red", C.c_int64),
-                ("n_fixed_cols", C.c_int64), ("obj_const", C.c_double), ("ms", C.c_double)]
+                ("n_fixed_cols", C.c_int64), ("obj_const", C.c_double), ("ms", C.c_double),
+                ("ms_propagate", C.c_double), ("ms_reduce", C.c_double), ("ms_setup", C.c_double)]
 
 
 class WsTrainParams(C.Structure):

@@ -3,10 +3,12 @@
 // LP (fixed columns folded into the row bounds, redundant rows dropped).
 //
 // Row activities, candidate bounds and the folded row bounds use explicitly
-// rounded FP64 operations in entry order (no contraction), so propagated
-// bounds and reduced-LP data are bit-identical run to run; min/max over a
-// column's candidates is order-free.  Every fixing and presolve decision is
-// made from those values.
+// rounded FP64 operations (no contraction); a row's sums are taken by one
+// warp in a fixed order (entry q of the row into lane q mod 32, each lane in
+// entry order, lanes combined by halving 16, 8, 4, 2, 1), so propagated
+// bounds and reduced-LP data are bit-identical run to run and to a CPU loop
+// that takes the same order; min/max over a column's candidates is
+// order-free.  Every fixing and presolve decision is made from those values.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -73,17 +75,36 @@ __global__ void k_fix(int G, int T, const double* __restrict__ x, const int* __r
   if (cnt) atomicAdd(nfixed, cnt);
 }
 
-// Activity range of each row over the current bounds: finite parts summed in
-// entry order, plus the number of infinite contributions (thread per row).
-__global__ void k_row_activity(const int* __restrict__ rp, const int* __restrict__ col,
-                               const double* __restrict__ val, int m, const double* __restrict__ xl,
-                               const double* __restrict__ xu, double* __restrict__ mn,
-                               double* __restrict__ mx, int* __restrict__ cmn, int* __restrict__ cmx) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kWarps = kThreads / 32;
+
+// one warp per item
+int grid_w(int64_t work) {
+  const int64_t g = (work + kWarps - 1) / kWarps;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// lane partials combined by halving (lane 0 holds the total)
+__device__ __forceinline__ double lanes_total(double v) {
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, w));
+  return v;
+}
+
+__device__ __forceinline__ int lanes_count(int c) { return __reduce_add_sync(0xffffffffu, c); }
+
+// Activity range of each row over the current bounds: finite parts in the
+// lane order above, plus the number of infinite contributions (warp per row).
+__global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict__ rp, const int* __restrict__ col,
+                                                           const double* __restrict__ val, int m,
+                                                           const double* __restrict__ xl,
+                                                           const double* __restrict__ xu, double* __restrict__ mn,
+                                                           double* __restrict__ mx, int* __restrict__ cmn,
+                                                           int* __restrict__ cmx) {
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= m) return;
   double a_mn = 0.0, a_mx = 0.0;
   int c_mn = 0, c_mx = 0;
-  for (int e = rp[i]; e < rp[i + 1]; e++) {
+  for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
     const double a = val[e];
     const int j = col[e];
     const double lmin = a > 0.0 ? xl[j] : xu[j];
@@ -93,50 +114,72 @@ __global__ void k_row_activity(const int* __restrict__ rp, const int* __restrict
     if (isinf(lmax)) c_mx++;
     else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
   }
-  mn[i] = a_mn;
-  mx[i] = a_mx;
-  cmn[i] = c_mn;
-  cmx[i] = c_mx;
+  a_mn = lanes_total(a_mn);
+  a_mx = lanes_total(a_mx);
+  c_mn = lanes_count(c_mn);
+  c_mx = lanes_count(c_mx);
+  if (lane == 0) {
+    mn[i] = a_mn;
+    mx[i] = a_mx;
+    cmn[i] = c_mn;
+    cmx[i] = c_mx;
+  }
 }
 
-// One Jacobi pass for each column (thread per column over its A^T entries):
-// candidate bounds from every row, integer rounding, acceptance thresholds.
-// Only column j's own bounds are read and written by thread j; row
-// activities come from the previous kernel, so the pass is Jacobi.
-__global__ void k_col_propagate(const int* __restrict__ rpt, const int* __restrict__ colt,
-                                const double* __restrict__ valt, int n, const double* __restrict__ lo,
-                                const double* __restrict__ hi, const double* __restrict__ mn,
-                                const double* __restrict__ mx, const int* __restrict__ cmn,
-                                const int* __restrict__ cmx, const uint8_t* __restrict__ is_int,
-                                double* __restrict__ xl, double* __restrict__ xu, int* __restrict__ flags) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// One Jacobi pass for each column (warp per column over its A^T entries):
+// candidate bounds from every row that can bind, integer rounding,
+// acceptance thresholds.  Only column j's own bounds are read and written by
+// warp j; row activities come from the previous kernel, so the pass is
+// Jacobi.  A row whose maximum activity cannot exceed hi (minimum cannot
+// fall below lo) implies no bound from that side and is skipped.
+__global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restrict__ rpt, const int* __restrict__ colt,
+                                                            const double* __restrict__ valt, int n,
+                                                            const double* __restrict__ lo,
+                                                            const double* __restrict__ hi,
+                                                            const double* __restrict__ mn,
+                                                            const double* __restrict__ mx,
+                                                            const int* __restrict__ cmn,
+                                                            const int* __restrict__ cmx,
+                                                            const uint8_t* __restrict__ is_int,
+                                                            double* __restrict__ xl, double* __restrict__ xu,
+                                                            int* __restrict__ flags) {
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (j >= n) return;
   const double oxl = xl[j], oxu = xu[j];
   double nlo = oxl, nhi = oxu;
-  for (int e = rpt[j]; e < rpt[j + 1]; e++) {
+  for (int e = rpt[j] + lane; e < rpt[j + 1]; e += 32) {
     const int i = colt[e];
     const double a = valt[e];
     const double lmin = a > 0.0 ? oxl : oxu;
     const double lmax = a > 0.0 ? oxu : oxl;
-    if (isfinite(hi[i])) {  // a x_j <= hi - (min activity of the other entries)
-      const bool ok = isinf(lmin) ? (cmn[i] == 1) : (cmn[i] == 0);
+    const double hii = hi[i], loi = lo[i], mni = mn[i], mxi = mx[i];
+    const int cmni = cmn[i], cmxi = cmx[i];
+    if (isfinite(hii) && !(cmxi == 0 && mxi <= hii)) {  // a x_j <= hi - (min activity of the rest)
+      const bool ok = isinf(lmin) ? (cmni == 1) : (cmni == 0);
       if (ok) {
-        const double rest = isinf(lmin) ? mn[i] : __dsub_rn(mn[i], __dmul_rn(a, lmin));
-        const double b = __ddiv_rn(__dsub_rn(hi[i], rest), a);
+        const double rest = isinf(lmin) ? mni : __dsub_rn(mni, __dmul_rn(a, lmin));
+        const double b = __ddiv_rn(__dsub_rn(hii, rest), a);
         if (a > 0.0) { if (b < nhi) nhi = b; }
         else { if (b > nlo) nlo = b; }
       }
     }
-    if (isfinite(lo[i])) {  // a x_j >= lo - (max activity of the other entries)
-      const bool ok = isinf(lmax) ? (cmx[i] == 1) : (cmx[i] == 0);
+    if (isfinite(loi) && !(cmni == 0 && mni >= loi)) {  // a x_j >= lo - (max activity of the rest)
+      const bool ok = isinf(lmax) ? (cmxi == 1) : (cmxi == 0);
       if (ok) {
-        const double rest = isinf(lmax) ? mx[i] : __dsub_rn(mx[i], __dmul_rn(a, lmax));
-        const double b = __ddiv_rn(__dsub_rn(lo[i], rest), a);
+        const double rest = isinf(lmax) ? mxi : __dsub_rn(mxi, __dmul_rn(a, lmax));
+        const double b = __ddiv_rn(__dsub_rn(loi, rest), a);
         if (a > 0.0) { if (b > nlo) nlo = b; }
         else { if (b < nhi) nhi = b; }
       }
     }
   }
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const double ol = __shfl_down_sync(0xffffffffu, nlo, w), oh = __shfl_down_sync(0xffffffffu, nhi, w);
+    if (ol > nlo) nlo = ol;
+    if (oh < nhi) nhi = oh;
+  }
+  if (lane != 0) return;
   double l = nlo, u = nhi, nxl = oxl, nxu = oxu;
   int changed = 0;
   if (is_int[j]) {
@@ -158,23 +201,42 @@ __global__ void k_col_propagate(const int* __restrict__ rpt, const int* __restri
   if (nxl > __dadd_rn(nxu, 1e-6)) atomicOr(flags + 1, 1);
 }
 
-// Reduction, per row: fold fixed columns into the bounds (entry order),
-// activity of the free columns, keep flag (non-redundant, non-empty), kept
-// entry count, violated emptied rows.
-__global__ void k_reduce_rows(const int* __restrict__ rp, const int* __restrict__ col,
-                              const double* __restrict__ val, int m, const double* __restrict__ lo,
-                              const double* __restrict__ hi, const double* __restrict__ xl,
-                              const double* __restrict__ xu, int* __restrict__ keep, int* __restrict__ knz,
-                              double* __restrict__ lo_r, double* __restrict__ hi_r, int* __restrict__ flags) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Reduced-LP rows (warp per row): fixed columns folded into the row bounds,
+// activity range over the free columns (lane order), redundancy test.
+__global__ void __launch_bounds__(kThreads) k_reduce_rows(const int* __restrict__ rp, const int* __restrict__ col,
+                                                          const double* __restrict__ val, int m,
+                                                          const double* __restrict__ lo,
+                                                          const double* __restrict__ hi,
+                                                          const double* __restrict__ xl,
+                                                          const double* __restrict__ xu, int* __restrict__ keep,
+                                                          int* __restrict__ knz, double* __restrict__ lo_r,
+                                                          double* __restrict__ hi_r, int* __restrict__ flags) {
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= m) return;
-  double shift = 0.0;
-  int kept = 0;
-  for (int e = rp[i]; e < rp[i + 1]; e++) {
+  double shift = 0.0, a_mn = 0.0, a_mx = 0.0;
+  int kept = 0, c_mn = 0, c_mx = 0;
+  for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
     const int j = col[e];
-    if (xl[j] == xu[j]) shift = __dadd_rn(shift, __dmul_rn(val[e], xl[j]));
-    else kept++;
+    const double a = val[e], l = xl[j], u = xu[j];
+    if (l == u) {
+      shift = __dadd_rn(shift, __dmul_rn(a, l));
+    } else {
+      kept++;
+      const double lmin = a > 0.0 ? l : u;
+      const double lmax = a > 0.0 ? u : l;
+      if (isinf(lmin)) c_mn++;
+      else a_mn = __dadd_rn(a_mn, __dmul_rn(a, lmin));
+      if (isinf(lmax)) c_mx++;
+      else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
+    }
   }
+  shift = lanes_total(shift);
+  a_mn = lanes_total(a_mn);
+  a_mx = lanes_total(a_mx);
+  kept = lanes_count(kept);
+  c_mn = lanes_count(c_mn);
+  c_mx = lanes_count(c_mx);
+  if (lane != 0) return;
   const double l = __dsub_rn(lo[i], shift), u = __dsub_rn(hi[i], shift);
   lo_r[i] = l;
   hi_r[i] = u;
@@ -183,19 +245,6 @@ __global__ void k_reduce_rows(const int* __restrict__ rp, const int* __restrict_
     keep[i] = 0;
     knz[i] = 0;
     return;
-  }
-  double a_mn = 0.0, a_mx = 0.0;
-  int c_mn = 0, c_mx = 0;
-  for (int e = rp[i]; e < rp[i + 1]; e++) {
-    const int j = col[e];
-    if (xl[j] == xu[j]) continue;
-    const double a = val[e];
-    const double lmin = a > 0.0 ? xl[j] : xu[j];
-    const double lmax = a > 0.0 ? xu[j] : xl[j];
-    if (isinf(lmin)) c_mn++;
-    else a_mn = __dadd_rn(a_mn, __dmul_rn(a, lmin));
-    if (isinf(lmax)) c_mx++;
-    else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
   }
   const bool lo_red = !isfinite(l) || (c_mn == 0 && a_mn >= l);
   const bool hi_red = !isfinite(u) || (c_mx == 0 && a_mx <= u);
@@ -210,27 +259,41 @@ __global__ void k_col_keep(int n, const double* __restrict__ xl, const double* _
 }
 
 // kept rows: entries of free columns, renumbered, in the original order
-__global__ void k_scatter_rows(const int* __restrict__ rp, const int* __restrict__ col,
-                               const double* __restrict__ val, int m, const int* __restrict__ keep,
-                               const int* __restrict__ newrow, const int* __restrict__ rp_r,
-                               const int* __restrict__ newcol, const int* __restrict__ keepc,
-                               const double* __restrict__ lo_t, const double* __restrict__ hi_t,
-                               int* __restrict__ col_r, double* __restrict__ val_r, double* __restrict__ lo_r,
-                               double* __restrict__ hi_r, int* __restrict__ row_map) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// (warp per row; a ballot orders each 32-entry slice)
+__global__ void __launch_bounds__(kThreads) k_scatter_rows(const int* __restrict__ rp, const int* __restrict__ col,
+                                                           const double* __restrict__ val, int m,
+                                                           const int* __restrict__ keep,
+                                                           const int* __restrict__ newrow,
+                                                           const int* __restrict__ rp_r,
+                                                           const int* __restrict__ newcol,
+                                                           const int* __restrict__ keepc,
+                                                           const double* __restrict__ lo_t,
+                                                           const double* __restrict__ hi_t,
+                                                           int* __restrict__ col_r, double* __restrict__ val_r,
+                                                           double* __restrict__ lo_r, double* __restrict__ hi_r,
+                                                           int* __restrict__ row_map) {
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= m || !keep[i]) return;
   const int r = newrow[i];
   int k = rp_r[r];
-  for (int e = rp[i]; e < rp[i + 1]; e++) {
-    const int j = col[e];
-    if (!keepc[j]) continue;
-    col_r[k] = newcol[j];
-    val_r[k] = val[e];
-    k++;
+  for (int e0 = rp[i]; e0 < rp[i + 1]; e0 += 32) {
+    const int e = e0 + lane;
+    const bool in = e < rp[i + 1];
+    const int j = in ? col[e] : 0;
+    const bool take = in && keepc[j];
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (take) {
+      const int pos = k + __popc(bal & ((1u << lane) - 1u));
+      col_r[pos] = newcol[j];
+      val_r[pos] = val[e];
+    }
+    k += __popc(bal);
   }
-  lo_r[r] = lo_t[i];
-  hi_r[r] = hi_t[i];
-  row_map[r] = i;
+  if (lane == 0) {
+    lo_r[r] = lo_t[i];
+    hi_r[r] = hi_t[i];
+    row_map[r] = i;
+  }
 }
 
 __global__ void k_scatter_cols(int n, const int* __restrict__ keepc, const int* __restrict__ newcol,
@@ -353,9 +416,9 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
   int hflags[2] = {0, 0};
   for (int pass = 0; pass < p.max_passes; pass++) {
     SCUC_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));  // changed; flags[1] (infeasible) persists
-    if (m) k_row_activity<<<grid1(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx);
+    if (m) k_row_activity<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx);
     if (n)
-      k_col_propagate<<<grid1(n), kThreads, 0, s>>>(rpt, colt, valt, n, lo, hi, mn, mx, cmn, cmx, isint, xl, xu,
+      k_col_propagate<<<grid_w(n), kThreads, 0, s>>>(rpt, colt, valt, n, lo, hi, mn, mx, cmn, cmx, isint, xl, xu,
                                                    flags);
     SCUC_CUDA(cudaGetLastError());
     SCUC_CUDA(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -370,6 +433,8 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
   SCUC_CUDA(cudaStreamSynchronize(s));
 
   scuc_fix_info I{};
+  const auto t_prop = clk::now();
+  I.ms_propagate = std::chrono::duration<double, std::milli>(t_prop - t0).count();
   I.nfixed = (int64_t)nf;
   I.passes = passes;
   I.infeasible = infeasible;
@@ -387,7 +452,7 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     SCUC_TRY(talloc(&hi_t, m));
     SCUC_TRY(talloc(&objc, 1));
     if (m)
-      k_reduce_rows<<<grid1(m), kThreads, 0, s>>>(rp, col, val, m, lo, hi, xl, xu, keep, knz, lo_t, hi_t, flags);
+      k_reduce_rows<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, lo, hi, xl, xu, keep, knz, lo_t, hi_t, flags);
     if (n) k_col_keep<<<grid1(n), kThreads, 0, s>>>(n, xl, xu, keepc);
     k_fixed_obj<<<1, 1024, 0, s>>>(n, c, xl, xu, objc);
     SCUC_CUDA(cudaGetLastError());
@@ -439,7 +504,7 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     SCUC_CUDA(cudaMemcpyAsync(rp_dev, rpr_h.data(), (mr + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
     // row offsets of kept rows by original row index for the scatter
     if (m)
-      k_scatter_rows<<<grid1(m), kThreads, 0, s>>>(rp, col, val, m, keep, newrow, rp_dev, newcol, keepc, lo_t, hi_t,
+      k_scatter_rows<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, keep, newrow, rp_dev, newcol, keepc, lo_t, hi_t,
                                                    static_cast<int*>(d_col), static_cast<double*>(d_val),
                                                    static_cast<double*>(d_lo), static_cast<double*>(d_hi), rmap);
     if (n)
@@ -449,6 +514,8 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     if (row_map_h && mr) SCUC_CUDA(cudaMemcpyAsync(row_map_h, rmap, mr * sizeof(int), cudaMemcpyDeviceToHost, s));
     if (col_map_h && nr) SCUC_CUDA(cudaMemcpyAsync(col_map_h, cmap, nr * sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaStreamSynchronize(s));
+    const auto t_red = clk::now();
+    I.ms_reduce = std::chrono::duration<double, std::milli>(t_red - t_prop).count();
     if (reduced && !I.infeasible) {
       Handle* H = new Handle();
       const int rc = H->init_device(mr, nr, nnzr, rp_dev, static_cast<int*>(d_col), static_cast<double*>(d_val),
@@ -460,6 +527,7 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
         return rc;
       }
       *reduced = H;
+      I.ms_setup = std::chrono::duration<double, std::milli>(clk::now() - t_red).count();
     } else {
       for (void* q : {d_rp, d_col, d_val, d_c, d_xl, d_xu, d_lo, d_hi}) cudaFree(q);
     }
