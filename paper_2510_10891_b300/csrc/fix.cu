@@ -259,23 +259,25 @@ __global__ void k_col_keep(int n, const double* __restrict__ xl, const double* _
 }
 
 // kept rows: entries of free columns, renumbered, in the original order
-// (warp per row; a ballot orders each 32-entry slice)
+// (warp per row; a ballot orders each 32-entry slice).  offs[i] is the first
+// reduced entry of row i (exclusive scan of the kept counts); posr[e], when
+// given, gets the reduced position of each copied entry e.
 __global__ void __launch_bounds__(kThreads) k_scatter_rows(const int* __restrict__ rp, const int* __restrict__ col,
                                                            const double* __restrict__ val, int m,
                                                            const int* __restrict__ keep,
                                                            const int* __restrict__ newrow,
-                                                           const int* __restrict__ rp_r,
+                                                           const int* __restrict__ offs,
                                                            const int* __restrict__ newcol,
                                                            const int* __restrict__ keepc,
                                                            const double* __restrict__ lo_t,
-                                                           const double* __restrict__ hi_t,
+                                                           const double* __restrict__ hi_t, int* __restrict__ rp_r,
                                                            int* __restrict__ col_r, double* __restrict__ val_r,
                                                            double* __restrict__ lo_r, double* __restrict__ hi_r,
-                                                           int* __restrict__ row_map) {
+                                                           int* __restrict__ row_map, int* __restrict__ posr) {
   const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= m || !keep[i]) return;
   const int r = newrow[i];
-  int k = rp_r[r];
+  int k = offs[i];
   for (int e0 = rp[i]; e0 < rp[i + 1]; e0 += 32) {
     const int e = e0 + lane;
     const bool in = e < rp[i + 1];
@@ -286,13 +288,59 @@ __global__ void __launch_bounds__(kThreads) k_scatter_rows(const int* __restrict
       const int pos = k + __popc(bal & ((1u << lane) - 1u));
       col_r[pos] = newcol[j];
       val_r[pos] = val[e];
+      if (posr) posr[e] = pos;
     }
     k += __popc(bal);
   }
   if (lane == 0) {
+    rp_r[r] = offs[i];
     lo_r[r] = lo_t[i];
     hi_r[r] = hi_t[i];
     row_map[r] = i;
+  }
+}
+
+// Reduced A^T from the parent's, which is sorted by row within each column:
+// a kept column keeps its entries in kept rows, in the same order (newrow is
+// increasing), so no sort is needed.  Warp per parent column.
+__global__ void __launch_bounds__(kThreads) k_count_kept_t(const int* __restrict__ rpt, const int* __restrict__ colt,
+                                                           int n, const int* __restrict__ keepc,
+                                                           const int* __restrict__ newcol,
+                                                           const int* __restrict__ keep, int* __restrict__ cnt) {
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (j >= n || !keepc[j]) return;
+  int c = 0;
+  for (int e = rpt[j] + lane; e < rpt[j + 1]; e += 32) c += keep[colt[e]] ? 1 : 0;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if (lane == 0) cnt[newcol[j]] = c;
+}
+
+__global__ void __launch_bounds__(kThreads) k_compact_t(const int* __restrict__ rpt, const int* __restrict__ colt,
+                                                        const int* __restrict__ permt,
+                                                        const double* __restrict__ valt, int n,
+                                                        const int* __restrict__ keepc,
+                                                        const int* __restrict__ newcol,
+                                                        const int* __restrict__ keep,
+                                                        const int* __restrict__ newrow,
+                                                        const int* __restrict__ posr,
+                                                        const int* __restrict__ rpt_r, int* __restrict__ colt_r,
+                                                        int* __restrict__ permt_r, double* __restrict__ valt_r) {
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (j >= n || !keepc[j]) return;
+  int k = rpt_r[newcol[j]];
+  for (int e0 = rpt[j]; e0 < rpt[j + 1]; e0 += 32) {
+    const int e = e0 + lane;
+    const bool in = e < rpt[j + 1];
+    const int i = in ? colt[e] : 0;
+    const bool take = in && keep[i];
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (take) {
+      const int pos = k + __popc(bal & ((1u << lane) - 1u));
+      colt_r[pos] = newrow[i];
+      permt_r[pos] = posr[permt[e]];
+      valt_r[pos] = valt[e];
+    }
+    k += __popc(bal);
   }
 }
 
@@ -440,14 +488,14 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
   I.infeasible = infeasible;
   if (!infeasible && (reduced || col_map_h || row_map_h || info)) {
     // reduced LP
-    int *keep = nullptr, *knz = nullptr, *keepc = nullptr, *newrow = nullptr, *newcol = nullptr, *rpr = nullptr;
+    int *keep = nullptr, *knz = nullptr, *keepc = nullptr, *newrow = nullptr, *newcol = nullptr, *offs = nullptr;
     double *lo_t = nullptr, *hi_t = nullptr, *objc = nullptr;
     SCUC_TRY(talloc(&keep, m + 1));
     SCUC_TRY(talloc(&knz, m + 1));
     SCUC_TRY(talloc(&keepc, n + 1));
     SCUC_TRY(talloc(&newrow, m + 1));
     SCUC_TRY(talloc(&newcol, n + 1));
-    SCUC_TRY(talloc(&rpr, m + 1));
+    SCUC_TRY(talloc(&offs, m + 1));
     SCUC_TRY(talloc(&lo_t, m));
     SCUC_TRY(talloc(&hi_t, m));
     SCUC_TRY(talloc(&objc, 1));
@@ -456,80 +504,102 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     if (n) k_col_keep<<<grid1(n), kThreads, 0, s>>>(n, xl, xu, keepc);
     k_fixed_obj<<<1, 1024, 0, s>>>(n, c, xl, xu, objc);
     SCUC_CUDA(cudaGetLastError());
-    SCUC_TRY(exclusive_scan(keep, m, newrow, s));
-    SCUC_TRY(exclusive_scan(keepc, n, newcol, s));
-    int mr = 0, nr = 0;
+    SCUC_TRY(exclusive_scan(keep, m, newrow, s));   // reduced row of each kept row; newrow[m] = rows kept
+    SCUC_TRY(exclusive_scan(keepc, n, newcol, s));  // reduced column of each free column
+    SCUC_TRY(exclusive_scan(knz, m, offs, s));      // first reduced entry of each kept row; offs[m] = entries
+    int mr = 0, nr = 0, nnzr = 0;
     SCUC_CUDA(cudaMemcpyAsync(&mr, newrow + m, sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaMemcpyAsync(&nr, newcol + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaMemcpyAsync(&nnzr, offs + m, sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaMemcpyAsync(&I.obj_const, objc, sizeof(double), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaStreamSynchronize(s));
     I.infeasible = hflags[1] ? 1 : 0;
     I.n_fixed_cols = n - nr;
-    // kept-entry counts of the kept rows, in kept-row order, then scan
-    std::vector<int> knz_h(m), keep_h(m);
-    if (m) {
-      SCUC_CUDA(cudaMemcpyAsync(knz_h.data(), knz, m * sizeof(int), cudaMemcpyDeviceToHost, s));
-      SCUC_CUDA(cudaMemcpyAsync(keep_h.data(), keep, m * sizeof(int), cudaMemcpyDeviceToHost, s));
-      SCUC_CUDA(cudaStreamSynchronize(s));
-    }
-    std::vector<int> rpr_h(mr + 1, 0);
-    {
-      int r = 0;
-      for (int i = 0; i < m; i++)
-        if (keep_h[i]) {
-          rpr_h[r + 1] = rpr_h[r] + knz_h[i];
-          r++;
-        }
-    }
-    const int64_t nnzr = rpr_h[mr];
     I.m_red = mr;
     I.n_red = nr;
     I.nnz_red = nnzr;
-    // device arrays of the reduced LP (ownership passes to the new handle)
+    // device arrays of the reduced LP and its transpose (ownership passes to the new handle)
     void *d_rp = nullptr, *d_col = nullptr, *d_val = nullptr, *d_c = nullptr, *d_xl = nullptr, *d_xu = nullptr,
-         *d_lo = nullptr, *d_hi = nullptr;
-    int *rmap = nullptr, *cmap = nullptr;
-    SCUC_TRY(dev_alloc_bytes(&d_rp, (mr + 1) * sizeof(int)));
-    SCUC_TRY(dev_alloc_bytes(&d_col, nnzr * sizeof(int)));
-    SCUC_TRY(dev_alloc_bytes(&d_val, nnzr * sizeof(double)));
-    SCUC_TRY(dev_alloc_bytes(&d_c, nr * sizeof(double)));
-    SCUC_TRY(dev_alloc_bytes(&d_xl, nr * sizeof(double)));
-    SCUC_TRY(dev_alloc_bytes(&d_xu, nr * sizeof(double)));
-    SCUC_TRY(dev_alloc_bytes(&d_lo, mr * sizeof(double)));
-    SCUC_TRY(dev_alloc_bytes(&d_hi, mr * sizeof(double)));
+         *d_lo = nullptr, *d_hi = nullptr, *d_rpt = nullptr, *d_colt = nullptr, *d_permt = nullptr,
+         *d_valt = nullptr;
+    std::vector<void*> owned;
+    struct FreeOwned {
+      std::vector<void*>& v;
+      ~FreeOwned() {
+        for (void* q : v) cudaFree(q);
+      }
+    } free_owned{owned};
+    auto oalloc = [&](void** q, size_t bytes) -> int {
+      SCUC_TRY(dev_alloc_bytes(q, bytes));
+      owned.push_back(*q);
+      return SCUC_OK;
+    };
+    SCUC_TRY(oalloc(&d_rp, (mr + 1) * sizeof(int)));
+    SCUC_TRY(oalloc(&d_col, nnzr * sizeof(int)));
+    SCUC_TRY(oalloc(&d_val, nnzr * sizeof(double)));
+    SCUC_TRY(oalloc(&d_c, nr * sizeof(double)));
+    SCUC_TRY(oalloc(&d_xl, nr * sizeof(double)));
+    SCUC_TRY(oalloc(&d_xu, nr * sizeof(double)));
+    SCUC_TRY(oalloc(&d_lo, mr * sizeof(double)));
+    SCUC_TRY(oalloc(&d_hi, mr * sizeof(double)));
+    const bool want_t = reduced && !I.infeasible;
+    int *rmap = nullptr, *cmap = nullptr, *posr = nullptr, *cntr = nullptr;
     SCUC_TRY(talloc(&rmap, mr));
     SCUC_TRY(talloc(&cmap, nr));
+    if (want_t) SCUC_TRY(talloc(&posr, nnz));
     int* rp_dev = static_cast<int*>(d_rp);
-    SCUC_CUDA(cudaMemcpyAsync(rp_dev, rpr_h.data(), (mr + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-    // row offsets of kept rows by original row index for the scatter
     if (m)
-      k_scatter_rows<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, keep, newrow, rp_dev, newcol, keepc, lo_t, hi_t,
-                                                   static_cast<int*>(d_col), static_cast<double*>(d_val),
-                                                   static_cast<double*>(d_lo), static_cast<double*>(d_hi), rmap);
+      k_scatter_rows<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, keep, newrow, offs, newcol, keepc, lo_t, hi_t,
+                                                   rp_dev, static_cast<int*>(d_col), static_cast<double*>(d_val),
+                                                   static_cast<double*>(d_lo), static_cast<double*>(d_hi), rmap,
+                                                   posr);
+    SCUC_CUDA(cudaMemcpyAsync(rp_dev + mr, offs + m, sizeof(int), cudaMemcpyDeviceToDevice, s));
     if (n)
       k_scatter_cols<<<grid1(n), kThreads, 0, s>>>(n, keepc, newcol, c, xl, xu, static_cast<double*>(d_c),
                                                    static_cast<double*>(d_xl), static_cast<double*>(d_xu), cmap);
     SCUC_CUDA(cudaGetLastError());
+    std::vector<int> rp_h, rpt_h;
+    if (want_t) {
+      SCUC_TRY(oalloc(&d_rpt, (nr + 1) * sizeof(int)));
+      SCUC_TRY(oalloc(&d_colt, nnzr * sizeof(int)));
+      SCUC_TRY(oalloc(&d_permt, nnzr * sizeof(int)));
+      SCUC_TRY(oalloc(&d_valt, nnzr * sizeof(double)));
+      SCUC_TRY(talloc(&cntr, nr + 1));
+      int* rpt_r = static_cast<int*>(d_rpt);
+      if (n) k_count_kept_t<<<grid_w(n), kThreads, 0, s>>>(rpt, colt, n, keepc, newcol, keep, cntr);
+      SCUC_CUDA(cudaGetLastError());
+      SCUC_TRY(exclusive_scan(cntr, nr, rpt_r, s));
+      if (n)
+        k_compact_t<<<grid_w(n), kThreads, 0, s>>>(rpt, colt, permt, valt, n, keepc, newcol, keep, newrow, posr,
+                                                   rpt_r, static_cast<int*>(d_colt), static_cast<int*>(d_permt),
+                                                   static_cast<double*>(d_valt));
+      SCUC_CUDA(cudaGetLastError());
+      rp_h.resize(mr + 1);
+      rpt_h.resize(nr + 1);
+      SCUC_CUDA(cudaMemcpyAsync(rp_h.data(), rp_dev, (mr + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCUC_CUDA(cudaMemcpyAsync(rpt_h.data(), rpt_r, (nr + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
     if (row_map_h && mr) SCUC_CUDA(cudaMemcpyAsync(row_map_h, rmap, mr * sizeof(int), cudaMemcpyDeviceToHost, s));
     if (col_map_h && nr) SCUC_CUDA(cudaMemcpyAsync(col_map_h, cmap, nr * sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaStreamSynchronize(s));
     const auto t_red = clk::now();
     I.ms_reduce = std::chrono::duration<double, std::milli>(t_red - t_prop).count();
-    if (reduced && !I.infeasible) {
+    if (want_t) {
+      owned.clear();  // the new handle frees them, also when its set-up fails
       Handle* H = new Handle();
+      const DevTranspose T{static_cast<int*>(d_rpt), static_cast<int*>(d_colt), static_cast<int*>(d_permt),
+                           static_cast<double*>(d_valt), &rp_h, &rpt_h};
       const int rc = H->init_device(mr, nr, nnzr, rp_dev, static_cast<int*>(d_col), static_cast<double*>(d_val),
                                     static_cast<double*>(d_c), static_cast<double*>(d_xl),
                                     static_cast<double*>(d_xu), static_cast<double*>(d_lo),
-                                    static_cast<double*>(d_hi), user);
+                                    static_cast<double*>(d_hi), user, &T);
       if (rc != SCUC_OK) {
         delete H;
         return rc;
       }
       *reduced = H;
       I.ms_setup = std::chrono::duration<double, std::milli>(clk::now() - t_red).count();
-    } else {
-      for (void* q : {d_rp, d_col, d_val, d_c, d_xl, d_xu, d_lo, d_hi}) cudaFree(q);
     }
   }
   I.ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();

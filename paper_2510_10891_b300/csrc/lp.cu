@@ -146,31 +146,24 @@ int build_partition(const std::vector<int>& rp, int m, Partition* P) {
 }
 
 // exclusive scan of n ints into out[0..n] (out[n] = total), recursive
+// out[0..n] = exclusive prefix sums of in[0..n-1], out[n] the total; stream
+// ordered on s, no host synchronisation
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s) {
   const int nb = (n + kScan - 1) / kScan;
-  int *bsum = nullptr, *boff = nullptr;
-  SCUC_TRY(dalloc(&bsum, nb));
-  SCUC_TRY(dalloc(&boff, nb + 1));
+  int* scratch = nullptr;  // block sums (nb), their offsets (nb + 1)
+  SCUC_CUDA(cudaMallocAsync((void**)&scratch, (2 * (size_t)nb + 2) * sizeof(int), s));
+  int *bsum = scratch, *boff = scratch + nb;
   if (n > 0) k_scan_block<<<nb, kScan, 0, s>>>(in, n, out, bsum);
   SCUC_CUDA(cudaGetLastError());
+  int rc = SCUC_OK;
   if (nb > 1) {
-    SCUC_TRY(exclusive_scan(bsum, nb, boff, s));
-    k_scan_add<<<nb, kScan, 0, s>>>(out, n, boff);
-    SCUC_CUDA(cudaGetLastError());
+    rc = exclusive_scan(bsum, nb, boff, s);
+    if (rc == SCUC_OK) k_scan_add<<<nb, kScan, 0, s>>>(out, n, boff);
   }
-  // total
-  int total = 0;
-  if (n > 0) {
-    int last_in = 0, last_out = 0;
-    SCUC_CUDA(cudaMemcpyAsync(&last_in, in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SCUC_CUDA(cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SCUC_CUDA(cudaStreamSynchronize(s));
-    total = last_in + last_out;
-  }
-  SCUC_CUDA(cudaMemcpyAsync(out + n, &total, sizeof(int), cudaMemcpyHostToDevice, s));
-  SCUC_CUDA(cudaStreamSynchronize(s));
-  cudaFree(bsum);
-  cudaFree(boff);
+  if (rc == SCUC_OK) k_scan_total<<<1, 32, 0, s>>>(in, n, out);
+  cudaFreeAsync(scratch, s);
+  SCUC_TRY(rc);
+  SCUC_CUDA(cudaGetLastError());
   return SCUC_OK;
 }
 
@@ -311,14 +304,21 @@ int Handle::begin(int32_t m_, int32_t n_, int64_t nnz_, cudaStream_t user_) {
 
 // Adopts device arrays (allocated by the library; ownership moves to the
 // handle) that already satisfy the input rules, then builds the device state.
+// With t, the transpose (columns sorted by row, permt the CSR position of
+// each entry) and both row-pointer arrays are adopted as well.
 int Handle::init_device(int32_t m_, int32_t n_, int64_t nnz_, int* d_rp, int* d_col, double* d_val,
                         double* d_c, double* d_xl, double* d_xu, double* d_lo, double* d_hi,
-                        cudaStream_t user_) {
+                        cudaStream_t user_, const DevTranspose* t) {
   rp = d_rp; col = d_col; val = d_val; c = d_c; xl = d_xl; xu = d_xu; lo = d_lo; hi = d_hi;
   for (void* p : {(void*)d_rp, (void*)d_col, (void*)d_val, (void*)d_c, (void*)d_xl, (void*)d_xu,
                   (void*)d_lo, (void*)d_hi})
     allocs.push_back(p);
+  if (t) {
+    rpt = t->rpt; colt = t->colt; permt = t->permt; valt = t->valt;
+    for (void* p : {(void*)rpt, (void*)colt, (void*)permt, (void*)valt}) allocs.push_back(p);
+  }
   SCUC_TRY(begin(m_, n_, nnz_, user_));
+  if (t) return setup_solver(*t->rp_h, *t->rpt_h);
   std::vector<int> rp32(m + 1);
   SCUC_CUDA(cudaMemcpyAsync(rp32.data(), rp, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, work));
   SCUC_CUDA(cudaStreamSynchronize(work));
@@ -327,6 +327,13 @@ int Handle::init_device(int32_t m_, int32_t n_, int64_t nnz_, int* d_rp, int* d_
 
 // transpose, partitions and solver buffers (data already on the device)
 int Handle::setup_device(const std::vector<int>& rp32) {
+  std::vector<int> rpt_h;
+  SCUC_TRY(build_transpose(&rpt_h));
+  return setup_solver(rp32, rpt_h);
+}
+
+// A^T in CSR form: count, scan, scatter, per-column sort by row, gather values
+int Handle::build_transpose(std::vector<int>* rpt_out) {
   cudaStream_t s = work;
 
   // transpose: count, scan, scatter, per-column sort by row, gather values
@@ -368,7 +375,13 @@ int Handle::setup_device(const std::vector<int>& rp32) {
   }
   if (nnz) k_gather_t<<<grid_for(nnz), kBlock, 0, s>>>(permt, nnz, val, valt);
   SCUC_CUDA(cudaGetLastError());
+  *rpt_out = std::move(rpt_h);
+  return SCUC_OK;
+}
 
+// partitions and solver buffers; rp32 / rpt_h: row pointers of A and A^T
+int Handle::setup_solver(const std::vector<int>& rp32, const std::vector<int>& rpt_h) {
+  cudaStream_t s = work;
   SCUC_TRY(build_partition(rp32, m, &pA));
   SCUC_TRY(build_partition(rpt_h, n, &pT));
   for (Partition* P : {&pA, &pT})

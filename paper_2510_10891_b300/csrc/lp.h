@@ -8,6 +8,14 @@ namespace scuc {
 
 struct DevLP;  // device view of a handle (lp_kernels.cuh)
 
+// A^T of a matrix built elsewhere (Handle::init_device adopts the arrays)
+struct DevTranspose {
+  int *rpt, *colt, *permt;
+  double* valt;
+  const std::vector<int>* rp_h;   // row pointers of A (m + 1)
+  const std::vector<int>* rpt_h;  // row pointers of A^T (n + 1)
+};
+
 // host plan of a Partition
 struct PartPlan {
   std::vector<int4> listx, desc;
@@ -72,8 +80,11 @@ struct Handle {
            const double* lo, const double* hi, cudaStream_t user);
   int begin(int32_t m, int32_t n, int64_t nnz, cudaStream_t user);
   int init_device(int32_t m, int32_t n, int64_t nnz, int* d_rp, int* d_col, double* d_val, double* d_c,
-                  double* d_xl, double* d_xu, double* d_lo, double* d_hi, cudaStream_t user);
+                  double* d_xl, double* d_xu, double* d_lo, double* d_hi, cudaStream_t user,
+                  const DevTranspose* t = nullptr);
   int setup_device(const std::vector<int>& rp32);
+  int build_transpose(std::vector<int>* rpt_h);
+  int setup_solver(const std::vector<int>& rp32, const std::vector<int>& rpt_h);
   int enter();
   int leave();
   DevLP dev() const;

@@ -120,6 +120,11 @@ __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__
   if (i < n) out[i] += boff[blockIdx.x];
 }
 
+// out[n] = the total
+__global__ void k_scan_total(const int* __restrict__ in, int n, int* __restrict__ out) {
+  if (threadIdx.x == 0) out[n] = n > 0 ? in[n - 1] + out[n - 1] : 0;
+}
+
 // --------------------------- scaling -------------------------------------
 __global__ void k_fill(double* __restrict__ a, int na, double* __restrict__ b, int nb, double v) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -34,6 +34,24 @@ def _oracle_round(inst, lp_d, x, tau, t_first=1):
     return fix, nf, pl, pu, passes
 
 
+def _same_transpose(P, reduced, exported):
+    """The reduced LP's A^T, compacted on the device from the parent's, is the
+    one a new handle builds from the exported LP (sorted by row within each
+    column): A^T y and A x agree bit for bit."""
+    import torch
+    fresh = P.LP(exported)
+    g = torch.Generator().manual_seed(7)
+    y = torch.randn(reduced.m, generator=g, dtype=torch.float64).cuda()
+    x = torch.randn(reduced.n, generator=g, dtype=torch.float64).cuda()
+    outs = {}
+    for name, h in (("reduced", reduced), ("fresh", fresh)):
+        outs[name] = (h.matvec(y, torch.empty(reduced.n, dtype=torch.float64, device="cuda"), transpose=True),
+                      h.matvec(x, torch.empty(reduced.m, dtype=torch.float64, device="cuda")))
+    for a, b in zip(outs["reduced"], outs["fresh"]):
+        assert torch.equal(a, b)
+    fresh.close()
+
+
 @pytest.mark.parametrize("name,tau,t_first", [("scuc14", 0.1, 1), ("scuc14", 0.3, 0),
                                               ("scuc2k", 0.1, 1), ("scuc2k", 0.02, 1)])
 def test_fix_propagate_reduce_parity(P, name, tau, t_first):
@@ -65,6 +83,7 @@ def test_fix_propagate_reduce_parity(P, name, tau, t_first):
     g = r["reduced"].export()
     for k in ("row_ptr", "col", "val", "c", "xl", "xu", "lo", "hi"):
         np.testing.assert_array_equal(g[k], red[k], err_msg=k)
+    _same_transpose(P, r["reduced"], g)
     # the reduced LP solves; small case: to the oracle's optimum, large case:
     # certified by the oracle's KKT evaluator on the reduced LP
     if name == "scuc14":
@@ -144,3 +163,4 @@ def test_fix_propagate_full_size_13k(P):
     assert (gi["m_red"], gi["n_red"], gi["nnz_red"]) == (red["m"], red["n"], len(red["val"]))
     np.testing.assert_array_equal(r["row_map"], rmap)
     np.testing.assert_array_equal(r["col_map"], cmap)
+    _same_transpose(P, r["reduced"], r["reduced"].export())
