@@ -94,14 +94,27 @@ __device__ __forceinline__ int lanes_count(int c) { return __reduce_add_sync(0xf
 
 // Activity range of each row over the current bounds: finite parts in the
 // lane order above, plus the number of infinite contributions (warp per row).
+// After the first pass a row is recomputed only when one of its columns
+// changed bounds in the previous pass (chg); otherwise its activity range is
+// the one already stored.  dirty[i] records whether row i was recomputed.
 __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict__ rp, const int* __restrict__ col,
                                                            const double* __restrict__ val, int m,
                                                            const double* __restrict__ xl,
                                                            const double* __restrict__ xu, double* __restrict__ mn,
                                                            double* __restrict__ mx, int* __restrict__ cmn,
-                                                           int* __restrict__ cmx) {
+                                                           int* __restrict__ cmx, const uint8_t* __restrict__ chg,
+                                                           uint8_t* __restrict__ dirty, int first) {
   const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= m) return;
+  if (!first) {
+    bool any = false;
+    for (int e0 = rp[i]; e0 < rp[i + 1] && !any; e0 += 32) {
+      const int e = e0 + lane;
+      any = __any_sync(0xffffffffu, e < rp[i + 1] && chg[col[e]]);
+    }
+    if (lane == 0) dirty[i] = any ? 1 : 0;
+    if (!any) return;
+  }
   double a_mn = 0.0, a_mx = 0.0;
   int c_mn = 0, c_mx = 0;
   for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
@@ -131,7 +144,11 @@ __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict
 // acceptance thresholds.  Only column j's own bounds are read and written by
 // warp j; row activities come from the previous kernel, so the pass is
 // Jacobi.  A row whose maximum activity cannot exceed hi (minimum cannot
-// fall below lo) implies no bound from that side and is skipped.
+// fall below lo) implies no bound from that side and is skipped.  After the
+// first pass a column whose own bounds did not change in the previous pass
+// (chg) and none of whose rows were recomputed (dirty) would repeat the
+// previous pass's candidates and decisions exactly, so it is skipped;
+// chg[j] then records whether column j changed in this pass.
 __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restrict__ rpt, const int* __restrict__ colt,
                                                             const double* __restrict__ valt, int n,
                                                             const double* __restrict__ lo,
@@ -142,9 +159,19 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
                                                             const int* __restrict__ cmx,
                                                             const uint8_t* __restrict__ is_int,
                                                             double* __restrict__ xl, double* __restrict__ xu,
-                                                            int* __restrict__ flags) {
+                                                            int* __restrict__ flags,
+                                                            const uint8_t* __restrict__ dirty,
+                                                            uint8_t* __restrict__ chg, int first) {
   const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (j >= n) return;
+  if (!first && !chg[j]) {
+    bool any = false;
+    for (int e0 = rpt[j]; e0 < rpt[j + 1] && !any; e0 += 32) {
+      const int e = e0 + lane;
+      any = __any_sync(0xffffffffu, e < rpt[j + 1] && dirty[colt[e]]);
+    }
+    if (!any) return;  // chg[j] stays 0
+  }
   const double oxl = xl[j], oxu = xu[j];
   double nlo = oxl, nhi = oxu;
   for (int e = rpt[j] + lane; e < rpt[j + 1]; e += 32) {
@@ -198,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
     xu[j] = nxu;
     atomicOr(flags + 0, 1);
   }
+  chg[j] = (uint8_t)changed;
   if (nxl > __dadd_rn(nxu, 1e-6)) atomicOr(flags + 1, 1);
 }
 
@@ -456,18 +484,23 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
   // F3: Jacobi propagation
   double *mn = nullptr, *mx = nullptr;
   int *cmn = nullptr, *cmx = nullptr;
+  uint8_t *chg = nullptr, *dirty = nullptr;
   SCUC_TRY(talloc(&mn, m));
   SCUC_TRY(talloc(&mx, m));
   SCUC_TRY(talloc(&cmn, m));
   SCUC_TRY(talloc(&cmx, m));
+  SCUC_TRY(talloc(&chg, n));
+  SCUC_TRY(talloc(&dirty, m));
   int passes = 0, infeasible = 0;
   int hflags[2] = {0, 0};
   for (int pass = 0; pass < p.max_passes; pass++) {
     SCUC_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));  // changed; flags[1] (infeasible) persists
-    if (m) k_row_activity<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx);
+    const int first = pass == 0 ? 1 : 0;
+    if (m)
+      k_row_activity<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx, chg, dirty, first);
     if (n)
       k_col_propagate<<<grid_w(n), kThreads, 0, s>>>(rpt, colt, valt, n, lo, hi, mn, mx, cmn, cmx, isint, xl, xu,
-                                                   flags);
+                                                   flags, dirty, chg, first);
     SCUC_CUDA(cudaGetLastError());
     SCUC_CUDA(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaStreamSynchronize(s));
