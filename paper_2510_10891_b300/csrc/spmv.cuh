@@ -122,20 +122,20 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 // Partial sum of val[e] * x[col[e]] for e = a + li, a + li + nl, ... < z:
 // consecutive lanes take consecutive entries, so one warp-wide gather touches
 // neighbouring columns (rows of these matrices list their columns in
-// increasing order, mostly a few apart).  U entries in flight per thread and
-// NA accumulators, combined in a fixed tree: eight and eight for FP32
-// values, four and two for FP64 (measured on the 13k-bus A^T).  The group
-// size nl is a compile-time constant, so the U loads of a round address
-// their entries with immediate offsets from one pointer.
-template <typename VT, int nl>
-__device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* __restrict__ val,
-                                        const VT* __restrict__ x, int a, int z, int li) {
-  constexpr int U = sizeof(VT) == 4 ? 8 : 4;
-  constexpr int NA = sizeof(VT) == 4 ? 8 : 2;
+// increasing order, mostly a few apart).  Entries go in batches of U per
+// thread whose loads are all issued before the first product; entry e + u*nl
+// of a batch goes to accumulator u mod NA, and the NA accumulators are
+// combined in a fixed tree.  PRED: the last partial batch is one predicated
+// batch (a row of 100 entries over 16 threads is then a single batch);
+// otherwise its entries are added one dependent load at a time into the
+// first accumulator.  Measured on the 13k-bus A^T: U = NA = 8 with
+// predication for FP32 values, U = 4, NA = 2 without it for FP64.
+template <typename VT, int U, int NA, bool PRED>
+__device__ __forceinline__ VT batched_dot(const int* __restrict__ col, const VT* __restrict__ val,
+                                          const VT* __restrict__ x, int e, int z, int nl) {
   VT s[NA];
 #pragma unroll
   for (int q = 0; q < NA; q++) s[q] = VT(0);
-  int e = a + li;
   for (; e + (U - 1) * nl < z; e += U * nl) {
     int c[U];
     VT v[U];
@@ -147,12 +147,35 @@ __device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* _
 #pragma unroll
     for (int u = 0; u < U; u++) s[u % NA] = fma_t(v[u], ldg(x + c[u]), s[u % NA]);
   }
-  for (; e < z; e += nl) s[0] = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s[0]);
+  if (!PRED) {
+    for (; e < z; e += nl) s[0] = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s[0]);
+  } else if (e < z) {
+    int c[U];
+    VT v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int q = e + u * nl;
+      c[u] = q < z ? ldcs(col + q) : -1;
+      v[u] = q < z ? ldcs(val + q) : VT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (c[u] >= 0) s[u % NA] = fma_t(v[u], ldg(x + c[u]), s[u % NA]);
+  }
 #pragma unroll
   for (int w = NA / 2; w > 0; w >>= 1)
 #pragma unroll
     for (int q = 0; q < w; q++) s[q] += s[q + w];
   return s[0];
+}
+
+// The group size nl a compile-time constant (FP32 values: the loads of a
+// batch address their entries with immediate offsets from one pointer).
+template <typename VT, int nl>
+__device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* __restrict__ val,
+                                        const VT* __restrict__ x, int a, int z, int li) {
+  return batched_dot<VT, sizeof(VT) == 4 ? 8 : 4, sizeof(VT) == 4 ? 8 : 2, sizeof(VT) == 4>(col, val, x,
+                                                                                               a + li, z, nl);
 }
 
 // The same with the group size known only at run time (measured faster for
@@ -160,59 +183,21 @@ __device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* _
 template <typename VT>
 __device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT* __restrict__ val,
                                            const VT* __restrict__ x, int a, int z, int li, int nl) {
-  constexpr int U = sizeof(VT) == 4 ? 8 : 4;
-  constexpr int NA = sizeof(VT) == 4 ? 8 : 2;
-  VT s[NA];
-#pragma unroll
-  for (int q = 0; q < NA; q++) s[q] = VT(0);
-  int e = a + li;
-  for (; e + (U - 1) * nl < z; e += U * nl) {
-    int c[U];
-    VT v[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      c[u] = ldcs(col + e + u * nl);
-      v[u] = ldcs(val + e + u * nl);
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) s[u % NA] = fma_t(v[u], ldg(x + c[u]), s[u % NA]);
-  }
-  for (; e < z; e += nl) s[0] = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), s[0]);
-#pragma unroll
-  for (int w = NA / 2; w > 0; w >>= 1)
-#pragma unroll
-    for (int q = 0; q < w; q++) s[q] += s[q + w];
-  return s[0];
+  return batched_dot<VT, sizeof(VT) == 4 ? 8 : 4, sizeof(VT) == 4 ? 8 : 2, sizeof(VT) == 4>(col, val, x,
+                                                                                               a + li, z, nl);
 }
 
 // One warp per chunk of a long row (chunk launch): chunk w = blockIdx.x *
-// (kBlock / 32) + warp; eight lane-strided entries in flight per lane; eight
-// accumulators combined in a fixed order, then a fixed warp tree; the sum
-// goes to part.cpart[w] in FP64.
+// (kBlock / 32) + warp; batches of eight lane-strided entries per lane (the
+// last one as above), eight accumulators combined in a fixed tree, then a
+// fixed warp tree; the sum goes to part.cpart[w] in FP64.
 template <typename VT>
 __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT* __restrict__ val,
                                            const VT* __restrict__ x, const Partition& part) {
-  constexpr int U = 8;
   const int w = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= part.nchunk) return;
   const int2 c = part.chunks[w];
-  VT acc[U];
-#pragma unroll
-  for (int u = 0; u < U; u++) acc[u] = VT(0);
-  int e = c.x + lane;
-  for (; e + 32 * (U - 1) < c.y; e += 32 * U) {
-    int cc[U];
-    VT vv[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      cc[u] = ldcs(col + e + 32 * u);
-      vv[u] = ldcs(val + e + 32 * u);
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) acc[u] = fma_t(vv[u], ldg(x + cc[u]), acc[u]);
-  }
-  for (; e < c.y; e += 32) acc[0] = fma_t(ldcs(val + e), ldg(x + ldcs(col + e)), acc[0]);
-  VT s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  VT s = batched_dot<VT, 8, 8, sizeof(VT) == 4>(col, val, x, c.x + lane, c.y, 32);
   s = warp_sum(s);
   if (lane == 0) part.cpart[w] = (double)s;
 }
