@@ -128,8 +128,10 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 // combined in a fixed tree.  PRED: the last partial batch is one predicated
 // batch (a row of 100 entries over 16 threads is then a single batch);
 // otherwise its entries are added one dependent load at a time into the
-// first accumulator.  Measured on the 13k-bus A^T: U = NA = 8 with
-// predication for FP32 values, U = 4, NA = 2 without it for FP64.
+// first accumulator.  Measured on the 13k-bus LP: list rows U = 12, NA = 2
+// with predication for FP32 values (U at least the 12 entries per thread of
+// the default partition, so most rows take one batch; U = 16 costs
+// occupancy), U = 4, NA = 2 without it for FP64.
 template <typename VT, int U, int NA, bool PRED>
 __device__ __forceinline__ VT batched_dot(const int* __restrict__ col, const VT* __restrict__ val,
                                           const VT* __restrict__ x, int e, int z, int nl) {
@@ -174,8 +176,7 @@ __device__ __forceinline__ VT batched_dot(const int* __restrict__ col, const VT*
 template <typename VT, int nl>
 __device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* __restrict__ val,
                                         const VT* __restrict__ x, int a, int z, int li) {
-  return batched_dot<VT, sizeof(VT) == 4 ? 8 : 4, sizeof(VT) == 4 ? 8 : 2, sizeof(VT) == 4>(col, val, x,
-                                                                                               a + li, z, nl);
+  return batched_dot<VT, sizeof(VT) == 4 ? 12 : 4, 2, sizeof(VT) == 4>(col, val, x, a + li, z, nl);
 }
 
 // The same with the group size known only at run time (measured faster for
@@ -188,16 +189,18 @@ __device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT
 }
 
 // One warp per chunk of a long row (chunk launch): chunk w = blockIdx.x *
-// (kBlock / 32) + warp; batches of eight lane-strided entries per lane (the
-// last one as above), eight accumulators combined in a fixed tree, then a
-// fixed warp tree; the sum goes to part.cpart[w] in FP64.
+// (kBlock / 32) + warp; lane-strided entries, for FP32 values one predicated
+// batch of 16 per lane (a whole 512-entry chunk; measured faster than two
+// batches of 8), for FP64 batches of 8; then a fixed warp tree; the sum goes
+// to part.cpart[w] in FP64.
 template <typename VT>
 __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT* __restrict__ val,
                                            const VT* __restrict__ x, const Partition& part) {
   const int w = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= part.nchunk) return;
   const int2 c = part.chunks[w];
-  VT s = batched_dot<VT, 8, 8, sizeof(VT) == 4>(col, val, x, c.x + lane, c.y, 32);
+  VT s = sizeof(VT) == 4 ? batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32)
+                          : batched_dot<VT, 8, 8, false>(col, val, x, c.x + lane, c.y, 32);
   s = warp_sum(s);
   if (lane == 0) part.cpart[w] = (double)s;
 }
