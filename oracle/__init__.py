@@ -54,7 +54,7 @@ class OrcParams(C.Structure):
                 ("restart_suff", C.c_double), ("restart_nec", C.c_double),
                 ("restart_long", C.c_double), ("log_cap", C.c_int32),
                 ("restart_ref", C.c_int32), ("restart_metric", C.c_int32),
-                ("sigma_update", C.c_int32)]
+                ("sigma_update", C.c_int32), ("algo", C.c_int32), ("infeas_tol", C.c_double)]
 
 
 class OrcLog(C.Structure):
@@ -76,7 +76,7 @@ DEFAULTS = dict(tol=1e-4, max_iter=100000, check_every=64, use_scaling=1, sigma0
                 lambda_in=0.0, lambda_safety=1.01, power_max_iter=500, power_tol=1e-4,
                 power_seed=0x5EED, restart_suff=0.2, restart_nec=0.8, restart_long=0.2,
                 log_cap=100000, restart_ref=0, restart_metric=0,
-                sigma_update=1)
+                sigma_update=1, algo=0, infeas_tol=0.0)
 
 
 def lib():

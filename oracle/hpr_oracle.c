@@ -237,7 +237,68 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
 }
 
 /* ---------------------------------------------------------------------- */
-/* Restarted HPR (Eq. 9)                                                   */
+/* Infeasibility certificates on the scaled LP (an LP of the same form:     */
+/* scaling maps certificates to certificates).                              */
+/* ---------------------------------------------------------------------- */
+/* Primal infeasibility (Farkas): a dual ray u with z = -A^T u has the
+ * homogeneous dual objective  sum_i (u_i > 0 ? lo_i : hi_i) u_i
+ * + sum_j (z_j > 0 ? xl_j : xu_j) z_j  > 0.  Terms that would need an
+ * infinite bound are not summed; their squares make up the violation.
+ * The ray is accepted when the objective F > 0 and ||violation|| <= tol F. */
+static int primal_infeasible(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
+                             const double* val, const double* lo, const double* hi,
+                             const double* xl, const double* xu, const double* u, double tol) {
+  double* aty = dalloc(n);
+  spmv_t(m, n, rp, col, val, u, aty);
+  double F = 0.0, V = 0.0;
+  for (int32_t i = 0; i < m; i++) {
+    if (u[i] > 0.0) {
+      if (isfinite(lo[i])) F += lo[i] * u[i];
+      else V += u[i] * u[i];
+    } else if (u[i] < 0.0) {
+      if (isfinite(hi[i])) F += hi[i] * u[i];
+      else V += u[i] * u[i];
+    }
+  }
+  for (int32_t j = 0; j < n; j++) {
+    const double z = -aty[j];
+    if (z > 0.0) {
+      if (isfinite(xl[j])) F += xl[j] * z;
+      else V += z * z;
+    } else if (z < 0.0) {
+      if (isfinite(xu[j])) F += xu[j] * z;
+      else V += z * z;
+    }
+  }
+  free(aty);
+  return F > 0.0 && sqrt(V) <= tol * F;
+}
+
+/* Dual infeasibility (primal unbounded): a direction d with c^T d < 0 that
+ * stays in the recession cones, A d in that of [lo, hi] ((A d)_i >= 0 where
+ * lo_i is finite, <= 0 where hi_i is finite) and d in that of [xl, xu].
+ * Accepted when c^T d < 0 and ||cone violation|| <= tol |c^T d|.          */
+static int dual_infeasible(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
+                           const double* val, const double* c, const double* lo, const double* hi,
+                           const double* xl, const double* xu, const double* d, double tol) {
+  double* ad = dalloc(m);
+  spmv(m, rp, col, val, d, ad);
+  double cd = 0.0, V = 0.0;
+  for (int32_t j = 0; j < n; j++) {
+    cd += c[j] * d[j];
+    if (d[j] < 0.0 && isfinite(xl[j])) V += d[j] * d[j];
+    if (d[j] > 0.0 && isfinite(xu[j])) V += d[j] * d[j];
+  }
+  for (int32_t i = 0; i < m; i++) {
+    if (ad[i] < 0.0 && isfinite(lo[i])) V += ad[i] * ad[i];
+    if (ad[i] > 0.0 && isfinite(hi[i])) V += ad[i] * ad[i];
+  }
+  free(ad);
+  return cd < 0.0 && sqrt(V) <= tol * (-cd);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Restarted HPR (Eq. 9); restarted PDHG with ergodic averaging (algo 1)   */
 /* ---------------------------------------------------------------------- */
 int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
                   const double* y_init, double* x_out, double* y_out, double* z_out,
@@ -262,6 +323,10 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   double *g = dalloc(n), *y = dalloc(m), *y0 = dalloc(m), *yb = dalloc(m), *q = dalloc(m);
   double *xo = dalloc(n), *yo = dalloc(m), *zo = dalloc(n);
   double *dyv = dalloc(m), *pv = dalloc(m);
+  /* PDHG: the step's x_bar, the running averages of the cycle, and the ray
+   * x_bar - x of a check iteration */
+  const int pdhg = prm->algo == 1;
+  double *xbr = dalloc(n), *xavg = dalloc(n), *yavg = dalloc(m), *dxv = dalloc(n);
 
   /* starting point, in scaled variables, projected onto K and the dual cone */
   for (int32_t j = 0; j < n; j++) {
@@ -288,8 +353,9 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   while (t < prm->max_iter) {
     const int is_check = ((t + 1) % prm->check_every == 0) || (t + 1 == prm->max_iter);
     const double s = 1.0 / (lambda * sigma);
-    const double wa = 1.0 / (double)(k + 2);        /* Halpern weights */
-    const double wb = (double)(k + 1) / (double)(k + 2);
+    /* HPR: Halpern weights; PDHG: weights of the running average */
+    const double wa = pdhg ? 1.0 / (double)(k + 1) : 1.0 / (double)(k + 2);
+    const double wb = pdhg ? (double)k / (double)(k + 1) : (double)(k + 1) / (double)(k + 2);
 
     /* x_bar = Pi_K(x + sigma (A^T y - c)); z_bar = (x_bar - v)/sigma */
     spmv_t(m, n, lp->row_ptr, lp->col, vs, y, g);
@@ -298,9 +364,14 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       double v = x[j] + sigma * (g[j] - cs[j]);
       double xbar = clampd(v, xls[j], xus[j]);
       xt[j] = 2.0 * xbar - x[j];                   /* reflection */
+      if (pdhg) {
+        xbr[j] = xbar;
+        xavg[j] = wa * xbar + wb * xavg[j];
+      }
       if (is_check) {
-        xb[j] = xbar;
-        zb[j] = (xbar - v) / sigma;
+        xb[j] = pdhg ? xavg[j] : xbar;
+        zb[j] = (xbar - v) / sigma;                /* PDHG: replaced below */
+        dxv[j] = xbar - x[j];
         dxx += (xbar - x[j]) * (xbar - x[j]);
       }
     }
@@ -310,18 +381,27 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
     for (int32_t i = 0; i < m; i++) {
       double r = y[i] - s * q[i];
       double ybar = r + s * clampd(-r / s, los[i], his[i]);
+      if (pdhg) yavg[i] = wa * ybar + wb * yavg[i];
       if (is_check) {
-        yb[i] = ybar;
+        yb[i] = pdhg ? yavg[i] : ybar;
         dyv[i] = ybar - y[i];
         dyy += (ybar - y[i]) * (ybar - y[i]);
       }
-      y[i] = wa * y0[i] + wb * (2.0 * ybar - y[i]);  /* Halpern step */
+      if (pdhg) y[i] = ybar;                         /* PDHG step */
+      else y[i] = wa * y0[i] + wb * (2.0 * ybar - y[i]);  /* Halpern step */
     }
-    for (int32_t j = 0; j < n; j++) x[j] = wa * x0[j] + wb * xt[j];
+    for (int32_t j = 0; j < n; j++) x[j] = pdhg ? xbr[j] : wa * x0[j] + wb * xt[j];
     k++;
     t++;
     if (!is_check) continue;
 
+    /* PDHG: the checked point is the average; its z is the reduced cost
+     * c - A^T y_avg where the bounds let it act, 0 elsewhere (the scaled
+     * copy is zeroed below where a bound is infinite) */
+    if (pdhg) {
+      spmv_t(m, n, lp->row_ptr, lp->col, vs, yb, g);
+      for (int32_t j = 0; j < n; j++) zb[j] = cs[j] - g[j];
+    }
     /* unscale the barred iterate and evaluate the KKT map on the original LP */
     for (int32_t j = 0; j < n; j++) {
       xo[j] = beta * Dc[j] * xb[j];
@@ -337,7 +417,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
      * metric of the iteration (cross term with A(x_bar - x) = A x_t - A x_bar),
      * or the KKT error */
     double rho;
-    if (prm->restart_metric == 2) {
+    if (pdhg || prm->restart_metric == 2) {
       rho = last[5];
     } else {
       double cross = 0.0;
@@ -352,6 +432,12 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
     const int was_first = first_check;
     if (last[5] <= prm->tol) {
       status = 0;
+    } else if (prm->infeas_tol > 0.0 &&
+               primal_infeasible(m, n, lp->row_ptr, lp->col, vs, los, his, xls, xus, dyv, prm->infeas_tol)) {
+      status = 5;  /* the dual ray y_bar - y certifies primal infeasibility */
+    } else if (prm->infeas_tol > 0.0 &&
+               dual_infeasible(m, n, lp->row_ptr, lp->col, vs, cs, los, his, xls, xus, dxv, prm->infeas_tol)) {
+      status = 6;  /* the direction x_bar - x certifies an unbounded primal */
     } else {
       /* restart rule (reading): sufficient / necessary / long */
       if (first_check) {
@@ -380,8 +466,18 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       e->rmap = last[6];
     }
     nlog++;
-    if (status == 0) break;
+    /* an infeasibility verdict returns its certificate, unscaled like y or x */
+    if (status == 5)
+      for (int32_t i = 0; i < m; i++) yo[i] = gamma * Dr[i] * dyv[i];
+    if (status == 6)
+      for (int32_t j = 0; j < n; j++) xo[j] = beta * Dc[j] * dxv[j];
+    if (status == 0 || status == 5 || status == 6) break;
     if (restart) {
+      /* PDHG restarts from the average */
+      if (pdhg) {
+        memcpy(x, xb, sizeof(double) * (size_t)n);
+        memcpy(y, yb, sizeof(double) * (size_t)m);
+      }
       /* primal-weight update from the displacement since the last restart */
       double ddx = 0.0, ddy = 0.0;
       for (int32_t j = 0; j < n; j++) ddx += (x[j] - x0[j]) * (x[j] - x0[j]);
@@ -426,6 +522,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   free(Dr); free(Dc); free(vs); free(cs); free(xls); free(xus); free(los); free(his);
   free(x); free(x0); free(xt); free(xb); free(zb); free(g); free(y); free(y0); free(yb);
   free(q); free(xo); free(yo); free(zo); free(dyv); free(pv);
+  free(xbr); free(xavg); free(yavg); free(dxv);
   return 0;
 }
 

@@ -54,6 +54,12 @@ typedef struct {
                             norm in which the iteration is nonexpansive);
                             2: the KKT error max(r_p, r_d, gap)            */
   int32_t sigma_update;  /* 1: sigma update at restarts; 0: keep sigma0    */
+  int32_t algo;          /* 0: restarted HPR (Eq. 9, Halpern step);
+                            1: restarted PDHG with ergodic averaging: the
+                            same two steps, no Halpern step, checks and
+                            restarts on the running average of the cycle  */
+  double infeas_tol;     /* > 0: infeasibility detection at every check
+                            (relative violation of the certificate)       */
 } orc_params;
 
 typedef struct {
@@ -66,7 +72,8 @@ typedef struct {
 
 typedef struct {
   int64_t iters;
-  int32_t status;    /* 0 optimal, 1 iteration limit */
+  int32_t status;    /* 0 optimal, 1 iteration limit, 5 primal infeasible,
+                        6 dual infeasible (primal unbounded)          */
   int32_t restarts;
   int32_t nlog;
   int32_t power_iters;
@@ -84,7 +91,10 @@ double orc_power_lambda(int32_t m, int32_t n, const int64_t* rp, const int32_t* 
                         const double* val, int32_t max_iter, double tol, uint64_t seed,
                         int32_t* iters_out);
 
-/* Restarted HPR iteration (Eq. 9).  x_init / y_init may be NULL. */
+/* Restarted HPR iteration (Eq. 9), or restarted PDHG with ergodic averaging
+ * (algo = 1).  x_init / y_init may be NULL.  With status 5 y_out holds the
+ * dual ray that certifies primal infeasibility, with status 6 x_out holds
+ * the primal ray that certifies unboundedness (both unscaled). */
 int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
                   const double* y_init, double* x_out, double* y_out, double* z_out,
                   orc_info* info, orc_log* log);
