@@ -61,7 +61,18 @@ enum scuc_status {
   SCUC_ST_ITER_LIMIT = 1,
   SCUC_ST_TIME_LIMIT = 2,
   SCUC_ST_NUMERICAL = 3,     /* NaN/Inf appeared in a residual              */
-  SCUC_ST_FALLBACK_COLD = 4  /* warm start rejected, solved from cold start */
+  SCUC_ST_FALLBACK_COLD = 4, /* warm start rejected, solved from cold start */
+  SCUC_ST_PRIMAL_INFEASIBLE = 5, /* infeas_tol > 0: y_out holds a Farkas ray  */
+  SCUC_ST_DUAL_INFEASIBLE = 6    /* infeas_tol > 0: x_out holds a direction of
+                                    unbounded descent (primal unbounded)    */
+};
+
+enum scuc_algo {
+  SCUC_ALGO_HPR = 0,         /* restarted Halpern PR iteration (Eq. 9)      */
+  SCUC_ALGO_PDHG_AVG = 1     /* restarted PDHG with ergodic averaging: the
+                                same two steps without the Halpern step;
+                                checks and restarts on the running average
+                                of the restart cycle                         */
 };
 
 enum scuc_precision {
@@ -113,6 +124,13 @@ typedef struct {
                              (the norm in which the iteration is
                              nonexpansive); 2 = KKT error                   */
   int32_t sigma_update;   /* 1: sigma update at restarts; 0: keep sigma0    */
+  int32_t algo;           /* SCUC_ALGO_HPR                                  */
+  double infeas_tol;      /* 0: off; > 0: at every check, declare the LP
+                             primal infeasible when y_bar - y is a Farkas
+                             ray, or unbounded when x_bar - x is a descent
+                             direction in the recession cone, each with
+                             relative violation <= infeas_tol (1e-8 is a
+                             sound choice); two extra FP64 SpMVs per check */
 } scuc_solve_params;
 
 typedef struct {
@@ -180,11 +198,17 @@ int scuc_lp_create_box(scuc_lp** out, int32_t m, int32_t n, int64_t nnz, const i
 /* Dimensions of a handle. */
 int scuc_lp_dims(const scuc_lp* lp, int32_t* m, int32_t* n, int64_t* nnz);
 
-/* Solve with restarted HPR (Eq. 9).
+/* Solve with restarted HPR (Eq. 9), or restarted PDHG with ergodic
+ * averaging (p->algo).
  *  x0[n], y0[m]: optional warm start (NULL = cold start from x = Pi_K(0),
  *    y = 0); projected onto K and onto the sign pattern of the rows.
  *  x_out[n], y_out[m], z_out[n]: caller buffers (NULL allowed) receiving
- *    the last checked point (x_bar, y_bar, z_bar) in the unscaled LP.
+ *    the last checked point (x_bar, y_bar, z_bar) in the unscaled LP; with
+ *    status SCUC_ST_PRIMAL_INFEASIBLE y_out receives the unscaled Farkas
+ *    ray u instead (sum_i (u_i > 0 ? lo_i : hi_i) u_i + sum_j (z_j > 0 ?
+ *    xl_j : xu_j) z_j > 0 with z = -A^T u), with SCUC_ST_DUAL_INFEASIBLE
+ *    x_out receives the direction d (c^T d < 0, A d and d in the recession
+ *    cones of the row box and of K).
  *  Host or device pointers according to p->device_ptrs.
  *  Per iteration k (k counts iterations since the last restart, scaled
  *  problem, s = 1/(lambda sigma)):
@@ -202,6 +226,11 @@ int scuc_lp_dims(const scuc_lp* lp, int32_t* m, int32_t* n, int64_t* nnz);
  *  lambda sigma ||y_bar-y||^2).  At a restart sigma <- sqrt(sigma *
  *  ||dx||/(sqrt(lambda) ||dy||)) with d the displacement since the last
  *  restart (skipped when either norm < 1e-10).
+ *  SCUC_ALGO_PDHG_AVG: x, y <- x_bar, y_bar; the running averages
+ *  (x_avg, y_avg) of the cycle's (x_bar, y_bar) (weights 1/(k+1)) are the
+ *  checked point, z the reduced cost c - A^T y_avg where a finite bound
+ *  lets it act (0 elsewhere); rho = the KKT error; a restart moves the
+ *  iterate and the anchor to the average.
  *  info (may be NULL) receives the outcome; the check log is kept in the
  *  handle (scuc_lp_get_log).  Synchronises the handle's stream.         */
 int scuc_lp_solve(scuc_lp* lp, const scuc_solve_params* p, const double* x0, const double* y0,
@@ -224,7 +253,9 @@ int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double*
  * test, so each follows the iteration of its own scuc_lp_solve (the same
  * checks and restart decisions; matvec sums may differ in rounding order).
  *  lps[count]: distinct handles on one device (SCUC_E_INVALID otherwise).
- *  p: as scuc_lp_solve (profile is ignored); NULL: defaults.
+ *  p: as scuc_lp_solve (profile is ignored); NULL: defaults.  Only
+ *    SCUC_ALGO_HPR without infeasibility detection (SCUC_E_INVALID
+ *    otherwise).
  *  x_out[count], y_out[count], z_out[count]: NULL, or per-LP output
  *    pointers (each may be NULL), device or host per p->device_ptrs.
  *  infos[count]: per-LP results; setup_ms/solve_ms/launches are those of

@@ -8,7 +8,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(HERE, "libscuclp.so")
 
 SCUC_OK, SCUC_E_INVALID, SCUC_E_CUDA, SCUC_E_OOM, SCUC_E_DEVICE_TIMEOUT, SCUC_E_INFEASIBLE = range(6)
-STATUS = {0: "optimal", 1: "iter_limit", 2: "time_limit", 3: "numerical", 4: "fallback_cold"}
+STATUS = {0: "optimal", 1: "iter_limit", 2: "time_limit", 3: "numerical", 4: "fallback_cold",
+          5: "primal_infeasible", 6: "dual_infeasible"}
+ALGO = {"hpr": 0, "pdhg_avg": 1}
 FP64, MIXED = 0, 1
 
 
@@ -21,7 +23,8 @@ class SolveParams(C.Structure):
                 ("restart_long", C.c_double), ("polish_factor", C.c_double),
                 ("polish_stall", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("device_ptrs", C.c_int32), ("restart_ref", C.c_int32),
-                ("restart_metric", C.c_int32), ("sigma_update", C.c_int32)]
+                ("restart_metric", C.c_int32), ("sigma_update", C.c_int32), ("algo", C.c_int32),
+                ("infeas_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):

@@ -105,6 +105,7 @@ struct Batch {
     L.x = x; L.x0 = x0; L.xt = xt; L.xbar = xbar; L.zbar = zbar; L.y = y; L.y0 = y0; L.ybar = ybar;
     L.xt32 = xt32; L.y32 = y32;
     L.qchk = qchk; L.dychk = dychk;
+    L.dxchk = nullptr;  // no infeasibility detection in batches
     L.coef = coef; L.coef_w = coef;
     L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
     L.gsum = gsum;
@@ -267,7 +268,7 @@ int launch_batch_period(Batch& B, cudaStream_t s, int check_every, int ga) {
     }
   }
   if (B.pA.nblk) k_res_primal<<<B.pA.nblk, kBlock, B.pA.smem, s>>>(L);
-  if (B.pT.nblk) k_res_dual<<<B.pT.nblk, kBlock, B.pT.smem, s>>>(L);
+  if (B.pT.nblk) k_res_dual<false><<<B.pT.nblk, kBlock, B.pT.smem, s>>>(L);
   k_decide<<<B.nlp, kDecideThreads, 0, s>>>(L, check_every);
   SCUC_CUDA(cudaGetLastError());
   return SCUC_OK;
@@ -315,6 +316,10 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
   if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
       (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1) {
     set_error("invalid solve parameters");
+    return SCUC_E_INVALID;
+  }
+  if (p.algo != SCUC_ALGO_HPR || p.infeas_tol != 0.0) {
+    set_error("scuc_lp_solve_batch: batches run SCUC_ALGO_HPR without infeasibility detection");
     return SCUC_E_INVALID;
   }
   if (nlp > 65535) {
@@ -491,6 +496,8 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
     c.restart_ref = p.restart_ref;
     c.restart_metric = p.restart_metric;
     c.sigma_update = p.sigma_update;
+    c.algo = SCUC_ALGO_HPR;
+    c.infeas_tol = 0.0;
     c.s_step = 1.0 / (lam[b] * p.sigma0);
     c.polish_factor = p.polish_factor;
     c.max_iter = ((p.max_iter + ce - 1) / ce) * ce;

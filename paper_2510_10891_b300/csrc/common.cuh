@@ -92,13 +92,14 @@ struct Ctrl {
   int32_t check_every, polish_stall, log_cap, precision, restart_ref, restart_metric;
   int64_t k, t, iters_fp32;
   double rho0, rho_prev, best_kkt, s_step;
-  int32_t sigma_update, pad1;
+  int32_t sigma_update, algo;  // algo: SCUC_ALGO_HPR or SCUC_ALGO_PDHG_AVG
   int32_t first_check, done, status, restart_pending;
   int32_t restarts, nlog, fp64_phase, stall;
   double kkt, rp, rd, gap, pobj, dobj;
   double reject_kkt;  // > 0: stop with SCUC_ST_FALLBACK_COLD if the first check has kkt >= this
   uint64_t t_start_ns;     // device clock at the start of the iterations
   uint64_t time_limit_ns;  // > 0: stop with SCUC_ST_TIME_LIMIT after this long (checked at checks)
+  double infeas_tol;       // > 0: infeasibility detection at checks (relative certificate violation)
 };
 
 struct PowerCtrl {

@@ -414,9 +414,10 @@ int Handle::setup_solver(const std::vector<int>& rp32, const std::vector<int>& r
   SCUC_TRY(alloc(&gsum32, n));
   SCUC_TRY(alloc(&partP, 4 * (size_t)epi_gx));
   SCUC_TRY(alloc(&partD, 2 * (size_t)pA.nblk));
-  SCUC_TRY(alloc(&partRA, 3 * (size_t)std::max(pA.nblk, kNormBlocks)));
+  SCUC_TRY(alloc(&partRA, 6 * (size_t)std::max(pA.nblk, kNormBlocks)));
   SCUC_TRY(alloc(&dychk, m));
-  SCUC_TRY(alloc(&partRT, 4 * (size_t)std::max(pT.nblk, kNormBlocks)));
+  SCUC_TRY(alloc(&dxchk, n));
+  SCUC_TRY(alloc(&partRT, 6 * (size_t)std::max(pT.nblk, kNormBlocks)));
   SCUC_TRY(alloc(&ctrl, 1));
   SCUC_TRY(alloc(&pctrl, 1));
   SCUC_TRY(alloc(&qv, n));
@@ -452,6 +453,7 @@ DevLP Handle::dev() const {
   L.x = x; L.x0 = x0; L.xt = xt; L.xbar = xbar; L.zbar = zbar; L.y = y; L.y0 = y0; L.ybar = ybar;
   L.xt32 = xt32; L.y32 = y32;
   L.qchk = uv; L.dychk = dychk;  // uv: power-method scratch, free during iterations
+  L.dxchk = dxchk;
   L.coef = coef; L.coef_w = coef;
   L.partP = partP; L.partD = partD; L.partRA = partRA; L.partRT = partRT;
   L.gsum = gsum;
@@ -578,7 +580,7 @@ int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
 // kernels of one period: anchor, iterations, residual SpMVs, decide
 int64_t Handle::period_kernels(int check_every) const {
   const int la = (pA.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0), lt = (pT.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0);
-  return 2 + (int64_t)check_every * (la + lt + 1) + la + lt;
+  return 2 + (int64_t)check_every * (la + lt + 1) + (la + lt) * (detect ? 2 : 1);
 }
 
 // check SpMVs (FP64) and the decide kernel of a period
@@ -587,7 +589,16 @@ int Handle::launch_checks(cudaStream_t s, int check_every) {
   if (pA.nchunk) k_chunks_iter<kChunksResPrimal, kPrecF64><<<pA.nchunkblk, kBlock, 0, s>>>(L);
   if (pA.nblk) k_res_primal<<<pA.nblk, kBlock, pA.smem, s>>>(L);
   if (pT.nchunk) k_chunks_iter<kChunksResDual, kPrecF64><<<pT.nchunkblk, kBlock, 0, s>>>(L);
-  if (pT.nblk) k_res_dual<<<pT.nblk, kBlock, pT.smem, s>>>(L);
+  if (pT.nblk) {
+    if (algo == SCUC_ALGO_PDHG_AVG) k_res_dual<true><<<pT.nblk, kBlock, pT.smem, s>>>(L);
+    else k_res_dual<false><<<pT.nblk, kBlock, pT.smem, s>>>(L);
+  }
+  if (detect) {  // certificate products A (x_bar - x), A^T (y_bar - y)
+    if (pA.nchunk) k_chunks_iter<kChunksInfRows, kPrecF64><<<pA.nchunkblk, kBlock, 0, s>>>(L);
+    if (pA.nblk) k_inf_rows<<<pA.nblk, kBlock, pA.smem, s>>>(L);
+    if (pT.nchunk) k_chunks_iter<kChunksInfCols, kPrecF64><<<pT.nchunkblk, kBlock, 0, s>>>(L);
+    if (pT.nblk) k_inf_cols<<<pT.nblk, kBlock, pT.smem, s>>>(L);
+  }
   k_decide<<<1, kDecideThreads, 0, s>>>(L, check_every);
   SCUC_CUDA(cudaGetLastError());
   return SCUC_OK;
@@ -672,7 +683,8 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
                   double* yo, double* zo, scuc_solve_info* info, double reject_kkt) {
   using clk = std::chrono::steady_clock;
   if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
-      (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1) {
+      (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1 ||
+      (p.algo != SCUC_ALGO_HPR && p.algo != SCUC_ALGO_PDHG_AVG) || !(p.infeas_tol >= 0.0 && p.infeas_tol < 1.0)) {
     set_error("invalid solve parameters");
     return SCUC_E_INVALID;
   }
@@ -724,6 +736,10 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.restart_ref = p.restart_ref;
   C.restart_metric = p.restart_metric;
   C.sigma_update = p.sigma_update;
+  C.algo = p.algo;
+  C.infeas_tol = p.infeas_tol;
+  algo = p.algo;
+  detect = p.infeas_tol > 0.0;
   C.s_step = 1.0 / (lambda * p.sigma0);
   C.polish_factor = p.polish_factor;
   C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
@@ -744,9 +760,14 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
     coef_cap = p.check_every;
   }
   coef_h.resize(2 * (size_t)p.check_every);
-  for (int j = 0; j < p.check_every; j++) {  // Halpern weights of the first period (k = j)
-    coef_h[2 * j] = 1.0 / (double)(j + 2);
-    coef_h[2 * j + 1] = (double)(j + 1) / (double)(j + 2);
+  for (int j = 0; j < p.check_every; j++) {  // weights of the first period (k = j)
+    if (p.algo == SCUC_ALGO_PDHG_AVG) {      // running average
+      coef_h[2 * j] = 1.0 / (double)(j + 1);
+      coef_h[2 * j + 1] = (double)j / (double)(j + 1);
+    } else {                                 // Halpern
+      coef_h[2 * j] = 1.0 / (double)(j + 2);
+      coef_h[2 * j + 1] = (double)(j + 1) / (double)(j + 2);
+    }
   }
   SCUC_CUDA(cudaMemcpyAsync(coef, coef_h.data(), coef_h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   const DevLP L = dev();
@@ -772,8 +793,9 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   int64_t n_p = 0, n_d = 0, n_p32 = 0, n_d32 = 0;
   int timed_out = 0;
   if (use_graph) {
-    const void* key[5] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
-                          (const void*)coef, (const void*)(intptr_t)(mixed ? 0 : 1)};
+    const void* key[7] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
+                          (const void*)coef, (const void*)(intptr_t)(mixed ? 0 : 1), (const void*)(intptr_t)algo,
+                          (const void*)(intptr_t)(detect ? 1 : 0)};
     if (!graph_exec || memcmp(key, graph_key, sizeof(key)) != 0) {
       if (graph_exec) {
         cudaGraphExecDestroy(graph_exec);
@@ -904,6 +926,8 @@ void scuc_default_params(scuc_solve_params* p) {
   p->restart_ref = 0;
   p->restart_metric = 0;
   p->sigma_update = 1;
+  p->algo = SCUC_ALGO_HPR;
+  p->infeas_tol = 0.0;
 }
 
 static int sense_to_box(int32_t m, const char* sense, const double* rhs, const double* range,

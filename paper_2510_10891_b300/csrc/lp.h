@@ -52,6 +52,7 @@ struct Handle {
   double *y = nullptr, *y0 = nullptr, *ybar = nullptr;
   float *xt32 = nullptr, *y32 = nullptr;
   double* dychk = nullptr;
+  double* dxchk = nullptr;  // x_bar - x of a check (infeasibility detection)
   double *qv = nullptr, *uv = nullptr, *wv = nullptr;
   double *partP = nullptr, *partD = nullptr, *partRA = nullptr, *partRT = nullptr;
   double* gsum = nullptr;  // A^T y of the primal step (FP64 phases)
@@ -63,8 +64,8 @@ struct Handle {
   scuc_check_log* log_d = nullptr;
   int log_cap = 0, last_nlog = 0;
   cudaGraphExec_t graph_exec = nullptr;
-  const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // check_every, FP32 values, log,
-                                                                               // coef, initial phase
+  // check_every, FP32 values, log, coef, initial phase, algorithm, detection
+  const void* graph_key[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t aux = nullptr;  // capture stream of the graph's conditional bodies
   double* coef = nullptr;
   int64_t nlaunch = 0, graph_nodes = 0;  // kernels launched by this handle; nodes of the period graph
@@ -95,6 +96,8 @@ struct Handle {
   int launch_iterations(cudaStream_t s, int check_every, bool profile);
   int launch_checks(cudaStream_t s, int check_every);
   int64_t period_kernels(int check_every) const;
+  int algo = SCUC_ALGO_HPR;  // of the current solve (kernels launched by the checks)
+  bool detect = false;       // infeasibility detection in the current solve
   int launch_period(int check_every, bool profile, bool fp64);
   int build_solve_graph(int check_every, int phase64);
   int solve(const scuc_solve_params& p, const double* x0, const double* y0, double* xo,

@@ -18,6 +18,7 @@ struct DevLP {
   double *x, *x0, *xt, *xbar, *zbar, *y, *y0, *ybar;
   float *xt32, *y32;
   double *qchk, *dychk;        // A x_t and y_bar - y at a check iteration
+  double* dxchk;               // x_bar - x at a check iteration (infeasibility detection)
   const double* coef;          // Halpern weights {1/(k+2), (k+1)/(k+2)} per period slot
   double* coef_w;              // same buffer, written by the decide kernel
   double* gsum;                // A^T y of the primal step in FP64 phases
@@ -77,10 +78,12 @@ __device__ __forceinline__ bool phase64(const Ctrl* c, int prec) {
 // ---------------------------------------------------------------------------
 // chunk launches of the long rows (one LP; batches have no long rows)
 // ---------------------------------------------------------------------------
-constexpr int kChunksPrimal = 0, kChunksDual = 1, kChunksResPrimal = 2, kChunksResDual = 3;
+constexpr int kChunksPrimal = 0, kChunksDual = 1, kChunksResPrimal = 2, kChunksResDual = 3, kChunksInfRows = 4,
+              kChunksInfCols = 5;
 
 // Chunk sums for the next main launch: A^T y (primal step) or A x_t (dual
-// step) in the phase's precision, A x_bar / A^T y_bar (checks) in FP64.
+// step) in the phase's precision, A x_bar / A^T y_bar (checks) and the
+// certificate products A (x_bar - x) / A^T (y_bar - y) in FP64.
 template <int KIND, int PREC>
 __global__ void __launch_bounds__(kBlock) k_chunks_iter(DevLP L) {
   const Ctrl* ctrl = L.ctrl;
@@ -94,8 +97,12 @@ __global__ void __launch_bounds__(kBlock) k_chunks_iter(DevLP L) {
     else chunk_warp<float>(L.col, L.vs32, L.xt32, L.pA);
   } else if (KIND == kChunksResPrimal) {
     chunk_warp<double>(L.col, L.vs, L.xbar, L.pA);
-  } else {
+  } else if (KIND == kChunksResDual) {
     chunk_warp<double>(L.colt, L.vst, L.ybar, L.pT);
+  } else if (KIND == kChunksInfRows) {
+    chunk_warp<double>(L.col, L.vs, L.dxchk, L.pA);
+  } else {
+    chunk_warp<double>(L.colt, L.vst, L.dychk, L.pT);
   }
 }
 
@@ -107,6 +114,8 @@ struct PrimalEpi {
   const DevLP& L;
   double sigma, wa, wb;
   bool fp64;
+  bool pdhg;  // restarted PDHG with ergodic averaging: x^{k+1} = x_bar, running average in xbar
+  bool ray;   // infeasibility detection: store x_bar - x on checks
   double acc[4];
   double xj, cj, xlj, xuj, x0j;  // the column's operands, loaded before its sum
   __device__ void load(int j) {
@@ -120,17 +129,30 @@ struct PrimalEpi {
     const double v = xj + sigma * (g - cj);
     const double xb = clampd(v, xlj, xuj);
     const double xt = 2.0 * xb - xj;
-    const double xn = wa * x0j + wb * xt;
+    double xn, xa = 0.0;
+    if (pdhg) {  // weights {1/(k+1), k/(k+1)} of the running average (rounded as written); k = 0 starts it
+      xn = xb;
+      xa = wb == 0.0 ? xb : __dadd_rn(__dmul_rn(wa, xb), __dmul_rn(wb, L.xbar[j]));
+      L.xbar[j] = xa;
+    } else {
+      xn = wa * x0j + wb * xt;
+    }
     L.x[j] = xn;
     if (fp64) L.xt[j] = xt;
     else L.xt32[j] = (float)xt;
     if (CHECK) {
+      if (ray) L.dxchk[j] = xb - xj;
+      acc[0] += (xb - xj) * (xb - xj);
+      if (pdhg) {  // the checked point is the average; its z comes with A^T y_avg
+        acc[1] += (xa - x0j) * (xa - x0j);
+        acc[2] += cj * xa;
+        return;
+      }
       double zb = (xb - v) / sigma;
       if (zb > 0.0 && !isfinite(xlj)) zb = 0.0;
       if (zb < 0.0 && !isfinite(xuj)) zb = 0.0;
       L.xbar[j] = xb;
       L.zbar[j] = zb;
-      acc[0] += (xb - xj) * (xb - xj);
       acc[1] += (xn - x0j) * (xn - x0j);
       acc[2] += cj * xb;
       if (zb > 0.0) acc[3] += xlj * zb;
@@ -171,8 +193,8 @@ __global__ void __launch_bounds__(kBlock) k_primal_epi(DevLP L, int j) {
   const Ctrl* ctrl = L.ctrl + lp;
   if (ctrl->done) return;
   const double* cf = L.coef + (size_t)lp * L.coef_stride;
-  PrimalEpi<CHECK> epi{L, ctrl->sigma, cf[2 * j], cf[2 * j + 1], phase64(ctrl, PREC),
-                       {0.0, 0.0, 0.0, 0.0}, 0.0, 0.0, 0.0, 0.0, 0.0};
+  PrimalEpi<CHECK> epi{L, ctrl->sigma, cf[2 * j], cf[2 * j + 1], phase64(ctrl, PREC), ctrl->algo == SCUC_ALGO_PDHG_AVG,
+                       ctrl->infeas_tol > 0.0, {0.0, 0.0, 0.0, 0.0}, 0.0, 0.0, 0.0, 0.0, 0.0};
   const float* g32 = L.gsum32;
   int c0, c1;
   lp_range(L.col0, lp, L.n, c0, c1);
@@ -193,6 +215,7 @@ struct DualEpi {
   const DevLP& L;
   double s, wa, wb;
   bool fp64;
+  bool pdhg;  // y^{k+1} = y_bar, running average in ybar
   double acc[2];
   double yi, loi, hii, y0i;  // the row's operands, loaded before its sum
   __device__ void load(int i) {
@@ -204,15 +227,23 @@ struct DualEpi {
   __device__ void row(int i, double q) {
     const double r = yi - s * q;
     const double yb = fmax(r + s * loi, 0.0) + fmin(r + s * hii, 0.0);
-    const double yn = wa * y0i + wb * (2.0 * yb - yi);
+    double yn, ya = 0.0;
+    if (pdhg) {
+      yn = yb;
+      ya = wb == 0.0 ? yb : __dadd_rn(__dmul_rn(wa, yb), __dmul_rn(wb, L.ybar[i]));
+      L.ybar[i] = ya;
+    } else {
+      yn = wa * y0i + wb * (2.0 * yb - yi);
+    }
     L.y[i] = yn;
     if (!fp64) L.y32[i] = (float)yn;
     if (CHECK) {
-      L.ybar[i] = yb;
+      if (!pdhg) L.ybar[i] = yb;
       L.qchk[i] = q;
       L.dychk[i] = yb - yi;
       acc[0] += (yb - yi) * (yb - yi);
-      acc[1] += (yn - y0i) * (yn - y0i);
+      const double d = (pdhg ? ya : yn) - y0i;
+      acc[1] += d * d;
     }
   }
 };
@@ -226,7 +257,7 @@ __global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_dual(DevLP L, int j)
   if (ctrl->done) return;
   const double* cf = L.coef + (size_t)lp * L.coef_stride;
   DualEpi<CHECK> epi{L, ctrl->s_step, cf[2 * j], cf[2 * j + 1], phase64(ctrl, PREC),
-                     {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
+                     ctrl->algo == SCUC_ALGO_PDHG_AVG, {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
   if (bp.er >= 0) epi.load(bp.er);
   if (epi.fp64) {
     spmv_run<double>(bp, L.rp, L.col, L.vs, L.xt, L.pA, smem, epi);
@@ -269,24 +300,106 @@ __global__ void __launch_bounds__(kBlock) k_res_primal(DevLP L) {
   block_store<3>(epi.acc, L.partRA, L.pA);
 }
 
-struct ResDualEpi {  // A^T y_bar: dual residual (unscaled)
+// A^T y_bar: dual residual (unscaled).  AVG (restarted PDHG): y_bar is the
+// running average and z the reduced cost c - A^T y_bar where a finite bound
+// lets it act (0 elsewhere), stored in zbar; acc[1] is its part of the dual
+// objective (scaled).
+template <bool AVG>
+struct ResDualEpi {
   const DevLP& L;
   double gamma;
-  double acc[1];
+  double acc[AVG ? 2 : 1];
   __device__ void load(int) {}
   __device__ void row(int j, double g) {
-    const double d = gamma * (L.c[j] - g - L.zbar[j]) / L.Dc[j];
+    double z;
+    if (AVG) {
+      const double xl = L.xl[j], xu = L.xu[j];
+      z = L.c[j] - g;
+      if (z > 0.0 && !isfinite(xl)) z = 0.0;
+      if (z < 0.0 && !isfinite(xu)) z = 0.0;
+      L.zbar[j] = z;
+      if (z > 0.0) acc[AVG ? 1 : 0] += xl * z;
+      else if (z < 0.0) acc[AVG ? 1 : 0] += xu * z;
+    } else {
+      z = L.zbar[j];
+    }
+    const double d = gamma * (L.c[j] - g - z) / L.Dc[j];
     acc[0] += d * d;
   }
 };
 
+template <bool AVG>
 __global__ void __launch_bounds__(kBlock) k_res_dual(DevLP L) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Ctrl* ctrl = L.ctrl + (L.blkT ? L.blkT[blockIdx.x] : 0);
   if (ctrl->done) return;
-  ResDualEpi epi{L, ctrl->gamma, {0.0}};
+  ResDualEpi<AVG> epi{L, ctrl->gamma, {}};
   spmv_block<double>(L.rpt, L.colt, L.vst, L.ybar, L.pT, smem, epi);
-  block_store<1>(epi.acc, L.partRT, L.pT);
+  block_store<AVG ? 2 : 1>(epi.acc, L.partRT, L.pT);
+}
+
+// ---------------------------------------------------------------------------
+// Infeasibility certificates at a check (scaled LP; scaling maps certificates
+// to certificates).  Rays: u = y_bar - y (dychk) and d = x_bar - x (dxchk).
+//  primal infeasible: F(u) = sum_i (u_i > 0 ? lo_i : hi_i) u_i
+//    + sum_j (z_j > 0 ? xl_j : xu_j) z_j with z = -A^T u, over the terms whose
+//    bound is finite, > 0; the other terms' squares are the violation;
+//  unbounded: c^T d < 0 with A d and d in the recession cones of [lo, hi]
+//    and [xl, xu]; the squares of the components outside are the violation.
+// Rows (A d, u):   partRA slots 3, 4, 5 = cone violation of A d, F rows, violation rows.
+// Columns (A^T u, d): partRT slots 2, 3, 4, 5 = F cols, violation cols, c^T d, cone violation of d.
+// ---------------------------------------------------------------------------
+struct InfRowsEpi {
+  const DevLP& L;
+  double acc[3];
+  __device__ void load(int) {}
+  __device__ void row(int i, double ad) {
+    const double lo = L.lo[i], hi = L.hi[i], u = L.dychk[i];
+    if ((ad < 0.0 && isfinite(lo)) || (ad > 0.0 && isfinite(hi))) acc[0] += ad * ad;
+    if (u > 0.0) {
+      if (isfinite(lo)) acc[1] += lo * u;
+      else acc[2] += u * u;
+    } else if (u < 0.0) {
+      if (isfinite(hi)) acc[1] += hi * u;
+      else acc[2] += u * u;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_inf_rows(DevLP L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Ctrl* ctrl = L.ctrl + (L.blkA ? L.blkA[blockIdx.x] : 0);
+  if (ctrl->done) return;
+  InfRowsEpi epi{L, {0.0, 0.0, 0.0}};
+  spmv_block<double>(L.rp, L.col, L.vs, L.dxchk, L.pA, smem, epi);
+  block_store<3>(epi.acc, L.partRA + 3 * (size_t)L.pA.nblk, L.pA);
+}
+
+struct InfColsEpi {
+  const DevLP& L;
+  double acc[4];
+  __device__ void load(int) {}
+  __device__ void row(int j, double atu) {
+    const double xl = L.xl[j], xu = L.xu[j], z = -atu, d = L.dxchk[j];
+    if (z > 0.0) {
+      if (isfinite(xl)) acc[0] += xl * z;
+      else acc[1] += z * z;
+    } else if (z < 0.0) {
+      if (isfinite(xu)) acc[0] += xu * z;
+      else acc[1] += z * z;
+    }
+    acc[2] += L.c[j] * d;
+    if ((d < 0.0 && isfinite(xl)) || (d > 0.0 && isfinite(xu))) acc[3] += d * d;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_inf_cols(DevLP L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Ctrl* ctrl = L.ctrl + (L.blkT ? L.blkT[blockIdx.x] : 0);
+  if (ctrl->done) return;
+  InfColsEpi epi{L, {0.0, 0.0, 0.0, 0.0}};
+  spmv_block<double>(L.rpt, L.colt, L.vst, L.dychk, L.pT, smem, epi);
+  block_store<4>(epi.acc, L.partRT + 2 * (size_t)L.pT.nblk, L.pT);
 }
 
 // fixed-order sum of one partial array by a single block
@@ -307,9 +420,15 @@ __device__ double decide_sum(const double* p, int cnt) {
 // ---------------------------------------------------------------------------
 // decide: residuals, restart rule, sigma update, stop (one block)
 // ---------------------------------------------------------------------------
+// sums of the infeasibility certificates (k_inf_rows / k_inf_cols)
+struct InfSums {
+  double f, v;       // primal infeasibility: objective of the ray, squared violation
+  double cd, vd;     // unboundedness: c^T d, squared cone violation
+};
+
 __device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, int chunk, double Sx,
                                   double Sxa, double pobj_s, double dz, double Sy, double Sya, double viol2,
-                                  double dy, double dres2, double cross);
+                                  double dy, double dres2, double cross, const InfSums& inf);
 
 // one block per LP of the batch (blockIdx.x = LP)
 __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
@@ -324,31 +443,49 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevLP L, int chunk) {
   const double Sx = decide_sum(L.partP + 0 * nP + p0, L.epi_gx);
   const double Sxa = decide_sum(L.partP + 1 * nP + p0, L.epi_gx);
   const double pobj_s = decide_sum(L.partP + 2 * nP + p0, L.epi_gx);
-  const double dz = decide_sum(L.partP + 3 * nP + p0, L.epi_gx);
+  const bool avg = C->algo == SCUC_ALGO_PDHG_AVG;  // z and its objective part come with A^T y_avg
+  const double dz = avg ? decide_sum(L.partRT + 1 * nT + t0, ct) : decide_sum(L.partP + 3 * nP + p0, L.epi_gx);
   const double Sy = decide_sum(L.partD + 0 * nA + a0, ca);
   const double Sya = decide_sum(L.partD + 1 * nA + a0, ca);
   const double viol2 = decide_sum(L.partRA + 0 * nA + a0, ca);
   const double dy = decide_sum(L.partRA + 1 * nA + a0, ca);
   const double dres2 = decide_sum(L.partRT + t0, ct);
   const double cross = decide_sum(L.partRA + 2 * nA + a0, ca);
+  InfSums inf{0.0, 0.0, 0.0, 0.0};
+  if (C->infeas_tol > 0.0) {
+    const double vq = decide_sum(L.partRA + 3 * nA + a0, ca);
+    const double fr = decide_sum(L.partRA + 4 * nA + a0, ca);
+    const double vr = decide_sum(L.partRA + 5 * nA + a0, ca);
+    const double fc = decide_sum(L.partRT + 2 * nT + t0, ct);
+    const double vc = decide_sum(L.partRT + 3 * nT + t0, ct);
+    const double cd = decide_sum(L.partRT + 4 * nT + t0, ct);
+    const double vd = decide_sum(L.partRT + 5 * nT + t0, ct);
+    inf = InfSums{fr + fc, vr + vc, cd, vd + vq};
+  }
   __shared__ long long s_knew;
   if (threadIdx.x == 0)
     s_knew = decide_logic(L, C, L.log + (size_t)lp * L.log_stride, chunk, Sx, Sxa, pobj_s, dz, Sy, Sya, viol2,
-                          dy, dres2, cross);
+                          dy, dres2, cross, inf);
   __syncthreads();
-  // Halpern weights of the next period, computed once (FP64 division is slow on
-  // this part; every iterate update would otherwise divide per thread)
+  // weights of the next period, computed once (FP64 division is slow on this
+  // part; every iterate update would otherwise divide per thread): Halpern
+  // {1/(k+2), (k+1)/(k+2)}, or the running average's {1/(k+1), k/(k+1)}
   const long long kn = s_knew;
   double* cw = L.coef_w + (size_t)lp * L.coef_stride;
   for (int j = threadIdx.x; j < chunk; j += kDecideThreads) {
-    cw[2 * j] = 1.0 / (double)(kn + j + 2);
-    cw[2 * j + 1] = (double)(kn + j + 1) / (double)(kn + j + 2);
+    if (avg) {
+      cw[2 * j] = 1.0 / (double)(kn + j + 1);
+      cw[2 * j + 1] = (double)(kn + j) / (double)(kn + j + 1);
+    } else {
+      cw[2 * j] = 1.0 / (double)(kn + j + 2);
+      cw[2 * j + 1] = (double)(kn + j + 1) / (double)(kn + j + 2);
+    }
   }
 }
 
 __device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, int chunk, double Sx,
                                   double Sxa, double pobj_s, double dz, double Sy, double Sya, double viol2,
-                                  double dy, double dres2, double cross) {
+                                  double dy, double dres2, double cross, const InfSums& inf) {
 
   const double sigma = C->sigma, lambda = C->lambda, bg = C->beta * C->gamma;
   const double rp = sqrt(viol2) / (1.0 + C->bnorm);
@@ -357,7 +494,7 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, 
   const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
   const double kkt = fmax(rp, fmax(rd, gap));
   const int64_t k = C->k + chunk, t = C->t + chunk;
-  const double rho = C->restart_metric == 2
+  const double rho = (C->restart_metric == 2 || C->algo == SCUC_ALGO_PDHG_AVG)
                          ? kkt
                          : sqrt(fmax(0.0, Sx / sigma + lambda * sigma * Sy +
                                               (C->restart_metric == 1 ? 2.0 * cross : 0.0)));
@@ -370,6 +507,10 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, 
     status = SCUC_ST_NUMERICAL;
   } else if (kkt <= C->tol) {
     status = SCUC_ST_OPTIMAL;
+  } else if (C->infeas_tol > 0.0 && inf.f > 0.0 && sqrt(inf.v) <= C->infeas_tol * inf.f) {
+    status = SCUC_ST_PRIMAL_INFEASIBLE;  // y_bar - y is a Farkas ray
+  } else if (C->infeas_tol > 0.0 && inf.cd < 0.0 && sqrt(inf.vd) <= C->infeas_tol * -inf.cd) {
+    status = SCUC_ST_DUAL_INFEASIBLE;    // x_bar - x is a direction of unbounded descent
   } else if (C->reject_kkt > 0.0 && t == (int64_t)C->check_every && kkt >= C->reject_kkt) {
     status = SCUC_ST_FALLBACK_COLD;  // a warm start whose first check is no better than the cold start
   } else {
@@ -440,17 +581,36 @@ __global__ void __launch_bounds__(kDecideThreads) k_loop_cond(DevLP L, cudaGraph
 }
 
 // restart: anchor <- current point (runs at the start of each period);
+// restarted PDHG moves the iterate to the cycle's average first;
 // blockIdx.y = LP of the batch
 __global__ void k_anchor(DevLP L) {
   const int lp = blockIdx.y;
   const Ctrl* C = L.ctrl + lp;
   if (C->done || !C->restart_pending) return;
+  const bool avg = C->algo == SCUC_ALGO_PDHG_AVG;
   int a, b;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   lp_range(L.col0, lp, L.n, a, b);
-  for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += stride) L.x0[i] = L.x[i];
+  for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += stride) {
+    if (avg) {
+      const double v = L.xbar[i];
+      L.x[i] = v;
+      L.x0[i] = v;
+    } else {
+      L.x0[i] = L.x[i];
+    }
+  }
   lp_range(L.row0, lp, L.m, a, b);
-  for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += stride) L.y0[i] = L.y[i];
+  for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += stride) {
+    if (avg) {
+      const double v = L.ybar[i];
+      L.y[i] = v;
+      L.y0[i] = v;
+      L.y32[i] = (float)v;
+    } else {
+      L.y0[i] = L.y[i];
+    }
+  }
 }
 
 }  // namespace

@@ -372,20 +372,26 @@ __global__ void k_init_iterates(DevLP L, const double* __restrict__ xin, const d
 }
 
 // blockIdx.y = LP of the batch
+// Outputs of the last check, unscaled; an infeasibility verdict returns its
+// certificate instead (the ray y_bar - y in yo, or the direction x_bar - x
+// in xo).
 __global__ void k_finalize(DevLP L, double* __restrict__ xo, double* __restrict__ yo, double* __restrict__ zo) {
   const int lp = blockIdx.y;
   const double beta = L.ctrl[lp].beta, gamma = L.ctrl[lp].gamma;
+  const int status = L.ctrl[lp].status;
+  const double* xs = status == SCUC_ST_DUAL_INFEASIBLE ? L.dxchk : L.xbar;
+  const double* ys = status == SCUC_ST_PRIMAL_INFEASIBLE ? L.dychk : L.ybar;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int c0, c1, r0, r1;
   lp_range(L.col0, lp, L.n, c0, c1);
   lp_range(L.row0, lp, L.m, r0, r1);
   for (int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c1; j += stride) {
-    if (xo) xo[j] = beta * L.Dc[j] * L.xbar[j];
+    if (xo) xo[j] = beta * L.Dc[j] * xs[j];
     if (zo) zo[j] = gamma * L.zbar[j] / L.Dc[j];
   }
   if (yo)
     for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += stride)
-      yo[i] = gamma * L.Dr[i] * L.ybar[i];
+      yo[i] = gamma * L.Dr[i] * ys[i];
 }
 
 // unscaled product (matvec entry point)

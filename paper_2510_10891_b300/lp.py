@@ -23,6 +23,8 @@ def default_params(**kw) -> L.SolveParams:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": L.FP64, "mixed": L.MIXED}[v]
+        if k == "algo" and isinstance(v, str):
+            v = L.ALGO[v]
         if not hasattr(p, k):
             raise TypeError("unknown solve parameter %r" % k)
         setattr(p, k, v)
