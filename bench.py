@@ -375,12 +375,13 @@ def main():
     if rank == 0 and not args.no_plain:
         # the same LP from cold start on the same GPU: plain FP64 and FP32
         # matvecs (solve + fix, as in the step)
-        def timed(prec):
+        def timed(prec, **extra):
             lp.set_bounds(xl0, xu0)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            pi = lp.solve_device(x_out=xo, y_out=yo, z_out=zo, tol=1e-4, precision=prec, time_limit_s=600.0)
+            pi = lp.solve_device(x_out=xo, y_out=yo, z_out=zo, tol=1e-4, precision=prec,
+                                 **{"time_limit_s": 600.0, **extra})
             r = lp.fix_and_propagate(inst.G, inst.T, inst.u_idx, inst.v_idx, inst.w_idx, inst.u_init, xo,
                                      tau=0.1, is_int=inst.is_int)
             e1.record(stream); e1.synchronize()
@@ -396,9 +397,16 @@ def main():
         t64, p64, fix64 = timed("fp64")
         x64 = xo.clone()
         tmx, pmx, _ = timed("mixed")
+        # the second algorithm (restarted PDHG with ergodic averaging) and the
+        # cost of infeasibility detection, same start and precision
+        tpd, ppd, _ = timed("mixed", algo="pdhg_avg", time_limit_s=120.0)
+        tdt, pdt, _ = timed("mixed", infeas_tol=1e-8)
         v = {"plain_fp64_s": t64, "plain_fp64_iters": p64["iters"], "plain_fp64_status": p64["status_name"],
              "cold_mixed_s": tmx, "cold_mixed_iters": pmx["iters"],
-             "speedup_vs_plain_fp64": t64 / per_step}
+             "speedup_vs_plain_fp64": t64 / per_step,
+             "pdhg_avg_cold_mixed": {"s": tpd, "iters": ppd["iters"], "status": ppd["status_name"],
+                                     "kkt": ppd["kkt"], "restarts": ppd["restarts"]},
+             "cold_mixed_with_detection": {"s": tdt, "iters": pdt["iters"], "status": pdt["status_name"]}}
         if warm:
             v["warm_mixed_s"] = per_step
             v["warm_mixed_iters"] = last["iters"]
