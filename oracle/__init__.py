@@ -227,3 +227,65 @@ def reduce(src, xl, xu):
                c=c[:nr].copy(), lo=lo[:mr].copy(), hi=hi[:mr].copy(), xl=xlr[:nr].copy(),
                xu=xur[:nr].copy())
     return red, rmap[:mr].copy(), cmap[:nr].copy(), oc.value, int(bad)
+
+
+# ---------------------------------------------------------------------------
+# Transmission filtering (Fig. 1): solve without the network security rows,
+# add the violated ones, re-solve from the previous point, until none is
+# violated.  Plain definitions on the unscaled LP.
+# ---------------------------------------------------------------------------
+def row_violations(pool, x, tol):
+    """Rows i of ``pool`` violated at x: lo_i - a_i x > tol (1 + |lo_i|) or
+    a_i x - hi_i > tol (1 + |hi_i|).  Returns the row indices (ascending) and
+    the largest relative violation (0 when none)."""
+    d = as_lp(pool)
+    import scipy.sparse as sp
+    A = sp.csr_matrix((d["val"], d["col"], d["row_ptr"]), shape=(d["m"], d["n"]))
+    ax = A @ _f64(x)
+    rows, worst = [], 0.0
+    for i in range(d["m"]):
+        lo, hi = d["lo"][i], d["hi"][i]
+        v = 0.0
+        if np.isfinite(lo) and lo - ax[i] > 0.0:
+            v = (lo - ax[i]) / (1.0 + abs(lo))
+        if np.isfinite(hi) and ax[i] - hi > 0.0:
+            v = max(v, (ax[i] - hi) / (1.0 + abs(hi)))
+        if v > tol:
+            rows.append(i)
+        worst = max(worst, v)
+    return np.asarray(rows, dtype=np.int32), worst
+
+
+def add_rows(base, pool, rows):
+    """The LP with base's rows followed by pool rows ``rows`` (in that order);
+    columns, costs and bounds are base's."""
+    b, p = as_lp(base), as_lp(pool)
+    rows = np.asarray(rows, dtype=np.int64)
+    lens = p["row_ptr"][rows + 1] - p["row_ptr"][rows]
+    rp = np.concatenate([b["row_ptr"], b["row_ptr"][-1] + np.cumsum(lens)]).astype(np.int64)
+    col = np.concatenate([b["col"]] + [p["col"][p["row_ptr"][r]:p["row_ptr"][r + 1]] for r in rows])
+    val = np.concatenate([b["val"]] + [p["val"][p["row_ptr"][r]:p["row_ptr"][r + 1]] for r in rows])
+    return dict(m=b["m"] + len(rows), n=b["n"], row_ptr=rp, col=col.astype(np.int32), val=val,
+                c=b["c"].copy(), xl=b["xl"].copy(), xu=b["xu"].copy(),
+                lo=np.concatenate([b["lo"], p["lo"][rows]]), hi=np.concatenate([b["hi"], p["hi"][rows]]))
+
+
+def transmission_filter(base, pool, viol_tol=1e-6, max_rounds=20, **params):
+    """Solve base, then repeatedly add the pool rows violated by the solution
+    (each at most once) and re-solve from the previous (x, y) with y = 0 on
+    the new rows.  Returns the last LP, its solve and the rounds."""
+    lp, x, y = as_lp(base), None, None
+    added = np.zeros(as_lp(pool)["m"], dtype=bool)
+    rounds = []
+    for _ in range(max_rounds):
+        r = hpr_solve(lp, x_init=x, y_init=y, **params)
+        viol, worst = row_violations(pool, r["x"], viol_tol)
+        new = viol[~added[viol]]
+        rounds.append(dict(m=lp["m"], iters=r["info"]["iters"], status=r["info"]["status"], violated=len(viol),
+                           added=len(new), max_violation=worst))
+        if len(new) == 0:
+            return dict(lp=lp, result=r, rounds=rounds, converged=len(viol) == 0)
+        added[new] = True
+        lp = add_rows(lp, pool, new)
+        x, y = r["x"], np.concatenate([r["y"], np.zeros(len(new))])
+    return dict(lp=lp, result=r, rounds=rounds, converged=False)

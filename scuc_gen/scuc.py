@@ -557,3 +557,29 @@ def make_scuc(cfg: SCUCConfig) -> SCUCInstance:
 def make_preset(name: str, **overrides) -> SCUCInstance:
     cfg = dataclasses.replace(PRESETS[name], **overrides)
     return make_scuc(cfg)
+
+
+def split_network_rows(inst: SCUCInstance):
+    """The transmission-filtering split of an instance (Fig. 1 of the paper):
+    ``base`` holds every row except the network security rows (base-case
+    line rows and N-1 rows), ``pool`` holds those rows over the same columns.
+    Both are LP dicts (row box form); ``pool_rows`` are the pool rows'
+    indices in the full instance.  Pure data selection."""
+    lo, hi = inst.row_bounds()
+    blocks = inst.params["row_blocks"]
+    net = np.zeros(inst.m, dtype=bool)
+    for name in ("line", "ctg"):
+        a, b = blocks[name]
+        net[a:b] = True
+    A = inst.csr()
+
+    def part(sel):
+        S = A[sel].tocsr()
+        S.sort_indices()
+        return dict(m=S.shape[0], n=inst.n, row_ptr=S.indptr.astype(np.int64), col=S.indices.astype(np.int32),
+                    val=S.data.astype(np.float64), c=inst.c.copy(), xl=inst.xl.copy(), xu=inst.xu.copy(),
+                    lo=lo[sel].copy(), hi=hi[sel].copy())
+
+    base_rows = np.flatnonzero(~net)
+    pool_rows = np.flatnonzero(net)
+    return part(base_rows), part(pool_rows), pool_rows
