@@ -283,6 +283,30 @@ int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_par
                         scuc_solve_info* infos, scuc_batch_info* binfo);
 
 /* ---------------------------------------------------------------------- */
+/* Transmission filtering (Fig. 1): the LP is solved without the network    */
+/* security rows; the rows of a pool that the solution violates are added   */
+/* and the LP is re-solved from the previous point, until none is violated. */
+/* ---------------------------------------------------------------------- */
+/* Rows of the pool LP (its rows, same columns as the LP being filtered)
+ * violated at x: lo_i - a_i x > tol (1 + |lo_i|) or a_i x - hi_i > tol (1 +
+ * |hi_i|) over the finite bounds (a_i x in FP64, unscaled values).
+ *  x[n]: host (x_on_device = 0) or device pointer on the pool's device.
+ *  rows_out[cap]: receives the first min(count, cap) violated row indices
+ *    in increasing order (host); *count_out the number violated (may exceed
+ *    cap); *worst_out (may be NULL) the largest relative violation, 0 when
+ *    none.  SCUC_E_INVALID for a null handle or x, cap < 0, tol < 0.  */
+int scuc_lp_row_violations(scuc_lp* pool, const double* x, int32_t x_on_device, double tol, int32_t* rows_out,
+                           int32_t cap, int32_t* count_out, double* worst_out);
+
+/* A new LP with base's rows followed by the pool rows rows[count] (in that
+ * order, host array, repeats allowed); costs and column bounds are base's
+ * current ones.  Built on the device from device copies; *out is a new
+ * handle on base's stream (caller destroys it).  SCUC_E_INVALID when the
+ * pool has another column count or device, or a row is out of range
+ * (nothing is created).                                                  */
+int scuc_lp_add_rows(scuc_lp* base, scuc_lp* pool, const int32_t* rows, int32_t count, scuc_lp** out);
+
+/* ---------------------------------------------------------------------- */
 /* Logic-driven fixing and presolve (Sec. 4.1 Round + Algorithm 1; the      */
 /* MILP-/LP-Presolve steps of Algorithm 2, Sec. 4.2)                        */
 /* ---------------------------------------------------------------------- */

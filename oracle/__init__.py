@@ -276,7 +276,7 @@ def transmission_filter(base, pool, viol_tol=1e-6, max_rounds=20, **params):
     the new rows.  Returns the last LP, its solve and the rounds."""
     lp, x, y = as_lp(base), None, None
     added = np.zeros(as_lp(pool)["m"], dtype=bool)
-    rounds = []
+    rounds, order = [], []
     for _ in range(max_rounds):
         r = hpr_solve(lp, x_init=x, y_init=y, **params)
         viol, worst = row_violations(pool, r["x"], viol_tol)
@@ -284,8 +284,10 @@ def transmission_filter(base, pool, viol_tol=1e-6, max_rounds=20, **params):
         rounds.append(dict(m=lp["m"], iters=r["info"]["iters"], status=r["info"]["status"], violated=len(viol),
                            added=len(new), max_violation=worst))
         if len(new) == 0:
-            return dict(lp=lp, result=r, rounds=rounds, converged=len(viol) == 0)
+            return dict(lp=lp, result=r, rounds=rounds, converged=len(viol) == 0,
+                        rows_added=np.asarray(order, dtype=np.int32))
         added[new] = True
+        order.extend(new.tolist())
         lp = add_rows(lp, pool, new)
         x, y = r["x"], np.concatenate([r["y"], np.zeros(len(new))])
-    return dict(lp=lp, result=r, rounds=rounds, converged=False)
+    return dict(lp=lp, result=r, rounds=rounds, converged=False, rows_added=np.asarray(order, dtype=np.int32))

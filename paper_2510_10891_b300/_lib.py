@@ -122,6 +122,9 @@ _SIGS = {
     "scuc_lp_set_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "scuc_lp_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_lp_row_violations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
+                                         C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "scuc_lp_add_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "scuc_lp_destroy": (None, [C.c_void_p]),
     "scuc_ws_default_train_params": (None, [C.POINTER(WsTrainParams)]),
     "scuc_ws_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_void_p]),

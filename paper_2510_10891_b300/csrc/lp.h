@@ -107,6 +107,9 @@ struct Handle {
   int kkt_noalloc(const double* x, const double* y, const double* z, double* out);
   int fix_and_propagate(const scuc_map& map, const uint8_t* is_int, const double* x, const scuc_fix_params& p,
                         int8_t* fix_out, Handle** reduced, int32_t* col_map, int32_t* row_map, scuc_fix_info* info);
+  int row_violations(const double* x, int on_device, double tol, int32_t* rows_out, int32_t cap, int32_t* count_out,
+                     double* worst_out);
+  int add_rows(const Handle& pool, const int32_t* rows, int32_t count, Handle** out);
   int get_bounds(double* xl, double* xu);
   int set_bounds(const double* xl, const double* xu, int on_device);
   int export_lp(int64_t* row_ptr, int32_t* col, double* val, double* c, double* xl, double* xu, double* lo,

@@ -139,6 +139,29 @@ class LP:
                                        C.c_void_p(out.data_ptr())))
         return out
 
+    # ----- transmission filtering (Fig. 1) -----
+
+    def row_violations(self, x, tol=1e-6, cap=None):
+        """Rows of this LP (a pool of candidate rows) violated at x (numpy
+        array, or torch CUDA float64 tensor): (row indices ascending, largest
+        relative violation)."""
+        cap = self.m if cap is None else int(cap)
+        out = np.zeros(max(cap, 1), dtype=np.int32)
+        cnt, worst = C.c_int32(), C.c_double()
+        on_dev = not isinstance(x, np.ndarray)
+        xp = C.c_void_p(x.data_ptr()) if on_dev else _ptr(_f64(x))
+        L.check(L.lib().scuc_lp_row_violations(self.h, xp, 1 if on_dev else 0, float(tol),
+                                               C.c_void_p(out.ctypes.data), cap, C.byref(cnt), C.byref(worst)))
+        return out[:min(cnt.value, cap)].copy(), worst.value
+
+    def add_rows(self, pool: "LP", rows) -> "LP":
+        """A new LP: this LP's rows followed by the pool rows ``rows``."""
+        r = np.ascontiguousarray(rows, dtype=np.int32)
+        h = C.c_void_p()
+        L.check(L.lib().scuc_lp_add_rows(self.h, pool.h, C.c_void_p(r.ctypes.data) if len(r) else None,
+                                         len(r), C.byref(h)))
+        return LP._adopt(h)
+
     # ----- fixing + presolve (Sec. 4.1-4.2) -----
 
     @classmethod
