@@ -57,10 +57,15 @@ def spmv_bytes(m, n, nnz_a, kind, prec):
     return (vb + 4) * nnz_a + 4 * (n + 1) + vb * m + 40 * n + 8 * n + (8 * n if vb == 8 else 4 * n)
 
 
+# sources the iteration SpMV kernels are built from (kernels, partition
+# planner, launch shapes): the stored DRAM traffic is valid while they are
+SPMV_SOURCES = ("common.cuh", "spmv.cuh", "lp_kernels.cuh", "lp.cu")
+
+
 def csrc_hash():
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2510_10891_b300", "csrc", "*"))):
-        with open(p, "rb") as f:
+    for name in SPMV_SOURCES:
+        with open(os.path.join(ROOT, "paper_2510_10891_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -241,6 +246,9 @@ def main():
     ap.add_argument("--ncu-case", default=None,
                     help="profiling target: 128 mixed-precision iterations (FP32 matvecs, no graph) "
                          "on this preset, no JSON line")
+    ap.add_argument("--ncu-fix", default=None,
+                    help="profiling target: one fixing round (Round, Algorithm 1, propagation, reduced LP) "
+                         "on this preset after a mixed-precision solve to 1e-4, no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -251,6 +259,20 @@ def main():
         r = lp.solve(want=("x",), tol=0.0, max_iter=128, use_graph=0, precision="mixed",
                      polish_stall=10 ** 6, polish_factor=0.0)
         print("ncu case %s: %d iterations" % (args.ncu_case, r["info"]["iters"]))
+        return 0
+    if args.ncu_fix:
+        import paper_2510_10891_b300 as P
+        from scuc_gen import make_preset
+        inst = make_preset(args.ncu_fix)
+        lp = P.LP(inst)
+        x = lp.solve(want=("x",), tol=1e-4, precision="mixed")["x"]
+        f = lp.fix_and_propagate(inst.G, inst.T, inst.u_idx, inst.v_idx, inst.w_idx, inst.u_init, x, tau=0.1,
+                                 is_int=inst.is_int)
+        i = f["info"]
+        print("ncu fix %s: %d fixed, %d passes, reduced LP %s, %.1f ms" %
+              (args.ncu_fix, i["nfixed"], i["passes"], (i["m_red"], i["n_red"], i["nnz_red"]), i["ms"]))
+        if f["reduced"] is not None:
+            f["reduced"].close()
         return 0
 
     import torch

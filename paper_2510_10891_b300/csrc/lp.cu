@@ -478,10 +478,26 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
   const int npass = use_scaling == 2 ? 11 : (use_scaling == 1 ? 1 : 0);
   for (int pass = 0; pass < npass; pass++) {
     const int use_max = pass < npass - 1 ? 1 : 0;  // Ruiz passes, then the sum pass
-    if (m) k_scale_factor<<<mb, kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, 0, use_max, uv);
-    if (n) k_scale_factor<<<nb, kBlock, 0, s>>>(rpt, colt, valt, n, Dr, Dc, 1, use_max, wv);
+    if (use_max) {
+      if (m) k_scale_factor<<<mb, kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, 0, use_max, uv);
+      if (n) k_scale_factor<<<nb, kBlock, 0, s>>>(rpt, colt, valt, n, Dr, Dc, 1, use_max, wv);
+      nlaunch += (m ? 1 : 0) + (n ? 1 : 0);
+    } else {
+      // sum pass as two products on the solver's balanced partitions (long
+      // rows in chunks): |A| Dc into uv, |A^T| Dr into wv; vs and vst hold
+      // |A| and |A^T| until the scaled values overwrite them below
+      if (nnz) k_abs2<<<grid_for(nnz), kBlock, 0, s>>>(val, vs, nnz, valt, vst, nnz);
+      if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, Dc, pA);
+      if (pA.nblk) k_spmv_plain<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, Dc, pA, uv);
+      if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, Dr, pT);
+      if (pT.nblk) k_spmv_plain<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, Dr, pT, wv);
+      if (m) k_factor_from_sums<<<mb, kBlock, 0, s>>>(m, Dr, uv, uv);
+      if (n) k_factor_from_sums<<<nb, kBlock, 0, s>>>(n, Dc, wv, wv);
+      nlaunch += (nnz ? 1 : 0) + (pA.nchunk ? 1 : 0) + (pA.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0) +
+                 (pT.nblk ? 1 : 0) + (m ? 1 : 0) + (n ? 1 : 0);
+    }
     k_mul2<<<grid_for(std::max(m, n)), kBlock, 0, s>>>(Dr, uv, m, Dc, wv, n);
-    nlaunch += (m ? 1 : 0) + (n ? 1 : 0) + 1;
+    nlaunch += 1;
   }
   nlaunch += 1 + (m ? 1 : 0) + (nnz ? 1 : 0) + 4;
   if (m) k_scale_vals<<<grid_for((int64_t)m * 32), kBlock, 0, s>>>(rp, col, val, m, Dr, Dc, vs);

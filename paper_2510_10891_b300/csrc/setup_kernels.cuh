@@ -135,7 +135,9 @@ __global__ void k_fill(double* __restrict__ a, int na, double* __restrict__ b, i
 // Factor of one scaling pass for each row of a CSR (thread per row,
 // sequential in entry order): 1/sqrt(max) (Ruiz) or 1/sqrt(sum) (Pock-
 // Chambolle) of |(Dr[row] * a) * Dc[col]| over the row, 1 for empty rows.
-// transposed = 1: the CSR is A^T (rows are columns of A).
+// transposed = 1: the CSR is A^T (rows are columns of A).  The solver runs
+// it for the Ruiz passes; its sum passes run as products (k_abs2 +
+// k_factor_from_sums), which balance the long rows.
 __global__ void k_scale_factor(const int* __restrict__ rp, const int* __restrict__ col,
                                const double* __restrict__ val, int m, const double* __restrict__ Dr,
                                const double* __restrict__ Dc, int transposed, int use_max,
@@ -149,6 +151,24 @@ __global__ void k_scale_factor(const int* __restrict__ rp, const int* __restrict
     else s += a;
   }
   out[i] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+}
+
+// |a| and |b| elementwise (the absolute matrix values of a sum pass)
+__global__ void k_abs2(const double* __restrict__ a, double* __restrict__ oa, int64_t na,
+                       const double* __restrict__ b, double* __restrict__ ob, int64_t nb) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += stride) oa[i] = fabs(a[i]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) ob[i] = fabs(b[i]);
+}
+
+// Factor of a sum pass from the row sums of |A| weighted by the other side's
+// D: sum_j |D_i a_ij D'_j| = D_i sum_j |a_ij| D'_j (D > 0), so the factor is
+// 1/sqrt(D_i * s_i), 1 for empty rows.  In place (out may be s).
+__global__ void k_factor_from_sums(int m, const double* __restrict__ D, const double* s, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const double v = D[i] * s[i];
+  out[i] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
 }
 
 __global__ void k_mul2(double* __restrict__ a, const double* __restrict__ fa, int na, double* __restrict__ b,
