@@ -57,9 +57,9 @@ def spmv_bytes(m, n, nnz_a, kind, prec):
     return (vb + 4) * nnz_a + 4 * (n + 1) + vb * m + 40 * n + 8 * n + (8 * n if vb == 8 else 4 * n)
 
 
-# sources the iteration SpMV kernels are built from (kernels, partition
-# planner, launch shapes): the stored DRAM traffic is valid while they are
-SPMV_SOURCES = ("common.cuh", "spmv.cuh", "lp_kernels.cuh", "lp.cu")
+# sources the iteration SpMV kernels are built from (kernels and the
+# partition planner): the stored DRAM traffic is valid while they are
+SPMV_SOURCES = ("common.cuh", "spmv.cuh", "lp_kernels.cuh", "partition.cu")
 
 
 def csrc_hash():

@@ -44,110 +44,8 @@ static int grid_for(int64_t work, int block = kBlock) {
   return (int)g;
 }
 
-// Host plan of a partition (see Partition): rows with more than kGroupRowMax
-// nonzeros are cut into chunks of kChunk entries when allow_long, else they
-// join the 32-thread list rows; rows of kShortMax+1..kGroupRowMax nonzeros
-// get a group of group_size_for(len, shape.ept) threads; runs of at least
-// shape.min_run consecutive short rows are packed into staged blocks of <=
-// kMaxRows rows / <= kNnzCap nonzeros (threads per row = largest power of
-// two with gsz * rows <= kBlock), shorter runs go to 4-thread list rows.
-// List classes run from 32 threads per row down to 4 (longest work first),
-// then the staged blocks, then the long rows.
-void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan) {
-  std::vector<int> G[4];  // G[k]: list rows with 32 >> k threads per row
-  *plan = PartPlan{};
-  plan->chunk_ptr.assign(1, 0);
-  auto cls = [](int gsz) { return gsz == 32 ? 0 : gsz == 16 ? 1 : gsz == 8 ? 2 : 3; };
-  auto flush_run = [&](int a, int b) {  // short rows [a, b)
-    if (b - a < shape.min_run) {
-      for (int r = a; r < b; r++) G[3].push_back(r);
-      return;
-    }
-    int r = a;
-    while (r < b) {
-      const int start = r;
-      int nz = 0;
-      while (r < b && r - start < kMaxRows && nz + (rp[r + 1] - rp[r]) <= kNnzCap) {
-        nz += rp[r + 1] - rp[r];
-        r++;
-      }
-      const int nr = r - start;
-      int g = 1;
-      while (g < 32 && g * 2 * nr <= kBlock) g *= 2;
-      plan->desc.push_back(make_int4(start, rp[start], rp[r], (nr << 8) | g));
-    }
-  };
-  int run0 = 0;
-  for (int r = 0; r < m; r++) {
-    const int len = rp[r + 1] - rp[r];
-    if (len <= kShortMax) continue;
-    flush_run(run0, r);
-    run0 = r + 1;
-    if (len > kGroupRowMax && allow_long) {
-      plan->long_rows.push_back(r);
-      for (int e = rp[r]; e < rp[r + 1]; e += kChunk)
-        plan->chunks.push_back(make_int2(e, std::min(rp[r + 1], e + kChunk)));
-      plan->chunk_ptr.push_back((int)plan->chunks.size());
-    } else {
-      G[cls(len > kGroupRowMax ? 32 : group_size_for(len, shape.ept))].push_back(r);
-    }
-  }
-  flush_run(run0, m);
-  for (int k = 0; k < 4; k++) {
-    plan->cls_row[k] = (int)plan->listx.size();
-    for (int r : G[k]) plan->listx.push_back(make_int4(r, rp[r], rp[r + 1], 0));
-    plan->cls_blk[k + 1] = plan->cls_blk[k] + (int)((G[k].size() + (kBlock >> (5 - k)) - 1) / (kBlock >> (5 - k)));
-  }
-  plan->cls_row[4] = (int)plan->listx.size();
-}
-
-// device copies of a planned partition (freed by free_partition)
-int upload_partition(const PartPlan& plan, Partition* P) {
-  *P = Partition{};
-  for (int k = 0; k < 5; k++) {
-    P->cls_blk[k] = plan.cls_blk[k];
-    P->cls_row[k] = plan.cls_row[k];
-  }
-  P->nstaged = (int)plan.desc.size();
-  P->nlong = (int)plan.long_rows.size();
-  P->nchunk = (int)plan.chunks.size();
-  P->nchunkblk = (P->nchunk + kBlock / 32 - 1) / (kBlock / 32);
-  P->nblk = plan.cls_blk[4] + P->nstaged + (P->nlong + kBlock - 1) / kBlock;
-  SCUC_TRY(dalloc(&P->listx, plan.listx.size()));
-  SCUC_TRY(dalloc(&P->desc, plan.desc.size()));
-  SCUC_TRY(dalloc(&P->chunks, plan.chunks.size()));
-  SCUC_TRY(dalloc(&P->long_rows, plan.long_rows.size()));
-  SCUC_TRY(dalloc(&P->chunk_ptr, plan.long_rows.size() + 1));
-  SCUC_TRY(dalloc(&P->cpart, plan.chunks.size()));
-  if (!plan.slot.empty()) SCUC_TRY(dalloc(&P->slot, plan.slot.size()));
-  auto up = [](void* dst, const void* src, size_t bytes) {
-    return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
-  };
-  SCUC_CUDA(up(P->listx, plan.listx.data(), plan.listx.size() * sizeof(int4)));
-  SCUC_CUDA(up(P->desc, plan.desc.data(), plan.desc.size() * sizeof(int4)));
-  SCUC_CUDA(up(P->chunks, plan.chunks.data(), plan.chunks.size() * sizeof(int2)));
-  SCUC_CUDA(up(P->long_rows, plan.long_rows.data(), plan.long_rows.size() * sizeof(int)));
-  SCUC_CUDA(up(P->chunk_ptr, plan.chunk_ptr.data(), plan.chunk_ptr.size() * sizeof(int)));
-  if (P->slot) SCUC_CUDA(up(P->slot, plan.slot.data(), plan.slot.size() * sizeof(int)));
-  return SCUC_OK;
-}
-
-void free_partition(Partition* P) {
-  for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
-                  (void*)P->cpart, (void*)P->slot})
-    if (q) cudaFree(q);
-  *P = Partition{};
-}
-
-int build_partition(const std::vector<int>& rp, int m, Partition* P) {
-  PartPlan plan;
-  plan_partition(rp, m, PartShape{}, true, &plan);
-  return upload_partition(plan, P);
-}
-
-// exclusive scan of n ints into out[0..n] (out[n] = total), recursive
-// out[0..n] = exclusive prefix sums of in[0..n-1], out[n] the total; stream
-// ordered on s, no host synchronisation
+// out[0..n] = exclusive prefix sums of in[0..n-1], out[n] the total
+// (recursive over block sums); stream ordered on s, no host synchronisation
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s) {
   const int nb = (n + kScan - 1) / kScan;
   int* scratch = nullptr;  // block sums (nb), their offsets (nb + 1)
