@@ -430,18 +430,31 @@ int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters
   SCUC_CUDA(cudaMemcpyAsync(pctrl, &P0, sizeof(PowerCtrl), cudaMemcpyHostToDevice, s));
   k_power_seed<<<kNormBlocks, kBlock, 0, s>>>(n, p.power_seed, qv, partRT);
   k_power_seed_norm<<<1, kDecideThreads, 0, s>>>(partRT, kNormBlocks, pctrl);
-  k_power_norm_seed<<<grid_for(n), kBlock, 0, s>>>(n, qv, pctrl);
+  // MIXED solves run the products in FP32 (values vs32 / vst32; q in xt32,
+  // u = A q in y32: both unused until the iterations start)
+  const bool f32 = p.precision == SCUC_MIXED && vs32 && vst32;
+  float* q32 = f32 ? xt32 : nullptr;
+  k_power_norm_seed<<<grid_for(n), kBlock, 0, s>>>(n, qv, q32, pctrl);
   nlaunch += 3;
   SCUC_CUDA(cudaGetLastError());
   PowerCtrl P{};
   for (int it = 0; it < p.power_max_iter; it += 16) {
     for (int j = 0; j < 16; j++) {
-      if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA);
-      if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
-      if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, uv, pT);
-      if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
+      if (f32) {
+        if (pA.nchunk) k_chunk_sums<float><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs32, q32, pA);
+        if (pA.nblk)
+          k_power_spmv32<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs32, q32, pA, nullptr, y32, partRA, pctrl);
+        if (pT.nchunk) k_chunk_sums<float><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst32, y32, pT);
+        if (pT.nblk)
+          k_power_spmv32<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst32, y32, pT, wv, xt32, partRT, pctrl);
+      } else {
+        if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA);
+        if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
+        if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, uv, pT);
+        if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
+      }
       k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);
-      k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, pctrl);
+      k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, q32, pctrl);
       nlaunch += 2 + (pA.nblk ? 1 : 0) + (pT.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0) + (pT.nchunk ? 1 : 0);
     }
     SCUC_CUDA(cudaGetLastError());

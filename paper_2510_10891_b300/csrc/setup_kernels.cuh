@@ -335,6 +335,34 @@ __global__ void __launch_bounds__(kBlock) k_power_spmv(const int* __restrict__ r
   block_store<1>(epi.acc, psum, part);
 }
 
+// FP32 products for MIXED solves (FP32 values and vectors, FP32 sums; the
+// squares and norms in FP64): out32 = the product, out (may be null) its
+// FP64 copy
+struct StoreEpi32 {
+  double* out;
+  float* out32;
+  double acc[1];
+  __device__ void load(int) {}
+  __device__ void row(int r, float a) {
+    const double d = (double)a;
+    if (out) out[r] = d;
+    out32[r] = a;
+    acc[0] += d * d;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_power_spmv32(const int* __restrict__ rp, const int* __restrict__ col,
+                                                         const float* __restrict__ val,
+                                                         const float* __restrict__ in, Partition part,
+                                                         double* __restrict__ out, float* __restrict__ out32,
+                                                         double* __restrict__ psum, const PowerCtrl* __restrict__ P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (P->done) return;
+  StoreEpi32 epi{out, out32, {0.0}};
+  spmv_block<float>(rp, col, val, in, part, smem, epi);
+  block_store<1>(epi.acc, psum, part);
+}
+
 __global__ void __launch_bounds__(kDecideThreads) k_power_decide(const double* pu, int nA, const double* pw,
                                                                  int nT, PowerCtrl* P) {
   if (P->done) return;
@@ -351,18 +379,28 @@ __global__ void __launch_bounds__(kDecideThreads) k_power_decide(const double* p
   P->lam_prev = lam;
 }
 
-// q = w / ||w||  (not needed once the estimate is final)
-__global__ void k_power_norm(int n, const double* __restrict__ w, double* __restrict__ q, const PowerCtrl* P) {
+// q = w / ||w||  (not needed once the estimate is final); q32 (may be null)
+// its FP32 copy for FP32 products
+__global__ void k_power_norm(int n, const double* __restrict__ w, double* __restrict__ q, float* __restrict__ q32,
+                             const PowerCtrl* P) {
   if (P->done) return;
   const double nw = P->nw;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) q[j] = w[j] / nw;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const double v = w[j] / nw;
+    q[j] = v;
+    if (q32) q32[j] = (float)v;
+  }
 }
 
-__global__ void k_power_norm_seed(int n, double* __restrict__ q, const PowerCtrl* P) {
+__global__ void k_power_norm_seed(int n, double* __restrict__ q, float* __restrict__ q32, const PowerCtrl* P) {
   const double nq = P->nw;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) q[j] /= nq;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const double v = q[j] / nq;
+    q[j] = v;
+    if (q32) q32[j] = (float)v;
+  }
 }
 
 // ------------------------ iterate init / output ---------------------------
