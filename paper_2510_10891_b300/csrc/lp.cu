@@ -6,7 +6,9 @@
 #include <cstring>
 #include <chrono>
 #include <string>
+#include <thread>
 #include <vector>
+#include <algorithm>
 
 #include "lp.h"
 #include "setup_kernels.cuh"
@@ -88,9 +90,108 @@ int Handle::alloc(T** p, size_t count) {
 // ---------------------------------------------------------------------------
 // validation (host, before any launch)
 // ---------------------------------------------------------------------------
-static int validate(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
-                    const double* val, const double* c, const double* xl, const double* xu,
-                    const double* lo, const double* hi) {
+// Input rules of scuc_lp_create, checked on the host before any kernel runs.
+// Sizes, pointers and the row pointers first (so no entry outside [0, nnz)
+// is read), then the entries and bounds in row / column chunks on host
+// threads; the error reported is the one of the first failing row (then
+// column), as a sequential pass would find it.
+namespace {
+
+struct CheckResult {
+  int64_t where = -1;  // first failing row / column of the chunk, -1: none
+  std::string msg;
+};
+
+void check_rows(int32_t i0, int32_t i1, int32_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                const double* lo, const double* hi, CheckResult* r) {
+  char buf[160];
+  for (int32_t i = i0; i < i1; i++) {
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+      if (col[e] < 0 || col[e] >= n || (e > row_ptr[i] && col[e] <= col[e - 1])) {
+        snprintf(buf, sizeof(buf), "column index out of range or not increasing in row %d", i);
+        r->where = i;
+        r->msg = buf;
+        return;
+      }
+      if (!std::isfinite(val[e])) {
+        snprintf(buf, sizeof(buf), "non-finite matrix value in row %d", i);
+        r->where = i;
+        r->msg = buf;
+        return;
+      }
+    }
+    if (std::isnan(lo[i]) || std::isnan(hi[i]) || lo[i] > hi[i] || lo[i] == INFINITY || hi[i] == -INFINITY) {
+      snprintf(buf, sizeof(buf), "invalid row bounds at row %d", i);
+      r->where = i;
+      r->msg = buf;
+      return;
+    }
+  }
+}
+
+void check_cols(int32_t j0, int32_t j1, const double* c, const double* xl, const double* xu, CheckResult* r) {
+  char buf[160];
+  for (int32_t j = j0; j < j1; j++)
+    if (!std::isfinite(c[j]) || std::isnan(xl[j]) || std::isnan(xu[j]) || xl[j] > xu[j] || xl[j] == INFINITY ||
+        xu[j] == -INFINITY) {
+      snprintf(buf, sizeof(buf), "invalid cost or bounds at column %d", j);
+      r->where = j;
+      r->msg = buf;
+      return;
+    }
+}
+
+}  // namespace
+
+// Entries, row boxes and columns checked by up to 32 host threads (row
+// chunks of about equal nonzeros).  Runs while the caller copies the arrays
+// to the device; join() returns the first error.
+struct Validator {
+  std::vector<std::thread> threads;
+  std::vector<CheckResult> rows, cols;
+  void start(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const double* val,
+             const double* c, const double* xl, const double* xu, const double* lo, const double* hi) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    int k = (int)std::min<int64_t>(std::max<unsigned>(hw, 1u), 32);
+    if (nnz + m + n < (int64_t)1 << 20) k = 1;
+    rows.assign(k, CheckResult{});
+    cols.assign(k, CheckResult{});
+    int32_t r0 = 0;
+    for (int t = 0; t < k; t++) {
+      // last row of chunk t: the first row whose start reaches (t+1)/k of the entries
+      int32_t r1 = t == k - 1 ? m
+                              : (int32_t)(std::lower_bound(row_ptr, row_ptr + m + 1, nnz * (t + 1) / k) - row_ptr);
+      r1 = std::max(r0, std::min(r1, m));
+      const int32_t c0 = (int32_t)((int64_t)n * t / k), c1 = (int32_t)((int64_t)n * (t + 1) / k);
+      threads.emplace_back([=] {
+        check_rows(r0, r1, n, row_ptr, col, val, lo, hi, &rows[t]);
+        check_cols(c0, c1, c, xl, xu, &cols[t]);
+      });
+      r0 = r1;
+    }
+  }
+  int join() {
+    for (auto& th : threads) th.join();
+    threads.clear();
+    for (const auto* v : {&rows, &cols})
+      for (const CheckResult& r : *v)
+        if (r.where >= 0) {
+          set_error("%s", r.msg.c_str());
+          return SCUC_E_INVALID;
+        }
+    return SCUC_OK;
+  }
+  ~Validator() {
+    for (auto& th : threads)
+      if (th.joinable()) th.join();
+  }
+};
+
+
+// sizes, pointers and the row pointers (nondecreasing from 0 to nnz)
+static int validate_shape(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                          const double* val, const double* c, const double* xl, const double* xu, const double* lo,
+                          const double* hi) {
   if (m < 0 || n < 0 || nnz < 0 || nnz >= (int64_t)INT32_MAX) {
     set_error("invalid sizes m=%d n=%d nnz=%lld", m, n, (long long)nnz);
     return SCUC_E_INVALID;
@@ -104,46 +205,24 @@ static int validate(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, c
     set_error("row_ptr[0] must be 0 and row_ptr[m] must equal nnz");
     return SCUC_E_INVALID;
   }
-  for (int32_t i = 0; i < m; i++) {
+  for (int32_t i = 0; i < m; i++)
     if (row_ptr[i + 1] < row_ptr[i]) {
       set_error("row_ptr decreases at row %d", i);
       return SCUC_E_INVALID;
     }
-    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
-      if (col[e] < 0 || col[e] >= n || (e > row_ptr[i] && col[e] <= col[e - 1])) {
-        set_error("column index out of range or not increasing in row %d", i);
-        return SCUC_E_INVALID;
-      }
-      if (!std::isfinite(val[e])) {
-        set_error("non-finite matrix value in row %d", i);
-        return SCUC_E_INVALID;
-      }
-    }
-    if (std::isnan(lo[i]) || std::isnan(hi[i]) || lo[i] > hi[i] || lo[i] == INFINITY ||
-        hi[i] == -INFINITY) {
-      set_error("invalid row bounds at row %d", i);
-      return SCUC_E_INVALID;
-    }
-  }
-  for (int32_t j = 0; j < n; j++) {
-    if (!std::isfinite(c[j]) || std::isnan(xl[j]) || std::isnan(xu[j]) || xl[j] > xu[j] ||
-        xl[j] == INFINITY || xu[j] == -INFINITY) {
-      set_error("invalid cost or bounds at column %d", j);
-      return SCUC_E_INVALID;
-    }
-  }
   return SCUC_OK;
 }
 
-// ---------------------------------------------------------------------------
-// creation: copies, transpose on the device, partitions
-// ---------------------------------------------------------------------------
 int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
                   const int32_t* col, const double* val, const double* c, const double* xl,
                   const double* xu, const double* lo, const double* hi, void* stream) {
-  SCUC_TRY(validate(m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi));
+  SCUC_TRY(validate_shape(m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi));
+  // the entries are checked while they are copied; no kernel runs before the
+  // check has passed
+  Validator V;
+  V.start(m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi);
   Handle* H = new Handle();
-  int rc = H->init(m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi, (cudaStream_t)stream);
+  int rc = H->init(m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi, (cudaStream_t)stream, &V);
   if (rc != SCUC_OK) {
     delete H;
     return rc;
@@ -154,7 +233,7 @@ int create_handle(Handle** out, int32_t m, int32_t n, int64_t nnz, const int64_t
 
 int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, const int32_t* col_,
                  const double* val_, const double* c_, const double* xl_, const double* xu_,
-                 const double* lo_, const double* hi_, cudaStream_t user_) {
+                 const double* lo_, const double* hi_, cudaStream_t user_, Validator* check) {
   SCUC_TRY(begin(m_, n_, nnz_, user_));
   cudaStream_t s = work;
 
@@ -182,6 +261,7 @@ int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, c
     SCUC_CUDA(cudaMemcpyAsync(lo, lo_, m * sizeof(double), cudaMemcpyHostToDevice, s));
     SCUC_CUDA(cudaMemcpyAsync(hi, hi_, m * sizeof(double), cudaMemcpyHostToDevice, s));
   }
+  if (check) SCUC_TRY(check->join());
   return setup_device(rp32);
 }
 

@@ -6,7 +6,8 @@
 
 namespace scuc {
 
-struct DevLP;  // device view of a handle (lp_kernels.cuh)
+struct DevLP;      // device view of a handle (lp_kernels.cuh)
+struct Validator;  // input checks of scuc_lp_create, run while the arrays are copied (lp.cu)
 
 // A^T of a matrix built elsewhere (Handle::init_device adopts the arrays)
 struct DevTranspose {
@@ -78,7 +79,7 @@ struct Handle {
   int alloc(T** p, size_t count);
   int init(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
            const double* val, const double* c, const double* xl, const double* xu,
-           const double* lo, const double* hi, cudaStream_t user);
+           const double* lo, const double* hi, cudaStream_t user, Validator* check = nullptr);
   int begin(int32_t m, int32_t n, int64_t nnz, cudaStream_t user);
   int init_device(int32_t m, int32_t n, int64_t nnz, int* d_rp, int* d_col, double* d_val, double* d_c,
                   double* d_xl, double* d_xu, double* d_lo, double* d_hi, cudaStream_t user,

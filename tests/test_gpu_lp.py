@@ -208,3 +208,49 @@ def test_scuc2k_full_size(P):
         s = lp.solve(tol=1e-4, precision=prec)
         assert s["info"]["status"] == 0, s["info"]
         assert oracle.kkt(inst, s["x"], s["y"], s["z"])["kkt"] <= 1e-4 * 1.0001
+
+
+def test_invalid_inputs_rejected_before_any_kernel(P):
+    """Malformed inputs give SCUC_E_INVALID with the first failing row or
+    column named (the entries are checked by several host threads while
+    they are copied; the first failure in row order is reported)."""
+    import scipy.sparse as sp
+    good = random_lp(40, 30, density=0.2, seed=3)
+    d0 = dict(m=good["m"], n=good["n"], row_ptr=good["row_ptr"].copy(), col=good["col"].copy(),
+              val=good["val"].copy(), c=good["c"].copy(), xl=good["xl"].copy(), xu=good["xu"].copy(),
+              sense=good["sense"].copy(), rhs=good["rhs"].copy(), rng_=good["rng_"].copy())
+    P.LP(d0).close()
+
+    def expect(d, text):
+        with pytest.raises(P._lib.ScucError) as e:
+            P.LP(d)
+        assert e.value.code == P._lib.SCUC_E_INVALID
+        assert text in str(e.value), str(e.value)
+
+    r = int(np.argmax(np.diff(d0["row_ptr"]) >= 2))      # a row with two entries
+    a = int(d0["row_ptr"][r])
+    d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in d0.items()}
+    d["col"][a], d["col"][a + 1] = d["col"][a + 1], d["col"][a]
+    expect(d, "not increasing in row %d" % r)
+    d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in d0.items()}
+    d["col"][a] = d0["n"]
+    expect(d, "out of range")
+    d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in d0.items()}
+    d["val"][a] = np.nan
+    expect(d, "non-finite matrix value in row %d" % r)
+    d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in d0.items()}
+    d["xl"][5], d["xu"][5] = 1.0, 0.0
+    expect(d, "invalid cost or bounds at column 5")
+    d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in d0.items()}
+    d["row_ptr"][3] = d["row_ptr"][4] + 1
+    expect(d, "row_ptr decreases")
+    # a large LP (several host threads): errors in two chunks, the first row is reported
+    big = sp.random(20000, 3000, density=0.02, random_state=np.random.default_rng(1), format="csr")
+    big.sort_indices()
+    db = dict(m=20000, n=3000, row_ptr=big.indptr.astype(np.int64), col=big.indices.astype(np.int32),
+              val=big.data.copy(), c=np.ones(3000), xl=np.zeros(3000), xu=np.ones(3000),
+              lo=np.full(20000, -np.inf), hi=np.full(20000, 10.0))
+    P.LP(db).close()
+    db["val"][big.indptr[17000]] = np.inf
+    db["val"][big.indptr[1234] + 1] = np.nan
+    expect(db, "non-finite matrix value in row 1234")
