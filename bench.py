@@ -244,8 +244,10 @@ def main():
     ap.add_argument("--start", default="warm", choices=["warm", "cold"],
                     help="warm: learned warm start (weights in paper_2510_10891_b300/weights)")
     ap.add_argument("--ncu-case", default=None,
-                    help="profiling target: 128 mixed-precision iterations (FP32 matvecs, no graph) "
-                         "on this preset, no JSON line")
+                    help="profiling target: 128 iterations (no graph; FP32 matvecs unless "
+                         "--ncu-precision fp64) on this preset, no JSON line")
+    ap.add_argument("--ncu-precision", default="mixed", choices=["mixed", "fp64"],
+                    help="matvec precision of the --ncu-case iterations")
     ap.add_argument("--ncu-fix", default=None,
                     help="profiling target: one fixing round (Round, Algorithm 1, propagation, reduced LP) "
                          "on this preset after a mixed-precision solve to 1e-4, no JSON line")
@@ -256,7 +258,7 @@ def main():
         import paper_2510_10891_b300 as P
         from scuc_gen import make_preset
         lp = P.LP(make_preset(args.ncu_case))
-        r = lp.solve(want=("x",), tol=0.0, max_iter=128, use_graph=0, precision="mixed",
+        r = lp.solve(want=("x",), tol=0.0, max_iter=128, use_graph=0, precision=args.ncu_precision,
                      polish_stall=10 ** 6, polish_factor=0.0)
         print("ncu case %s: %d iterations" % (args.ncu_case, r["info"]["iters"]))
         return 0

@@ -131,7 +131,9 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 // first accumulator.  Measured on the 13k-bus LP: list rows U = 12, NA = 2
 // with predication for FP32 values (U at least the 12 entries per thread of
 // the default partition, so most rows take one batch; U = 16 costs
-// occupancy), U = 4, NA = 2 without it for FP64.
+// occupancy); for FP64 values, which are bound by B300's FP64 pipe (2 DFMA
+// per clock per SM) rather than by loads in flight, U = 4 without
+// predication and a single accumulator (no combining adds).
 template <typename VT, int U, int NA, bool PRED>
 __device__ __forceinline__ VT batched_dot(const int* __restrict__ col, const VT* __restrict__ val,
                                           const VT* __restrict__ x, int e, int z, int nl) {
@@ -184,15 +186,17 @@ __device__ __forceinline__ VT group_dot(const int* __restrict__ col, const VT* _
 template <typename VT>
 __device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT* __restrict__ val,
                                            const VT* __restrict__ x, int a, int z, int li, int nl) {
-  return batched_dot<VT, sizeof(VT) == 4 ? 8 : 4, sizeof(VT) == 4 ? 8 : 2, sizeof(VT) == 4>(col, val, x,
+  return batched_dot<VT, sizeof(VT) == 4 ? 8 : 4, sizeof(VT) == 4 ? 8 : 1, sizeof(VT) == 4>(col, val, x,
                                                                                                a + li, z, nl);
 }
 
 // One warp per chunk of a long row (chunk launch): chunk w = blockIdx.x *
 // (kBlock / 32) + warp; lane-strided entries, for FP32 values one predicated
 // batch of 16 per lane (a whole 512-entry chunk; measured faster than two
-// batches of 8), for FP64 batches of 8; then a fixed warp tree; the sum goes
-// to part.cpart[w] in FP64.
+// batches of 8), for FP64 batches of 8 into one accumulator (FP64-pipe
+// bound: eight accumulators cost seven combining adds per 16 products, 20%
+// of the dual step); then a fixed warp tree; the sum goes to part.cpart[w]
+// in FP64.
 template <typename VT>
 __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT* __restrict__ val,
                                            const VT* __restrict__ x, const Partition& part) {
@@ -200,7 +204,7 @@ __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT
   if (w >= part.nchunk) return;
   const int2 c = part.chunks[w];
   VT s = sizeof(VT) == 4 ? batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32)
-                          : batched_dot<VT, 8, 8, false>(col, val, x, c.x + lane, c.y, 32);
+                          : batched_dot<VT, 8, 1, false>(col, val, x, c.x + lane, c.y, 32);
   s = warp_sum(s);
   if (lane == 0) part.cpart[w] = (double)s;
 }
