@@ -354,11 +354,8 @@ def main():
         wall = time.perf_counter() - t_all0
     if dist:
         dist.barrier()
-    per_step = float(np.mean(times))
-    if dist:
-        t = torch.tensor([per_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        per_step = float(t.item())
+    from paper_2510_10891_b300.ranks import max_over_ranks
+    per_step = max_over_ranks(float(np.mean(times)), dist, device="cuda")
     clocks = clk.summary()
 
     # roofline of the dominant SpMV (largest summed time), from the timed steps
