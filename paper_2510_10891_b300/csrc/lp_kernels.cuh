@@ -60,6 +60,20 @@ __device__ __forceinline__ double clampd(double v, double l, double u) {
   return v < l ? l : (v > u ? u : v);
 }
 
+// The same order tests on the integer pipes: non-NaN doubles ordered as
+// signed 64-bit keys (-0 sorts just below +0, which changes at most the sign
+// of a zero result).  The iteration epilogues are bound by B300's FP64 pipe.
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ double clamp_k(double v, double l, double u) {
+  const long long k = dkey(v);
+  return k < dkey(l) ? l : (k > dkey(u) ? u : v);
+}
+__device__ __forceinline__ double max0(double v) { return __double_as_longlong(v) > 0 ? v : 0.0; }
+__device__ __forceinline__ double min0(double v) { return __double_as_longlong(v) < 0 ? v : 0.0; }
+
 // Kernels and their helpers have internal linkage: every translation unit
 // that launches them compiles its own copy.
 namespace {
@@ -127,7 +141,7 @@ struct PrimalEpi {
   }
   __device__ void row(int j, double g) {
     const double v = xj + sigma * (g - cj);
-    const double xb = clampd(v, xlj, xuj);
+    const double xb = clamp_k(v, xlj, xuj);
     const double xt = 2.0 * xb - xj;
     double xn, xa = 0.0;
     if (pdhg) {  // weights {1/(k+1), k/(k+1)} of the running average (rounded as written); k = 0 starts it
@@ -226,7 +240,7 @@ struct DualEpi {
   }
   __device__ void row(int i, double q) {
     const double r = yi - s * q;
-    const double yb = fmax(r + s * loi, 0.0) + fmin(r + s * hii, 0.0);
+    const double yb = max0(r + s * loi) + min0(r + s * hii);
     double yn, ya = 0.0;
     if (pdhg) {
       yn = yb;
