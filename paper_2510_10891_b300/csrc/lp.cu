@@ -249,8 +249,34 @@ int Handle::init(int32_t m_, int32_t n_, int64_t nnz_, const int64_t* row_ptr, c
   SCUC_TRY(alloc(&hi, m));
   SCUC_CUDA(cudaMemcpyAsync(rp, rp32.data(), (m + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   if (nnz) {
-    SCUC_CUDA(cudaMemcpyAsync(col, col_, nnz * sizeof(int), cudaMemcpyHostToDevice, s));
-    SCUC_CUDA(cudaMemcpyAsync(val, val_, nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+    // Large arrays are page-locked for the copy (register + DMA + unregister
+    // measured 64 ms against 122 ms for a pageable copy of the 13k-bus
+    // matrix) and released before returning; the next array is registered
+    // while the previous one is copied.  If registration fails (memory
+    // already registered by the caller, or not registrable) the copy is a
+    // plain pageable one.
+    const void* srcs[2] = {col_, val_};
+    void* dsts[2] = {col, val};
+    const size_t sizes[2] = {nnz * sizeof(int), nnz * sizeof(double)};
+    bool pinned[2] = {false, false};
+    int rc = SCUC_OK;
+    for (int k = 0; k < 2 && rc == SCUC_OK; k++) {
+      if (sizes[k] >= ((size_t)64 << 20)) {
+        if (cudaHostRegister(const_cast<void*>(srcs[k]), sizes[k], cudaHostRegisterDefault) == cudaSuccess)
+          pinned[k] = true;
+        else
+          (void)cudaGetLastError();  // not registrable: pageable copy
+      }
+      if (cudaMemcpyAsync(dsts[k], srcs[k], sizes[k], cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        set_error("host-to-device copy of the matrix failed");
+        rc = SCUC_E_CUDA;
+      }
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    for (int k = 0; k < 2; k++)
+      if (pinned[k]) cudaHostUnregister(const_cast<void*>(srcs[k]));
+    SCUC_TRY(rc);
+    SCUC_CUDA(e);
   }
   if (n) {
     SCUC_CUDA(cudaMemcpyAsync(c, c_, n * sizeof(double), cudaMemcpyHostToDevice, s));
