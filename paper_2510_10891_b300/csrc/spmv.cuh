@@ -3,8 +3,9 @@
 // Rows with more than kGroupRowMax nonzeros ("long rows": the dense PTDF,
 // N-1, balance and reserve rows) are cut into chunks of kChunk entries; a
 // chunk launch (k_chunk_sums and friends) gives every chunk one warp that
-// streams it with coalesced lane-strided loads, eight entries in flight per
-// lane, and stores the chunk sum.  The main launch gives every long row one
+// streams it with coalesced lane-strided loads (the whole chunk in flight
+// for FP32 values, eight entries per lane at a time for FP64) and stores the
+// chunk sum.  The main launch gives every long row one
 // thread that adds its chunk sums in chunk order and runs the epilogue; its
 // other blocks are
 //  * list blocks: kBlock/gsz rows of similar length, gsz = 32, 16, 8 or 4
@@ -18,8 +19,7 @@
 // precision of the products (spmv_run).  Every thread that will run an
 // epilogue row calls epi.load(row) first, so the epilogue's operands are
 // fetched while the row is being summed; the row sums go through shared
-// memory so the epilogue runs one row per thread with full warps (a warp
-// instruction costs the FP64 pipe the same however few lanes are active).
+// memory so the epilogue runs one row per thread with full warps.
 // The chain of dependent loads before the first product is short (record ->
 // matrix entries -> gathered vector) because blocks are short-lived and
 // thousands of them run back to back.
