@@ -123,12 +123,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(inst, gpu_iters, power_iters):
+def cpu_baseline(inst, gpu_iters, power_iters, result=None):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     same LP: setup plus 8 and 16 HPR iterations (lambda fixed, so no power
-    method), extrapolated to the iteration count of the solve."""
+    method), extrapolated to the iteration count of the solve.  With the
+    timed step's returned point, also the oracle's FP64 KKT evaluation of it
+    on the unscaled LP (the error of the GPU result against the oracle)."""
     import oracle
     lp = oracle.as_lp(inst)
+    check = None
+    if result is not None:
+        k = oracle.kkt(lp, *result)
+        check = {k2: float(k[k2]) for k2 in ("kkt", "rp", "rd", "gap", "pobj", "dobj")}
     kw = dict(tol=0.0, lambda_in=1.0, check_every=8)
     t0 = time.perf_counter(); oracle.hpr_solve(lp, max_iter=8, **kw); t8 = time.perf_counter() - t0
     t0 = time.perf_counter(); oracle.hpr_solve(lp, max_iter=16, **kw); t16 = time.perf_counter() - t0
@@ -139,7 +145,7 @@ def cpu_baseline(inst, gpu_iters, power_iters):
             "sample": "oracle on the full LP: setup + 8 and + 16 iterations (%.1f s of CPU work); "
                       "%.3f s/iteration x (%d HPR + %d power iterations) + %.2f s setup"
                       % (t8 + t16, per_iter, gpu_iters, power_iters, setup),
-            "s_per_iter": per_iter}
+            "s_per_iter": per_iter, "oracle_kkt_of_step_result": check}
 
 
 def batched_variant(P):
@@ -352,6 +358,8 @@ def main():
             times.append(e0.elapsed_time(e1) / 1e3)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_all0
+    # the last timed step's point, for the oracle's check in the CPU leg
+    step_result = (xo.cpu().numpy(), yo.cpu().numpy(), zo.cpu().numpy()) if not args.no_cpu else None
     if dist:
         dist.barrier()
     from paper_2510_10891_b300.ranks import max_over_ranks
@@ -553,7 +561,8 @@ def main():
 
     if rank == 0 and not args.no_cpu:
         it_fp64 = out.pop("_fp64_iters", last["iters"])
-        out["cpu_baseline"] = cpu_baseline(inst, it_fp64, out.pop("_power_iters", last["power_iters"]))
+        out["cpu_baseline"] = cpu_baseline(inst, it_fp64, out.pop("_power_iters", last["power_iters"]),
+                                           step_result)
     out.pop("_fp64_iters", None); out.pop("_power_iters", None)
     if rank == 0:
         print(json.dumps(out))
