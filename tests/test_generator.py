@@ -119,3 +119,27 @@ def test_ptdf_network_rows():
     assert np.all(np.abs(ax[l0:l1] - mid) <= w / 1.5 + 2e-3 * np.abs(mid).max() + 1e-9)
     u0, u1 = blocks["unit"]
     assert np.all(ax[u0:u1] >= lp["lo"][u0:u1] - 1e-9) and np.all(ax[u0:u1] <= lp["hi"][u0:u1] + 1e-9)
+
+
+def test_split_network_rows_partitions_the_rows():
+    """Transmission-filtering split: the pool is exactly the base-case line
+    and N-1 row blocks, the base is every other row, and together they are
+    the full instance's rows (same columns, values and row bounds)."""
+    import numpy as np
+    import scipy.sparse as sp
+    from scuc_gen import make_preset, split_network_rows
+    inst = make_preset("scuc14")
+    base, pool, pool_rows = split_network_rows(inst)
+    blocks = inst.params["row_blocks"]
+    want = np.concatenate([np.arange(*blocks["line"]), np.arange(*blocks["ctg"])])
+    np.testing.assert_array_equal(pool_rows, want)
+    assert base["m"] + pool["m"] == inst.m and base["n"] == pool["n"] == inst.n
+    A = inst.csr()
+    lo, hi = inst.row_bounds()
+    base_rows = np.setdiff1d(np.arange(inst.m), pool_rows)
+    for part, rows in ((base, base_rows), (pool, pool_rows)):
+        P = sp.csr_matrix((part["val"], part["col"], part["row_ptr"]), shape=(part["m"], part["n"]))
+        assert (P != A[rows]).nnz == 0
+        np.testing.assert_array_equal(part["lo"], lo[rows])
+        np.testing.assert_array_equal(part["hi"], hi[rows])
+        np.testing.assert_array_equal(part["c"], inst.c)
