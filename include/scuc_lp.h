@@ -20,6 +20,11 @@
  *   Presolve ........... Sec. 4.2, Algorithm 2 (MILP-/LP-Presolve): bound
  *                        propagation and removal of fixed columns and
  *                        redundant rows.
+ *   Second algorithm ... restarted PDHG with ergodic averaging on the same
+ *                        steps (the method HPR improves on, Sec. 3), and
+ *                        infeasibility detection with certificates.
+ *   Filtering .......... the transmission-filtering loop of Fig. 1: violated
+ *                        pool rows found on the device and appended.
  *
  * Conventions (all entry points):
  *   - Return value is an scuc_err code; SCUC_OK on success.  On failure
@@ -34,8 +39,11 @@
  *   - Invalid input (sizes, unsorted or out-of-range column indices, NaN,
  *     lo > hi, xl > xu) returns SCUC_E_INVALID before any launch.
  *   - Sizes: m, n < 2^31 and nnz < 2^31 (32-bit indices on the device).
- *   - No entry point allocates pinned host memory per call or synchronises
- *     the whole device; each solve synchronises its stream before returning.
+ *   - No entry point synchronises the whole device; each solve synchronises
+ *     its stream before returning.  Solves allocate no pinned host memory;
+ *     creating a handle allocates a small pinned control block and
+ *     page-locks the caller's matrix arrays (>= 64 MiB each) for the
+ *     duration of their copy, releasing them before it returns.
  */
 #ifndef SCUC_LP_H
 #define SCUC_LP_H
