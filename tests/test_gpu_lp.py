@@ -254,3 +254,32 @@ def test_invalid_inputs_rejected_before_any_kernel(P):
     db["val"][big.indptr[17000]] = np.inf
     db["val"][big.indptr[1234] + 1] = np.nan
     expect(db, "non-finite matrix value in row 1234")
+
+
+def test_create_page_locks_large_arrays_and_releases_them(P, torch_cuda):
+    """scuc_lp_create page-locks matrix arrays of >= 64 MiB for the copy and
+    releases them: the caller can register the same memory afterwards; an
+    array the caller has already pinned is copied as it is (registration
+    fails, plain copy); both give the same LP bit for bit."""
+    import scipy.sparse as sp
+    torch = torch_cuda
+    m, n = 20000, 9000
+    A = sp.random(m, n, density=0.05, random_state=np.random.default_rng(5), format="csr")   # 9M entries
+    A.sort_indices()
+    assert A.nnz * 8 >= 64 << 20
+    d = dict(m=m, n=n, row_ptr=A.indptr.astype(np.int64), col=A.indices.astype(np.int32), val=A.data.copy(),
+             c=np.ones(n), xl=np.zeros(n), xu=np.ones(n), lo=np.full(m, -np.inf), hi=np.full(m, 1.0))
+    a = P.LP(d)
+    cudart = torch.cuda.cudart()
+    rc = cudart.cudaHostRegister(d["val"].ctypes.data, d["val"].nbytes, 0)
+    assert int(rc) == 0, rc                        # released by create
+    cudart.cudaHostUnregister(d["val"].ctypes.data)
+    pinned = torch.from_numpy(d["val"]).pin_memory()            # caller-pinned copy of the values
+    d2 = dict(d, val=pinned.numpy())
+    b = P.LP(d2)
+    ea, eb = a.export(), b.export()
+    for k in ("row_ptr", "col", "val", "lo", "hi"):
+        np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
+    np.testing.assert_array_equal(eb["val"], d["val"])
+    a.close()
+    b.close()
