@@ -139,3 +139,31 @@ def test_pdhg_average_is_the_mean_of_projected_gradient_steps():
                              lambda_in=1.0, restart_suff=0.0, restart_nec=0.0, restart_long=2.0,
                              algo=1)
         np.testing.assert_allclose(r["x"], np.mean(steps[:k], axis=0), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_pdhg_averaged_point_invariants(seed):
+    """The checked point of PDHG is an average of projected points, so it
+    stays in K, its y has the sign each row's bounds allow, and z vanishes
+    where the bound it would price is infinite (at every iteration limit)."""
+    lp = oracle.as_lp(random_lp(50, 35, density=0.15, seed=seed, senses="GLER"))
+    for k in (64, 256, 1024):
+        r = oracle.hpr_solve(lp, tol=0.0, max_iter=k, algo=1)
+        x, y, z = r["x"], r["y"], r["z"]
+        assert np.all(x >= lp["xl"] - 1e-12) and np.all(x <= lp["xu"] + 1e-12)
+        assert np.all(y[~np.isfinite(lp["lo"])] <= 0.0) and np.all(y[~np.isfinite(lp["hi"])] >= 0.0)
+        assert np.all(z[~np.isfinite(lp["xl"])] <= 0.0) and np.all(z[~np.isfinite(lp["xu"])] >= 0.0)
+
+
+@pytest.mark.parametrize("algo", [0, 1])
+def test_detection_silent_on_feasible_tiny_lps(algo):
+    """Ten feasible tiny LPs (HiGHS optimal): detection never declares them
+    infeasible and both algorithms reach HiGHS's optimum."""
+    for seed in range(10):
+        A, lo, hi, c, xl, xu = _tiny(50 + seed)
+        lp = dense_lp(A, lo, hi, c, xl, xu)
+        st, f = highs_status(lp)
+        assert st == 0
+        r = oracle.hpr_solve(lp, tol=1e-9, max_iter=400000, algo=algo, infeas_tol=1e-8)
+        assert r["info"]["status"] == 0
+        assert r["info"]["pobj"] == pytest.approx(f, rel=1e-6, abs=1e-6)
