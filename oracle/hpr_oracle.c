@@ -238,7 +238,10 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
 
 /* ---------------------------------------------------------------------- */
 /* Infeasibility certificates on the scaled LP (an LP of the same form:     */
-/* scaling maps certificates to certificates).                              */
+/* scaling maps certificates to certificates).  The paper defines no        */
+/* infeasibility test; these are the Farkas and recession-cone certificates */
+/* of LP duality for Eq. 8 with a row box, tested on the step displacement  */
+/* (the reading listed with the design notes).                              */
 /* ---------------------------------------------------------------------- */
 /* Primal infeasibility (Farkas): a dual ray u with z = -A^T u has the
  * homogeneous dual objective  sum_i (u_i > 0 ? lo_i : hi_i) u_i
