@@ -8,9 +8,9 @@
  * source with the CUDA library.  Every loop is scalar, sequential and in the
  * order the formulas are written; no blocking, fusion or reordering.
  *
- * Readings of points the paper leaves open (restart rule, sigma update,
- * residual normalisation, propagation tolerances) are the ones listed in the
- * design notes; each is named where it is used below.
+ * Points the paper leaves open (restart rule, sigma update, residual
+ * normalisation, propagation tolerances and summation order) are settled by
+ * a stated reading, each written out where it is used below.
  */
 #include "hpr_oracle.h"
 
@@ -241,7 +241,7 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
 /* scaling maps certificates to certificates).  The paper defines no        */
 /* infeasibility test; these are the Farkas and recession-cone certificates */
 /* of LP duality for Eq. 8 with a row box, tested on the step displacement  */
-/* (the reading listed with the design notes).                              */
+/* (for an infeasible LP it tends to the iteration's minimal displacement). */
 /* ---------------------------------------------------------------------- */
 /* Primal infeasibility (Farkas): a dual ray u with z = -A^T u has the
  * homogeneous dual objective  sum_i (u_i > 0 ? lo_i : hi_i) u_i

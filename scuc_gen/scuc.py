@@ -61,8 +61,8 @@ class SCUCConfig:
     contingencies: int = 0
     seed: int = 1
     eta_scaling: bool = True
-    # "pmax": eta^P = max_g P^U_g (the text of Sec. 3.A); "pmin": max_g P^L_g
-    # (its displayed formula).  See the readings list of the design notes.
+    # "pmax": eta^P = max_g P^U_g (the text of Sec. 3.A, which names the
+    # maximum production limit); "pmin": max_g P^L_g (its displayed formula).
     eta_reading: str = "pmax"
     ptdf_trunc: float = 1e-3
     reserve_frac: float = 0.03
