@@ -407,8 +407,10 @@ int scuc_lp_export(const scuc_lp* lp, int64_t* row_ptr, int32_t* col, double* va
  *    An LP that needs more slots (3 per row block of A plus 4 per row block
  *    of A^T) is rejected with SCUC_E_INVALID and a message naming the sizes.
  *  The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and keeps it; make that first call before any
- *    stream capture on that device.
+ *    (cudaGetSymbolAddress) and keeps it for the device's current context;
+ *    make that first call before any stream capture on that device.  After
+ *    a device reset the next call (with a new handle) looks it up again.
+ *  kkt is the largest of r_p, r_d and gap, or NaN when one of them is NaN.
  *  All calls share the one array: calls whose work overlaps on the GPU (for
  *    example on two unsynchronised streams) race on it.  Each call writes
  *    every slot it later reads, so contents left by earlier calls are never

@@ -25,19 +25,28 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _SRC = os.path.join(_HERE, "hpr_oracle.c")
 _lib = None
+_lib_omp = None
+
+
+def _compile(out, extra, force):
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "hpr_oracle.h"))):
+        tmp = out + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math"] + extra + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "hpr_oracle.h"))):
-        tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA
+    contraction): the single-threaded library the tests use, and the same
+    source with OpenMP for timing on all host cores."""
+    _compile(_SO_OMP, ["-fopenmp"], force)
+    return _compile(_SO, [], force)
 
 
 class OrcLP(C.Structure):
@@ -79,18 +88,35 @@ DEFAULTS = dict(tol=1e-4, max_iter=100000, check_every=64, use_scaling=1, sigma0
                 sigma_update=1, algo=0, infeas_tol=0.0)
 
 
+def _load(path):
+    L = C.CDLL(path)
+    L.orc_power_lambda.restype = C.c_double
+    L.orc_round.restype = C.c_int32
+    L.orc_fix.restype = C.c_int64
+    L.orc_propagate.restype = C.c_int32
+    L.orc_reduce.restype = C.c_int
+    L.orc_hpr_solve.restype = C.c_int
+    L.orc_set_threads.restype = C.c_int32
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        _lib = C.CDLL(_SO)
-        _lib.orc_power_lambda.restype = C.c_double
-        _lib.orc_round.restype = C.c_int32
-        _lib.orc_fix.restype = C.c_int64
-        _lib.orc_propagate.restype = C.c_int32
-        _lib.orc_reduce.restype = C.c_int
-        _lib.orc_hpr_solve.restype = C.c_int
+        _lib = _load(_SO)
     return _lib
+
+
+def lib_threads(threads):
+    """The OpenMP build with ``threads`` threads (all host cores when 0);
+    returns the library and the thread count its loops use."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        _lib_omp = _load(_SO_OMP)
+    k = int(_lib_omp.orc_set_threads(C.c_int32(int(threads))))
+    return _lib_omp, k
 
 
 def _p(a):
@@ -136,23 +162,28 @@ def _struct(d):
                  _p(d["xl"]), _p(d["xu"]), _p(d["lo"]), _p(d["hi"]))
 
 
-def hpr_solve(src, x_init=None, y_init=None, **params):
+def hpr_solve(src, x_init=None, y_init=None, threads=None, **params):
+    """Restarted HPR (or PDHG with averaging) on the CPU.  ``threads``: None
+    runs the single-threaded oracle; k >= 0 the OpenMP build on k threads
+    (0: all host cores), whose norms and dot products add in another order."""
     d = as_lp(src)
     p = dict(DEFAULTS)
     p.update(params)
+    L, nthr = (lib(), 1) if threads is None else lib_threads(threads)
     prm = OrcParams(**p)
     x = np.zeros(d["n"]); y = np.zeros(d["m"]); z = np.zeros(d["n"])
     info = OrcInfo()
     log = (OrcLog * max(1, p["log_cap"]))()
     xi = _f64(x_init) if x_init is not None else None
     yi = _f64(y_init) if y_init is not None else None
-    lib().orc_hpr_solve(C.byref(_struct(d)), C.byref(prm), _p(xi), _p(yi), _p(x), _p(y), _p(z),
-                        C.byref(info), log)
+    L.orc_hpr_solve(C.byref(_struct(d)), C.byref(prm), _p(xi), _p(yi), _p(x), _p(y), _p(z),
+                    C.byref(info), log)
     nlog = min(info.nlog, p["log_cap"])
     logs = [dict(iter=log[i].iter, restart=log[i].restart, first=log[i].first, rp=log[i].rp,
                  rd=log[i].rd, gap=log[i].gap, pobj=log[i].pobj, dobj=log[i].dobj,
                  rho=log[i].rho, sigma=log[i].sigma, rmap=log[i].rmap) for i in range(nlog)]
     inf = {f[0].rstrip("_"): getattr(info, f[0]) for f in OrcInfo._fields_}
+    inf["threads"] = nthr
     return dict(x=x, y=y, z=z, info=inf, log=logs)
 
 

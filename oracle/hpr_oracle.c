@@ -9,14 +9,42 @@
  * order the formulas are written; no blocking, fusion or reordering.
  *
  * Points the paper leaves open (restart rule, sigma update, residual
- * normalisation, propagation tolerances and summation order) are settled by
- * a stated reading, each written out where it is used below.
+ * normalisation, propagation tolerances) are settled by a stated reading,
+ * each written out where it is used below.  Every sum runs over its terms in
+ * index order.
  */
 #include "hpr_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* The same source builds single-threaded (the oracle the tests use) and with
+ * OpenMP (a timing baseline on all host cores): the pragmas only split
+ * loops whose iterations are independent, and every row or column sum keeps
+ * its order.  Only the scalar sums marked "reduction" (norms, dot products)
+ * are added in a different order when more than one thread runs.         */
+#define ORC_STR(x) #x
+#ifdef _OPENMP
+#define ORC_PAR(clauses) _Pragma(ORC_STR(omp parallel for schedule(static) clauses))
+#define ORC_PAR_ROWS _Pragma("omp parallel for schedule(dynamic, 256)")
+#else
+#define ORC_PAR(clauses)
+#define ORC_PAR_ROWS
+#endif
+
+int32_t orc_set_threads(int32_t k) {
+#ifdef _OPENMP
+  if (k > 0) omp_set_num_threads(k);
+  return (int32_t)omp_get_max_threads();
+#else
+  (void)k;
+  return 1;
+#endif
+}
 
 static double clampd(double v, double l, double u) {
   if (v < l) return l;
@@ -34,9 +62,10 @@ static double bound_mag(double lo, double hi) {
 
 static double* dalloc(int64_t k) { return (double*)calloc((size_t)(k > 0 ? k : 1), sizeof(double)); }
 
-/* y = A x (CSR) */
+/* y = A x (CSR): y_i = sum_k a_ik x_k over the row's entries in order */
 static void spmv(int32_t m, const int64_t* rp, const int32_t* col, const double* val,
                  const double* x, double* y) {
+  ORC_PAR_ROWS
   for (int32_t i = 0; i < m; i++) {
     double s = 0.0;
     for (int64_t k = rp[i]; k < rp[i + 1]; k++) s += val[k] * x[col[k]];
@@ -44,16 +73,51 @@ static void spmv(int32_t m, const int64_t* rp, const int32_t* col, const double*
   }
 }
 
-/* y = A^T x (CSR of A, scatter in row order) */
-static void spmv_t(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
-                   const double* val, const double* x, double* y) {
-  for (int32_t j = 0; j < n; j++) y[j] = 0.0;
+/* Column index of a CSR matrix: the entries of column j, in increasing row
+ * order, are the CSR positions pos[cp[j] .. cp[j+1]) of rows row[...].    */
+typedef struct {
+  int64_t* cp;
+  int32_t* row;
+  int64_t* pos;
+} orc_cols;
+
+static void cols_build(int32_t m, int32_t n, const int64_t* rp, const int32_t* col, orc_cols* t) {
+  const int64_t nnz = rp[m];
+  t->cp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  t->row = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  t->pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+  for (int64_t k = 0; k < nnz; k++) t->cp[col[k] + 1]++;
+  for (int32_t j = 0; j < n; j++) t->cp[j + 1] += t->cp[j];
+  int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t j = 0; j < n; j++) next[j] = t->cp[j];
   for (int32_t i = 0; i < m; i++)
-    for (int64_t k = rp[i]; k < rp[i + 1]; k++) y[col[k]] += val[k] * x[i];
+    for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+      const int64_t p = next[col[k]]++;
+      t->row[p] = i;
+      t->pos[p] = k;
+    }
+  free(next);
+}
+
+static void cols_free(orc_cols* t) {
+  free(t->cp);
+  free(t->row);
+  free(t->pos);
+}
+
+/* y = A^T x: y_j = sum_i a_ij x_i over the column's entries in row order */
+static void spmv_t(int32_t n, const orc_cols* t, const double* val, const double* x, double* y) {
+  ORC_PAR_ROWS
+  for (int32_t j = 0; j < n; j++) {
+    double s = 0.0;
+    for (int64_t p = t->cp[j]; p < t->cp[j + 1]; p++) s += val[t->pos[p]] * x[t->row[p]];
+    y[j] = s;
+  }
 }
 
 static double dot(int64_t k, const double* a, const double* b) {
   double s = 0.0;
+  ORC_PAR(reduction(+ : s))
   for (int64_t i = 0; i < k; i++) s += a[i] * b[i];
   return s;
 }
@@ -147,23 +211,25 @@ static uint64_t splitmix64_at(uint64_t seed, uint64_t j) {
   return z ^ (z >> 31);
 }
 
-double orc_power_lambda(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
-                        const double* val, int32_t max_iter, double tol, uint64_t seed,
-                        int32_t* iters_out) {
+static double power_lambda(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
+                           const orc_cols* tc, const double* val, int32_t max_iter, double tol,
+                           uint64_t seed, int32_t* iters_out) {
   double* q = dalloc(n);
   double* u = dalloc(m);
   double* w = dalloc(n);
   for (int32_t j = 0; j < n; j++) q[j] = 0.5 + (double)(splitmix64_at(seed, (uint64_t)j) >> 11) * 0x1.0p-53;
   double nq = sqrt(dot(n, q, q));
+  ORC_PAR()
   for (int32_t j = 0; j < n; j++) q[j] /= nq;
   double lam = 0.0, lam_prev = 0.0;
   int32_t it = 0;
   for (it = 1; it <= max_iter; it++) {
     spmv(m, rp, col, val, q, u);           /* u = A q          */
-    spmv_t(m, n, rp, col, val, u, w);      /* w = A^T A q      */
+    spmv_t(n, tc, val, u, w);              /* w = A^T A q      */
     lam = dot(m, u, u);                    /* q^T A^T A q      */
     double nw = sqrt(dot(n, w, w));
     if (nw == 0.0) break;
+    ORC_PAR()
     for (int32_t j = 0; j < n; j++) q[j] = w[j] / nw;
     if (it > 1 && fabs(lam - lam_prev) <= tol * lam) break;
     lam_prev = lam;
@@ -176,17 +242,29 @@ double orc_power_lambda(int32_t m, int32_t n, const int64_t* rp, const int32_t* 
   return lam;
 }
 
+double orc_power_lambda(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
+                        const double* val, int32_t max_iter, double tol, uint64_t seed,
+                        int32_t* iters_out) {
+  orc_cols tc;
+  cols_build(m, n, rp, col, &tc);
+  double lam = power_lambda(m, n, rp, col, &tc, val, max_iter, tol, seed, iters_out);
+  cols_free(&tc);
+  return lam;
+}
+
 /* ---------------------------------------------------------------------- */
 /* KKT residuals on the unscaled LP (Theorem 1 map, normalised)            */
 /* ---------------------------------------------------------------------- */
-void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z, double* out) {
+static void kkt(const orc_lp* lp, const orc_cols* tc, const double* x, const double* y,
+                const double* z, double* out) {
   const int32_t m = lp->m, n = lp->n;
   double* ax = dalloc(m);
   double* aty = dalloc(n);
   spmv(m, lp->row_ptr, lp->col, lp->val, x, ax);
-  spmv_t(m, n, lp->row_ptr, lp->col, lp->val, y, aty);
+  spmv_t(n, tc, lp->val, y, aty);
   /* primal: distance of A x to [lo, hi] */
   double pr = 0.0, bn = 0.0;
+  ORC_PAR(reduction(+ : pr, bn))
   for (int32_t i = 0; i < m; i++) {
     double d = ax[i] - clampd(ax[i], lp->lo[i], lp->hi[i]);
     pr += d * d;
@@ -195,6 +273,7 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
   }
   /* dual: c - A^T y - z */
   double dr = 0.0, cn = 0.0;
+  ORC_PAR(reduction(+ : dr, cn))
   for (int32_t j = 0; j < n; j++) {
     double d = lp->c[j] - aty[j] - z[j];
     dr += d * d;
@@ -202,11 +281,14 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
   }
   /* objectives: dual uses the bound each multiplier prices */
   double pobj = 0.0, dobj = 0.0;
+  ORC_PAR(reduction(+ : pobj))
   for (int32_t j = 0; j < n; j++) pobj += lp->c[j] * x[j];
+  ORC_PAR(reduction(+ : dobj))
   for (int32_t i = 0; i < m; i++) {
     if (y[i] > 0.0 && isfinite(lp->lo[i])) dobj += lp->lo[i] * y[i];
     else if (y[i] < 0.0 && isfinite(lp->hi[i])) dobj += lp->hi[i] * y[i];
   }
+  ORC_PAR(reduction(+ : dobj))
   for (int32_t j = 0; j < n; j++) {
     if (z[j] > 0.0 && isfinite(lp->xl[j])) dobj += lp->xl[j] * z[j];
     else if (z[j] < 0.0 && isfinite(lp->xu[j])) dobj += lp->xu[j] * z[j];
@@ -216,16 +298,19 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
   out[2] = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
   out[3] = pobj;
   out[4] = dobj;
-  out[5] = fmax(out[0], fmax(out[1], out[2]));
+  /* the largest of the three; NaN if any of them is NaN */
+  out[5] = (isnan(out[0]) || isnan(out[1]) || isnan(out[2])) ? NAN : fmax(out[0], fmax(out[1], out[2]));
   /* Theorem 1 map R(x,y,z) with the row box generalising R^m_+:
    * R1 = y - P(y - A x), P(r) = r + Pi_[lo,hi](-r)  (= Pi_+(y - Ax + theta)
    * for rows A x >= theta);  R2 = x - Pi_K(x - z);  R3 = c - A^T y - z   */
   double rr = 0.0;
+  ORC_PAR(reduction(+ : rr))
   for (int32_t i = 0; i < m; i++) {
     double r = y[i] - ax[i];
     double p = r + clampd(-r, lp->lo[i], lp->hi[i]);
     rr += (y[i] - p) * (y[i] - p);
   }
+  ORC_PAR(reduction(+ : rr))
   for (int32_t j = 0; j < n; j++) {
     double r2 = x[j] - clampd(x[j] - z[j], lp->xl[j], lp->xu[j]);
     double r3 = lp->c[j] - aty[j] - z[j];
@@ -234,6 +319,13 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
   out[6] = sqrt(rr);
   free(ax);
   free(aty);
+}
+
+void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z, double* out) {
+  orc_cols tc;
+  cols_build(lp->m, lp->n, lp->row_ptr, lp->col, &tc);
+  kkt(lp, &tc, x, y, z, out);
+  cols_free(&tc);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -248,11 +340,11 @@ void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z
  * + sum_j (z_j > 0 ? xl_j : xu_j) z_j  > 0.  Terms that would need an
  * infinite bound are not summed; their squares make up the violation.
  * The ray is accepted when the objective F > 0 and ||violation|| <= tol F. */
-static int primal_infeasible(int32_t m, int32_t n, const int64_t* rp, const int32_t* col,
-                             const double* val, const double* lo, const double* hi,
-                             const double* xl, const double* xu, const double* u, double tol) {
+static int primal_infeasible(int32_t m, int32_t n, const orc_cols* tc, const double* val,
+                             const double* lo, const double* hi, const double* xl,
+                             const double* xu, const double* u, double tol) {
   double* aty = dalloc(n);
-  spmv_t(m, n, rp, col, val, u, aty);
+  spmv_t(n, tc, val, u, aty);
   double F = 0.0, V = 0.0;
   for (int32_t i = 0; i < m; i++) {
     if (u[i] > 0.0) {
@@ -312,13 +404,15 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   double *xls = dalloc(n), *xus = dalloc(n), *los = dalloc(m), *his = dalloc(m);
   double beta = 1.0, gamma = 1.0;
   orc_scale(lp, prm->use_scaling, Dr, Dc, &beta, &gamma, vs, cs, xls, xus, los, his);
+  orc_cols tc; /* A^T products run over the columns, each in row order */
+  cols_build(m, n, lp->row_ptr, lp->col, &tc);
 
   double lambda = prm->lambda_in;
   int32_t piters = 0;
   if (!(lambda > 0.0)) {
     lambda = prm->lambda_safety *
-             orc_power_lambda(m, n, lp->row_ptr, lp->col, vs, prm->power_max_iter, prm->power_tol,
-                              prm->power_seed, &piters);
+             power_lambda(m, n, lp->row_ptr, lp->col, &tc, vs, prm->power_max_iter, prm->power_tol,
+                          prm->power_seed, &piters);
     if (!(lambda > 0.0)) lambda = 1.0; /* no constraints: any positive value */
   }
 
@@ -332,10 +426,12 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   double *xbr = dalloc(n), *xavg = dalloc(n), *yavg = dalloc(m), *dxv = dalloc(n);
 
   /* starting point, in scaled variables, projected onto K and the dual cone */
+  ORC_PAR()
   for (int32_t j = 0; j < n; j++) {
     double v = x_init ? x_init[j] / (beta * Dc[j]) : 0.0;
     x[j] = clampd(v, xls[j], xus[j]);
   }
+  ORC_PAR()
   for (int32_t i = 0; i < m; i++) {
     double v = y_init ? y_init[i] / (gamma * Dr[i]) : 0.0;
     if (!isfinite(los[i]) && v > 0.0) v = 0.0;
@@ -361,8 +457,9 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
     const double wb = pdhg ? (double)k / (double)(k + 1) : (double)(k + 1) / (double)(k + 2);
 
     /* x_bar = Pi_K(x + sigma (A^T y - c)); z_bar = (x_bar - v)/sigma */
-    spmv_t(m, n, lp->row_ptr, lp->col, vs, y, g);
+    spmv_t(n, &tc, vs, y, g);
     double dxx = 0.0;
+    ORC_PAR(reduction(+ : dxx))
     for (int32_t j = 0; j < n; j++) {
       double v = x[j] + sigma * (g[j] - cs[j]);
       double xbar = clampd(v, xls[j], xus[j]);
@@ -381,6 +478,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
     /* y_bar = prox: r = y - s A x_tilde; y_bar = r + s * Pi_[lo,hi](-r/s) */
     spmv(m, lp->row_ptr, lp->col, vs, xt, q);
     double dyy = 0.0;
+    ORC_PAR(reduction(+ : dyy))
     for (int32_t i = 0; i < m; i++) {
       double r = y[i] - s * q[i];
       double ybar = r + s * clampd(-r / s, los[i], his[i]);
@@ -393,6 +491,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       if (pdhg) y[i] = ybar;                         /* PDHG step */
       else y[i] = wa * y0[i] + wb * (2.0 * ybar - y[i]);  /* Halpern step */
     }
+    ORC_PAR()
     for (int32_t j = 0; j < n; j++) x[j] = pdhg ? xbr[j] : wa * x0[j] + wb * xt[j];
     k++;
     t++;
@@ -402,10 +501,12 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
      * c - A^T y_avg where the bounds let it act, 0 elsewhere (the scaled
      * copy is zeroed below where a bound is infinite) */
     if (pdhg) {
-      spmv_t(m, n, lp->row_ptr, lp->col, vs, yb, g);
+      spmv_t(n, &tc, vs, yb, g);
+      ORC_PAR()
       for (int32_t j = 0; j < n; j++) zb[j] = cs[j] - g[j];
     }
     /* unscale the barred iterate and evaluate the KKT map on the original LP */
+    ORC_PAR()
     for (int32_t j = 0; j < n; j++) {
       xo[j] = beta * Dc[j] * xb[j];
       double zz = gamma * zb[j] / Dc[j];
@@ -413,8 +514,9 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       if (zz < 0.0 && !isfinite(lp->xu[j])) zz = 0.0;
       zo[j] = zz;
     }
+    ORC_PAR()
     for (int32_t i = 0; i < m; i++) yo[i] = gamma * Dr[i] * yb[i];
-    orc_kkt(lp, xo, yo, zo, last);
+    kkt(lp, &tc, xo, yo, zo, last);
     have_out = 1;
     /* restart metric: fixed-point residual of the step, optionally in the
      * metric of the iteration (cross term with A(x_bar - x) = A x_t - A x_bar),
@@ -426,6 +528,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       double cross = 0.0;
       if (prm->restart_metric == 1) {
         spmv(m, lp->row_ptr, lp->col, vs, xb, pv);
+        ORC_PAR(reduction(+ : cross))
         for (int32_t i = 0; i < m; i++) cross += (q[i] - pv[i]) * dyv[i];
       }
       rho = sqrt(fmax(0.0, dxx / sigma + lambda * sigma * dyy + 2.0 * cross));
@@ -433,10 +536,12 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
 
     int restart = 0;
     const int was_first = first_check;
-    if (last[5] <= prm->tol) {
+    if (!isfinite(last[5])) {
+      status = 3;  /* a residual is NaN or infinite: stop (no verdict) */
+    } else if (last[5] <= prm->tol) {
       status = 0;
     } else if (prm->infeas_tol > 0.0 &&
-               primal_infeasible(m, n, lp->row_ptr, lp->col, vs, los, his, xls, xus, dyv, prm->infeas_tol)) {
+               primal_infeasible(m, n, &tc, vs, los, his, xls, xus, dyv, prm->infeas_tol)) {
       status = 5;  /* the dual ray y_bar - y certifies primal infeasibility */
     } else if (prm->infeas_tol > 0.0 &&
                dual_infeasible(m, n, lp->row_ptr, lp->col, vs, cs, los, his, xls, xus, dxv, prm->infeas_tol)) {
@@ -474,7 +579,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       for (int32_t i = 0; i < m; i++) yo[i] = gamma * Dr[i] * dyv[i];
     if (status == 6)
       for (int32_t j = 0; j < n; j++) xo[j] = beta * Dc[j] * dxv[j];
-    if (status == 0 || status == 5 || status == 6) break;
+    if (status == 0 || status == 3 || status == 5 || status == 6) break;
     if (restart) {
       /* PDHG restarts from the average */
       if (pdhg) {
@@ -483,7 +588,9 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
       }
       /* primal-weight update from the displacement since the last restart */
       double ddx = 0.0, ddy = 0.0;
+      ORC_PAR(reduction(+ : ddx))
       for (int32_t j = 0; j < n; j++) ddx += (x[j] - x0[j]) * (x[j] - x0[j]);
+      ORC_PAR(reduction(+ : ddy))
       for (int32_t i = 0; i < m; i++) ddy += (y[i] - y0[i]) * (y[i] - y0[i]);
       ddx = sqrt(ddx);
       ddy = sqrt(ddy);
@@ -526,6 +633,7 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
   free(x); free(x0); free(xt); free(xb); free(zb); free(g); free(y); free(y0); free(yb);
   free(q); free(xo); free(yo); free(zo); free(dyv); free(pv);
   free(xbr); free(xavg); free(yavg); free(dxv);
+  cols_free(&tc);
   return 0;
 }
 
@@ -574,39 +682,25 @@ int64_t orc_fix(int32_t G, int32_t T, const double* u, const double* v, const do
 /* ---------------------------------------------------------------------- */
 /* Bound propagation (stands in for MILP-/LP-Presolve of Algorithm 2)      */
 /* ---------------------------------------------------------------------- */
-/* Activity range of one row over the bounds: finite parts and the number of
- * infinite contributions, summed in entry order.                          */
-/* Sums over the entries of one row are taken in a fixed order that a warp
- * of 32 lanes can reproduce: entry k0 + q goes to partial sum q mod 32
- * (each partial in entry order), then partials are combined by halving,
- * p[l] += p[l + w] for w = 16, 8, 4, 2, 1.  (The definitions fix no order;
- * this one is shared with the GPU so both take the same rounding.) */
-#define ORC_LANES 32
-static double lanes_total(double* p) {
-  for (int w = ORC_LANES / 2; w > 0; w >>= 1)
-    for (int l = 0; l < w; l++) p[l] += p[l + w];
-  return p[0];
-}
-
-/* activity range of row entries [k0, k1): min and max of sum a_k x_k over
- * the bounds, with the infinite contributions counted apart */
+/* Activity range of one row over the bounds: the minimum and maximum of
+ * sum_k a_k x_k for x within [xl, xu], with the finite parts summed in entry
+ * order and the infinite contributions counted apart.                     */
 static void row_activity(int64_t k0, int64_t k1, const int32_t* col, const double* val,
                          const double* xl, const double* xu, double* mn, double* mx,
                          int32_t* cmn, int32_t* cmx) {
-  double p_mn[ORC_LANES] = {0}, p_mx[ORC_LANES] = {0};
+  double s_mn = 0.0, s_mx = 0.0;
   int32_t c_mn = 0, c_mx = 0;
   for (int64_t k = k0; k < k1; k++) {
-    const int q = (int)((k - k0) % ORC_LANES);
     double a = val[k];
     double lmin = a > 0.0 ? xl[col[k]] : xu[col[k]];
     double lmax = a > 0.0 ? xu[col[k]] : xl[col[k]];
     if (isinf(lmin)) c_mn++;
-    else p_mn[q] += a * lmin;
+    else s_mn += a * lmin;
     if (isinf(lmax)) c_mx++;
-    else p_mx[q] += a * lmax;
+    else s_mx += a * lmax;
   }
-  *mn = lanes_total(p_mn);
-  *mx = lanes_total(p_mx);
+  *mn = s_mn;
+  *mx = s_mx;
   *cmn = c_mn;
   *cmx = c_mx;
 }
@@ -707,34 +801,31 @@ int orc_reduce(int32_t m, int32_t n, const int64_t* rp, const int32_t* col, cons
   rp_r[0] = 0;
   for (int32_t i = 0; i < m; i++) {
     /* fold the fixed columns into the row bounds */
-    double p_sh[ORC_LANES] = {0};
+    double shift = 0.0;
     int64_t kept = 0;
     for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-      if (newcol[col[k]] < 0) p_sh[(k - rp[i]) % ORC_LANES] += val[k] * xl[col[k]];
+      if (newcol[col[k]] < 0) shift += val[k] * xl[col[k]];
       else kept++;
     }
-    const double shift = lanes_total(p_sh);
     double l = lo[i] - shift, u = hi[i] - shift;
     if (kept == 0) {
       if (l > 1e-6 * fmax(1.0, fabs(l)) || u < -1e-6 * fmax(1.0, fabs(u))) bad = 1;
       continue;
     }
-    /* activity range over the free columns */
-    double p_mn[ORC_LANES] = {0}, p_mx[ORC_LANES] = {0};
+    /* activity range over the free columns, in entry order */
+    double mn = 0.0, mx = 0.0;
     int32_t cmn = 0, cmx = 0;
     for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
       const int32_t j = col[k];
       if (newcol[j] < 0) continue;
-      const int q = (int)((k - rp[i]) % ORC_LANES);
       const double a = val[k];
       const double lmin = a > 0.0 ? xl[j] : xu[j];
       const double lmax = a > 0.0 ? xu[j] : xl[j];
       if (isinf(lmin)) cmn++;
-      else p_mn[q] += a * lmin;
+      else mn += a * lmin;
       if (isinf(lmax)) cmx++;
-      else p_mx[q] += a * lmax;
+      else mx += a * lmax;
     }
-    const double mn = lanes_total(p_mn), mx = lanes_total(p_mx);
     int lo_red = !isfinite(l) || (cmn == 0 && mn >= l);
     int hi_red = !isfinite(u) || (cmx == 0 && mx <= u);
     if (lo_red && hi_red) continue;

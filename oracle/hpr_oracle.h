@@ -72,8 +72,9 @@ typedef struct {
 
 typedef struct {
   int64_t iters;
-  int32_t status;    /* 0 optimal, 1 iteration limit, 5 primal infeasible,
-                        6 dual infeasible (primal unbounded)          */
+  int32_t status;    /* 0 optimal, 1 iteration limit, 3 numerical (a
+                        residual is NaN or infinite), 5 primal
+                        infeasible, 6 dual infeasible (primal unbounded) */
   int32_t restarts;
   int32_t nlog;
   int32_t power_iters;
@@ -103,6 +104,10 @@ int orc_hpr_solve(const orc_lp* lp, const orc_params* prm, const double* x_init,
  * dobj, kkt, ||R||} (out holds 7).  z is used as given (the caller
  * projects it).                                                          */
 void orc_kkt(const orc_lp* lp, const double* x, const double* y, const double* z, double* out);
+
+/* Threads of the OpenMP build (k > 0 sets them); returns the threads that
+ * loops will use (1 in the single-threaded build).                       */
+int32_t orc_set_threads(int32_t k);
 
 /* Round(s, tau) (Sec. 4.1). */
 int32_t orc_round(double s, double tau);

@@ -20,17 +20,50 @@ static __device__ __align__(256) double g_kkt_scratch[kNoallocSlots];
 
 constexpr int kMaxDevices = 256;
 std::mutex g_addr_mu;
-double* g_addr[kMaxDevices] = {};  // device address of g_kkt_scratch, per device
+// device address of g_kkt_scratch, per device, with the ID of the context it
+// was looked up in: a device reset ends that context, the next context loads
+// the module again (possibly at another address) and has another ID
+double* g_addr[kMaxDevices] = {};
+unsigned long long g_addr_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device.  In host code the array's name is only a host-side stand-in.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// ID of the current context (driver calls reached through the runtime, so the
+// library links no driver library); 0 when unavailable
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context, looked up once
+// per device and context (the device must be current).  In host code the
+// array's name is only a host-side stand-in, never a device address.
 int scratch_address(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) {
     set_error("device ordinal %d out of range", device);
     return SCUC_E_INVALID;
   }
   std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[device]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_addr[device] || ctx == 0 || ctx != g_addr_ctx[device]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_kkt_scratch);
     if (e != cudaSuccess || !p) {
@@ -39,6 +72,7 @@ int scratch_address(int device, double** out) {
       return SCUC_E_CUDA;
     }
     g_addr[device] = static_cast<double*>(p);
+    g_addr_ctx[device] = ctx;
   }
   *out = g_addr[device];
   return SCUC_OK;
@@ -148,7 +182,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_kkt_final(const double* __res
     out[2] = gap;
     out[3] = pobj;
     out[4] = dobj;
-    out[5] = fmax(rp, fmax(rd, gap));
+    out[5] = (rp != rp || rd != rd || gap != gap) ? (double)NAN : fmax(rp, fmax(rd, gap));  // NaN carried
   }
 }
 

@@ -506,7 +506,9 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, 
   const double rd = sqrt(dres2) / (1.0 + C->cnorm);
   const double pobj = bg * pobj_s, dobj = bg * (dy + dz);
   const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
-  const double kkt = fmax(rp, fmax(rd, gap));
+  // fmax returns its other operand for a NaN, so a NaN residual is carried
+  // into kkt explicitly (it then stops the solve as SCUC_ST_NUMERICAL)
+  const double kkt = (rp != rp || rd != rd || gap != gap) ? (double)NAN : fmax(rp, fmax(rd, gap));
   const int64_t k = C->k + chunk, t = C->t + chunk;
   const double rho = (C->restart_metric == 2 || C->algo == SCUC_ALGO_PDHG_AVG)
                          ? kkt

@@ -2,6 +2,8 @@
 than itself: exact tiny-LP solvers, closed forms, HiGHS, eigvalsh, the
 invariants of an optimal primal-dual pair, and the O(1/k) bound of Theorem 1.
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -282,3 +284,33 @@ def test_eta_scaling_equivalence():
     assert fa == pytest.approx(fb, rel=1e-9)
     ra = oracle.hpr_solve(a, tol=1e-7, max_iter=400000)
     assert ra["info"]["pobj"] * a.objective_scale == pytest.approx(fb, rel=2e-6)
+
+
+def _golden_kkt_points():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "kkt_2x3.txt")
+    pts = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("point "):
+                a, b = line[len("point "):].split("|")
+                v = [float(t) for t in a.split()]
+                pts.append((v[0:3], v[3:5], v[5:8], [float(t) for t in b.split()]))
+    return pts
+
+
+def test_kkt_hand_worked_golden():
+    """orc_kkt against residuals, objectives and Theorem 1's map worked by hand
+    on a 2x3 LP at two non-optimal points (tests/golden/kkt_2x3.txt): both
+    signs of y and z, terms left out at infinite bounds, the bound norm of a
+    ranged row taken from its larger finite bound."""
+    inf = np.inf
+    lp = dict(m=2, n=3, row_ptr=np.array([0, 2, 4]), col=np.array([0, 1, 1, 2]),
+              val=np.array([1.0, 2.0, 1.0, -1.0]), c=np.array([2.0, -1.0, 2.0]),
+              xl=np.array([0.0, -inf, 0.0]), xu=np.array([4.0, 5.0, inf]),
+              lo=np.array([3.0, -4.0]), hi=np.array([inf, 2.0]))
+    pts = _golden_kkt_points()
+    assert len(pts) == 2
+    for x, y, z, want in pts:
+        k = oracle.kkt(lp, np.array(x), np.array(y), np.array(z))
+        got = [k[key] for key in ("rp", "rd", "gap", "pobj", "dobj", "kkt", "rmap")]
+        np.testing.assert_allclose(got, want, rtol=1e-14, atol=0)
