@@ -139,6 +139,12 @@ typedef struct {
                              direction in the recession cone, each with
                              relative violation <= infeas_tol (1e-8 is a
                              sound choice); two extra FP64 SpMVs per check */
+  int32_t spmv_layout;    /* 0: the primal step's A^T y runs on a sliced ELL
+                             copy of A^T (slices of 32 columns of A, one per
+                             lane) when the handle has one (every column of
+                             A holds <= 4096 nonzeros); 1: on the CSR
+                             partition, like every other product          */
+  int32_t reserved0;      /* 0 */
 } scuc_solve_params;
 
 typedef struct {

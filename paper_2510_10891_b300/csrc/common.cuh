@@ -83,6 +83,25 @@ struct Partition {
   int* slot = nullptr;           // [nblk] partial-sum slot of each block, or nullptr
 };
 
+// Sliced ELL copy of a CSR matrix (used for A^T in the primal step): rows
+// go in slices of 32, one row per lane; entry k of the row in lane r of
+// slice s sits at (sptr[s] + k) * 32 + r, so a warp reads one slice step
+// with one coalesced request.  Rows are sorted by length within windows of
+// kSellWindow consecutive rows (neighbouring columns of the SCUC LP share
+// most of their rows, so the lanes of a slice gather nearby vector
+// entries); slices run longest first.  A row shorter than its slice is
+// padded with its last column and a zero value.
+constexpr int kSellWindow = 256;
+struct Sell {
+  int nslice = 0;
+  int64_t nent = 0;       // entries incl. padding (= sptr[nslice] * 32)
+  int* sptr = nullptr;    // [nslice + 1] first step of each slice
+  int* rows = nullptr;    // [nslice * 32] row of each lane, -1: none
+  int2* cv32 = nullptr;   // [nent] {column, FP32 value bits}
+  int* col = nullptr;     // [nent] column (FP64 values)
+  double* v64 = nullptr;  // [nent] FP64 value
+};
+
 // Device-resident solver state.  Parameters are written by the host before a
 // solve; the state is advanced only by the decide kernel.
 struct Ctrl {

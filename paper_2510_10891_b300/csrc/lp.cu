@@ -388,6 +388,9 @@ int Handle::setup_solver(const std::vector<int>& rp32, const std::vector<int>& r
   cudaStream_t s = work;
   SCUC_TRY(build_partition(rp32, m, &pA));
   SCUC_TRY(build_partition(rpt_h, n, &pT));
+  // sliced ELL copy of A^T for the primal step (its values follow each
+  // scaling); matrices with chunked long columns keep the CSR partition
+  if (pT.nlong == 0 && n > 0) SCUC_TRY(build_sell(rpt_h, n, &sT, &allocs));
   for (Partition* P : {&pA, &pT})
     for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
                     (void*)P->cpart, (void*)P->slot})
@@ -456,6 +459,7 @@ DevLP Handle::dev() const {
   L.c = cs; L.xl = xls; L.xu = xus; L.lo = los; L.hi = his; L.Dr = Dr; L.Dc = Dc;
   L.x = x; L.x0 = x0; L.xt = xt; L.xbar = xbar; L.zbar = zbar; L.y = y; L.y0 = y0; L.ybar = ybar;
   L.xt32 = xt32; L.y32 = y32;
+  L.sT = sT;
   L.qchk = uv; L.dychk = dychk;  // uv: power-method scratch, free during iterations
   L.dxchk = dxchk;
   L.coef = coef; L.coef_w = coef;
@@ -522,6 +526,12 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
       k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vst, nnz, vst32);
       nlaunch += 2;
     }
+    SCUC_CUDA(cudaGetLastError());
+  }
+  if (sT.nslice) {
+    k_sell_fill<<<(sT.nslice + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(sT, rpt, colt, vst,
+                                                                              need_f32 ? vst32 : nullptr);
+    nlaunch += 1;
     SCUC_CUDA(cudaGetLastError());
   }
   return SCUC_OK;
@@ -593,8 +603,12 @@ int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
   for (int j = 0; j < check_every; j++) {
     const bool chk = (j == check_every - 1);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 0], s));
-    if (pT.nchunk) k_chunks_iter<kChunksPrimal, PREC><<<pT.nchunkblk, kBlock, 0, s>>>(L);
-    if (pT.nblk) k_primal_sum<PREC><<<pT.nblk, kBlock, pT.smem, s>>>(L);
+    if (use_sell) {
+      k_primal_sell<PREC><<<(sT.nslice + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(L);
+    } else {
+      if (pT.nchunk) k_chunks_iter<kChunksPrimal, PREC><<<pT.nchunkblk, kBlock, 0, s>>>(L);
+      if (pT.nblk) k_primal_sum<PREC><<<pT.nblk, kBlock, pT.smem, s>>>(L);
+    }
     if (chk) k_primal_epi<true, PREC><<<epi_gx, kBlock, 0, s>>>(L, j);
     else k_primal_epi<false, PREC><<<epi_gx, kBlock, 0, s>>>(L, j);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 1], s));
@@ -613,7 +627,8 @@ int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
 // kernels of one period: anchor, iterations, residual SpMVs, decide
 int64_t Handle::period_kernels(int check_every) const {
   const int la = (pA.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0), lt = (pT.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0);
-  return 2 + (int64_t)check_every * (la + lt + 1) + (la + lt) * (detect ? 2 : 1);
+  const int lt_iter = use_sell ? 1 : lt;
+  return 2 + (int64_t)check_every * (la + lt_iter + 1) + (la + lt) * (detect ? 2 : 1);
 }
 
 // check SpMVs (FP64) and the decide kernel of a period
@@ -717,7 +732,8 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   using clk = std::chrono::steady_clock;
   if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
       (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1 ||
-      (p.algo != SCUC_ALGO_HPR && p.algo != SCUC_ALGO_PDHG_AVG) || !(p.infeas_tol >= 0.0 && p.infeas_tol < 1.0)) {
+      (p.algo != SCUC_ALGO_HPR && p.algo != SCUC_ALGO_PDHG_AVG) || !(p.infeas_tol >= 0.0 && p.infeas_tol < 1.0) ||
+      (p.spmv_layout != 0 && p.spmv_layout != 1)) {
     set_error("invalid solve parameters");
     return SCUC_E_INVALID;
   }
@@ -773,6 +789,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.infeas_tol = p.infeas_tol;
   algo = p.algo;
   detect = p.infeas_tol > 0.0;
+  use_sell = sT.nslice > 0 && p.spmv_layout == 0;
   C.s_step = 1.0 / (lambda * p.sigma0);
   C.polish_factor = p.polish_factor;
   C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
@@ -826,9 +843,9 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   int64_t n_p = 0, n_d = 0, n_p32 = 0, n_d32 = 0;
   int timed_out = 0;
   if (use_graph) {
-    const void* key[7] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
+    const void* key[8] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
                           (const void*)coef, (const void*)(intptr_t)(mixed ? 0 : 1), (const void*)(intptr_t)algo,
-                          (const void*)(intptr_t)(detect ? 1 : 0)};
+                          (const void*)(intptr_t)(detect ? 1 : 0), (const void*)(intptr_t)(use_sell ? 1 : 0)};
     if (!graph_exec || memcmp(key, graph_key, sizeof(key)) != 0) {
       if (graph_exec) {
         cudaGraphExecDestroy(graph_exec);

@@ -26,6 +26,9 @@ struct PartPlan {
   int cls_row[5] = {0, 0, 0, 0, 0};
 };
 int build_partition(const std::vector<int>& rp, int m, Partition* P);
+// sliced ELL structure of a CSR matrix with row pointers rp (values filled
+// on the device by k_sell_fill); freed with the handle's allocations
+int build_sell(const std::vector<int>& rp, int m, Sell* S, std::vector<void*>* allocs);
 void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan);
 int upload_partition(const PartPlan& plan, Partition* P);
 void free_partition(Partition* P);
@@ -44,6 +47,7 @@ struct Handle {
   double *val = nullptr, *valt = nullptr, *vs = nullptr, *vst = nullptr;
   float *vs32 = nullptr, *vst32 = nullptr;
   Partition pA, pT;
+  Sell sT;  // sliced ELL copy of A^T for the primal step (nslice = 0: none)
   // problem data (unscaled and scaled)
   double *c = nullptr, *xl = nullptr, *xu = nullptr, *lo = nullptr, *hi = nullptr;
   double *Dr = nullptr, *Dc = nullptr, *cs = nullptr, *xls = nullptr, *xus = nullptr,
@@ -65,8 +69,8 @@ struct Handle {
   scuc_check_log* log_d = nullptr;
   int log_cap = 0, last_nlog = 0;
   cudaGraphExec_t graph_exec = nullptr;
-  // check_every, FP32 values, log, coef, initial phase, algorithm, detection
-  const void* graph_key[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // check_every, FP32 values, log, coef, initial phase, algorithm, detection, layout
+  const void* graph_key[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t aux = nullptr;  // capture stream of the graph's conditional bodies
   double* coef = nullptr;
   int64_t nlaunch = 0, graph_nodes = 0;  // kernels launched by this handle; nodes of the period graph
@@ -98,6 +102,7 @@ struct Handle {
   int launch_checks(cudaStream_t s, int check_every);
   int64_t period_kernels(int check_every) const;
   int algo = SCUC_ALGO_HPR;  // of the current solve (kernels launched by the checks)
+  bool use_sell = false;     // the current solve's primal products run on sT
   bool detect = false;       // infeasibility detection in the current solve
   int launch_period(int check_every, bool profile, bool fp64);
   int build_solve_graph(int check_every, int phase64);

@@ -114,6 +114,56 @@ void free_partition(Partition* P) {
   *P = Partition{};
 }
 
+// Sliced ELL structure (Sell, common.cuh): rows sorted by length (longest
+// first, ties by index) within windows of kSellWindow rows, cut into slices
+// of 32; slices ordered longest first (the longest start first, so the
+// launch ends evenly).  Rows longer than kGroupRowMax are not supported
+// (the caller keeps the CSR partition for such matrices).
+int build_sell(const std::vector<int>& rp, int m, Sell* S, std::vector<void*>* allocs) {
+  *S = Sell{};
+  struct Slice {
+    int len;
+    int first;  // index into order
+  };
+  std::vector<int> order(m);
+  std::vector<Slice> slices;
+  for (int w0 = 0; w0 < m; w0 += kSellWindow) {
+    const int w1 = std::min(m, w0 + kSellWindow);
+    for (int r = w0; r < w1; r++) order[r] = r;
+    std::stable_sort(order.begin() + w0, order.begin() + w1,
+                     [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+    for (int q = w0; q < w1; q += 32) slices.push_back(Slice{rp[order[q] + 1] - rp[order[q]], q});
+  }
+  std::stable_sort(slices.begin(), slices.end(), [](const Slice& a, const Slice& b) { return a.len > b.len; });
+  const int ns = (int)slices.size();
+  std::vector<int> sptr(ns + 1, 0), rows((size_t)ns * 32, -1);
+  for (int k = 0; k < ns; k++) {
+    const Slice& sl = slices[k];
+    const int w1 = std::min(m, (sl.first / kSellWindow + 1) * kSellWindow);
+    for (int l = 0; l < 32 && sl.first + l < w1; l++) rows[(size_t)k * 32 + l] = order[sl.first + l];
+    if ((int64_t)sptr[k] + sl.len > (int64_t)INT32_MAX / 32) {
+      set_error("sliced ELL copy of %d rows exceeds 2^31 entries", m);
+      return SCUC_E_INVALID;
+    }
+    sptr[k + 1] = sptr[k] + sl.len;
+  }
+  S->nslice = ns;
+  S->nent = (int64_t)sptr[ns] * 32;
+  SCUC_TRY(palloc(&S->sptr, sptr.size()));
+  allocs->push_back(S->sptr);
+  SCUC_TRY(palloc(&S->rows, rows.size()));
+  allocs->push_back(S->rows);
+  SCUC_TRY(palloc(&S->cv32, (size_t)S->nent));
+  allocs->push_back(S->cv32);
+  SCUC_TRY(palloc(&S->col, (size_t)S->nent));
+  allocs->push_back(S->col);
+  SCUC_TRY(palloc(&S->v64, (size_t)S->nent));
+  allocs->push_back(S->v64);
+  SCUC_CUDA(cudaMemcpy(S->sptr, sptr.data(), sptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  SCUC_CUDA(cudaMemcpy(S->rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return SCUC_OK;
+}
+
 int build_partition(const std::vector<int>& rp, int m, Partition* P) {
   PartPlan plan;
   plan_partition(rp, m, PartShape{}, true, &plan);

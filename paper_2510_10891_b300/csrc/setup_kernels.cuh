@@ -288,6 +288,32 @@ __global__ void k_to_f32(const double* __restrict__ a, int64_t k, float* __restr
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k; e += stride) b[e] = (float)a[e];
 }
 
+// Values of the sliced ELL copy (Sell) from the CSR arrays of the same
+// matrix: one warp per slice, lane r copies its row's entries in order and
+// pads the slice with its last column and zero.  FP32 values (v32 != null)
+// go to cv32 with their columns, FP64 values (v64 != null) to col / v64.
+__global__ void __launch_bounds__(kBlock) k_sell_fill(Sell S, const int* __restrict__ rp,
+                                                      const int* __restrict__ col, const double* __restrict__ v64,
+                                                      const float* __restrict__ v32) {
+  const int sl = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (sl >= S.nslice) return;
+  const int r = S.rows[(size_t)sl * 32 + lane];
+  const int a = r >= 0 ? rp[r] : 0, len = r >= 0 ? rp[r + 1] - a : 0;
+  const int last = len > 0 ? col[a + len - 1] : 0;
+  const int steps = S.sptr[sl + 1] - S.sptr[sl];
+  const int64_t base = (int64_t)S.sptr[sl] * 32 + lane;
+  for (int k = 0; k < steps; k++) {
+    const int64_t e = base + (int64_t)k * 32;
+    const bool in = k < len;
+    const int c = in ? col[a + k] : last;
+    if (v32) S.cv32[e] = make_int2(c, __float_as_int(in ? v32[a + k] : 0.0f));
+    if (v64) {
+      S.col[e] = c;
+      S.v64[e] = in ? v64[a + k] : 0.0;
+    }
+  }
+}
+
 // --------------------------- power method ---------------------------------
 __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j) {
   uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;

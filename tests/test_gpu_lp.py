@@ -92,6 +92,30 @@ def test_solve_parity_random(P, case):
     assert k["kkt"] == pytest.approx(gi["kkt"], rel=1e-9, abs=1e-14)
 
 
+@pytest.mark.parametrize("case", LP_CASES + [(5000, 40, 0.002, 4, 0, 1, "GL")])
+def test_spmv_layouts_agree(P, case):
+    """The primal step's A^T y on the sliced ELL copy of A^T (the default) and
+    on the CSR partition (spmv_layout = 1): FP64 solves take the same restart
+    decisions at every check with iterates equal to rounding, and mixed
+    solves reach the tolerance under the oracle's KKT evaluation.  Covers
+    ragged slices, empty columns and a column of 5,000 entries (no sliced
+    copy: both layouts run the CSR partition, bit for bit)."""
+    m, n, dens, seed, lr, lc, sen = case
+    d = random_lp(m, n, density=dens, seed=seed, long_rows=lr, long_cols=lc, senses=sen)
+    lp = P.LP(d)
+    kw = dict(tol=1e-6, max_iter=20480, check_every=64)
+    a, b = lp.solve(spmv_layout=0, **kw), lp.solve(spmv_layout=1, **kw)
+    assert a["info"]["status"] == b["info"]["status"] and a["info"]["iters"] == b["info"]["iters"]
+    _compare_logs(a["log"], b["log"])
+    assert _rel(a["x"], b["x"]) < 1e-8 and _rel(a["y"], b["y"]) < 1e-8
+    if lc and m > 4096:
+        np.testing.assert_array_equal(a["x"], b["x"])
+    for layout in (0, 1):
+        r = lp.solve(spmv_layout=layout, tol=1e-4, precision="mixed", max_iter=20480)
+        assert r["info"]["status"] == 0
+        assert oracle.kkt(d, r["x"], r["y"], r["z"])["kkt"] <= 1e-4 * 1.0001
+
+
 def test_solve_parity_scuc14(P):
     inst = make_preset("scuc14")
     kw = dict(tol=1e-4, max_iter=100000)
