@@ -114,11 +114,16 @@ typedef struct {
   double restart_nec;     /* 0.8 */
   double restart_long;    /* 0.2 */
   double polish_factor;   /* 1: MIXED switches to FP64 matvecs at kkt <=
-                             factor*tol (1: only on a stall -- FP32 matvecs
-                             reach 1e-4 on the 13k-bus LP in as many
-                             iterations as FP64; 10 polishes the last decade) */
-  int32_t polish_stall;   /* 20: ... or after this many checks without a
-                             10% improvement of the best KKT measure       */
+                             max(factor*tol, polish_floor), or on a stall;
+                             FP32 matvecs reach 1e-4, 1e-5 and 1e-6 on the
+                             13k-bus LP in as many iterations as FP64, so
+                             with factor 1 and tol >= polish_floor the whole
+                             solve runs FP32 matvecs; 10 polishes the last
+                             decade                                        */
+  int32_t polish_stall;   /* 200: ... or after this many checks without a
+                             10% improvement of the best KKT measure (HPR's
+                             KKT measure has plateaus of dozens of checks
+                             that FP64 matvecs do not shorten)              */
   int32_t use_graph;      /* 1: replay each check period as a CUDA graph    */
   int32_t profile;        /* 1: time the two SpMV kernels with CUDA events  */
   int32_t device_ptrs;    /* 1: x0/y0 and x/y/z_out of scuc_lp_solve are
@@ -145,6 +150,10 @@ typedef struct {
                              A holds <= 4096 nonzeros); 1: on the CSR
                              partition, like every other product          */
   int32_t reserved0;      /* 0 */
+  double polish_floor;    /* 1e-6: MIXED moves to FP64 matvecs once kkt <=
+                             this (the accuracy FP32 matvecs were measured to
+                             reach without extra iterations), so tolerances
+                             below it get an FP64 final phase              */
 } scuc_solve_params;
 
 typedef struct {
@@ -423,6 +432,16 @@ int scuc_lp_export(const scuc_lp* lp, int64_t* row_ptr, int32_t* col, double* va
  *    used.                                                               */
 int scuc_lp_kkt_noalloc(scuc_lp* lp, const double* x_dev, const double* y_dev, const double* z_dev,
                         double* out_dev);
+
+/* FMA throughput of the current device, measured (no counterpart in the
+ * paper): every thread of 8 blocks per SM runs eight independent
+ * register-resident FMA chains of 16,384 steps; the best of three timed
+ * launches after one warm-up (CUDA events), clocks left as they are.
+ * fp64: 1 for FP64 (DFMA), 0 for FP32.  tflops receives 2 * FMAs / time in
+ * TFLOP/s, ms (nullable) the launch time.  The FP64 SpMV kernels are bound
+ * by this rate as much as by HBM (one DFMA per nonzero).  Allocates and
+ * frees a small device buffer; SCUC_E_CUDA on a CUDA error.            */
+int scuc_probe_fma_peak(int32_t fp64, double* tflops, double* ms);
 
 void scuc_lp_destroy(scuc_lp* lp);
 

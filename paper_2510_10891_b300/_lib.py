@@ -24,7 +24,8 @@ class SolveParams(C.Structure):
                 ("polish_stall", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("device_ptrs", C.c_int32), ("restart_ref", C.c_int32),
                 ("restart_metric", C.c_int32), ("sigma_update", C.c_int32), ("algo", C.c_int32),
-                ("infeas_tol", C.c_double), ("spmv_layout", C.c_int32), ("reserved0", C.c_int32)]
+                ("infeas_tol", C.c_double), ("spmv_layout", C.c_int32), ("reserved0", C.c_int32),
+                ("polish_floor", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -114,6 +115,7 @@ _SIGS = {
                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                       C.POINTER(SolveInfo), C.POINTER(BatchInfo)]),
     "scuc_lp_kkt_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "scuc_probe_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "scuc_default_fix_params": (None, [C.POINTER(FixParams)]),
     "scuc_fix_and_propagate": (C.c_int, [C.c_void_p, C.POINTER(ScucMap), C.c_void_p, C.c_void_p,
                                          C.POINTER(FixParams), C.c_void_p, C.POINTER(C.c_void_p),

@@ -503,6 +503,7 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
     c.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
     c.check_every = ce;
     c.polish_stall = p.polish_stall;
+    c.polish_floor = p.polish_floor;
     c.log_cap = B.log_cap;
     c.precision = p.precision;
     c.k = 0; c.t = 0; c.iters_fp32 = 0;

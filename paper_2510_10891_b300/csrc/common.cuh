@@ -119,6 +119,7 @@ struct Ctrl {
   uint64_t t_start_ns;     // device clock at the start of the iterations
   uint64_t time_limit_ns;  // > 0: stop with SCUC_ST_TIME_LIMIT after this long (checked at checks)
   double infeas_tol;       // > 0: infeasibility detection at checks (relative certificate violation)
+  double polish_floor;     // MIXED: FP64 matvecs from kkt <= max(polish_factor * tol, polish_floor)
 };
 
 struct PowerCtrl {

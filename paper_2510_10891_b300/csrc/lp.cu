@@ -733,7 +733,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
       (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1 ||
       (p.algo != SCUC_ALGO_HPR && p.algo != SCUC_ALGO_PDHG_AVG) || !(p.infeas_tol >= 0.0 && p.infeas_tol < 1.0) ||
-      (p.spmv_layout != 0 && p.spmv_layout != 1)) {
+      (p.spmv_layout != 0 && p.spmv_layout != 1) || !(p.polish_floor >= 0.0)) {
     set_error("invalid solve parameters");
     return SCUC_E_INVALID;
   }
@@ -795,6 +795,7 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
   C.check_every = p.check_every;
   C.polish_stall = p.polish_stall;
+  C.polish_floor = p.polish_floor;
   C.log_cap = log_cap;
   C.precision = p.precision;
   C.k = 0; C.t = 0; C.iters_fp32 = 0;
@@ -969,7 +970,8 @@ void scuc_default_params(scuc_solve_params* p) {
   p->restart_nec = 0.8;
   p->restart_long = 0.2;
   p->polish_factor = 1.0;
-  p->polish_stall = 20;
+  p->polish_stall = 200;
+  p->polish_floor = 1e-6;
   p->use_graph = 1;
   p->profile = 0;
   p->device_ptrs = 0;

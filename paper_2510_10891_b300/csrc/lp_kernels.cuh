@@ -631,7 +631,7 @@ __device__ long long decide_logic(const DevLP& L, Ctrl* C, scuc_check_log* log, 
   if (status < 0 && C->precision == SCUC_MIXED && !C->fp64_phase) {
     if (kkt < 0.9 * C->best_kkt) { C->best_kkt = kkt; C->stall = 0; }
     else C->stall++;
-    if (kkt <= C->polish_factor * C->tol || C->stall >= C->polish_stall) C->fp64_phase = 1;
+    if (kkt <= fmax(C->polish_factor * C->tol, C->polish_floor) || C->stall >= C->polish_stall) C->fp64_phase = 1;
   }
   C->k = restart ? 0 : k;
   C->t = t;

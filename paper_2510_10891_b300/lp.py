@@ -269,3 +269,11 @@ def solve_batch(lps, outputs=None, autotune=True, **params):
             d["x"], d["y"], d["z"] = host[i]
         res.append(d)
     return res, {f[0]: getattr(bi, f[0]) for f in L.BatchInfo._fields_}
+
+
+def fma_peak(fp64=True):
+    """Measured FMA throughput of the current device in TFLOP/s
+    (scuc_probe_fma_peak): FP64 (DFMA) or FP32.  Returns (tflops, ms)."""
+    t, ms = C.c_double(), C.c_double()
+    L.check(L.lib().scuc_probe_fma_peak(1 if fp64 else 0, C.byref(t), C.byref(ms)))
+    return t.value, ms.value

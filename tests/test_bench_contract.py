@@ -8,15 +8,14 @@ import bench
 
 
 def test_stored_traffic_matches_the_kernel_sources():
-    path = os.path.join(bench.ROOT, "profiles", "spmv_traffic_scuc13k.json")
+    path = os.path.join(bench.ROOT, "profiles", bench.TRAFFIC_FILE)
     with open(path) as f:
         t = json.load(f)
     assert t["csrc_sha"] == bench.csrc_hash(), "SpMV sources changed since the DRAM capture: re-measure"
     assert set(t["dram_bytes_per_launch"]) >= {"primal_fp32", "dual_fp32"}
     # measured traffic is at least the algorithmic bytes' order (no stale tiny value)
-    m, n, nnz = 1598472, 1476000, 113470128
     for kind in ("primal", "dual"):
-        ratio = t["dram_bytes_per_launch"][kind + "_fp32"] / bench.spmv_bytes(m, n, nnz, kind, "fp32")
+        ratio = t["dram_bytes_per_launch"][kind + "_fp32"] / bench.spmv_bytes(t["m"], t["n"], t["nnz"], kind, "fp32")
         assert 0.9 < ratio < 1.5, (kind, ratio)
 
 

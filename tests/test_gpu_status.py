@@ -52,6 +52,25 @@ def test_polish_switch_near_tolerance(P, scuc2k):
     assert oracle.kkt(scuc2k, r["x"], r["y"], r["z"])["kkt"] <= tol * 1.0001
 
 
+def test_polish_switch_at_floor(P, scuc2k):
+    """polish_floor: below the tolerance trigger, the first check with KKT <=
+    polish_floor moves the solve to FP64 matvecs (a tolerance below the
+    accuracy FP32 matvecs reach gets an FP64 final phase)."""
+    tol, floor = 1e-5, 1e-4
+    r = P.LP(scuc2k).solve(tol=tol, precision="mixed", polish_floor=floor, polish_stall=10 ** 6)
+    i, log = r["info"], r["log"]
+    assert i["status"] == ST["optimal"]
+    assert 0 < i["iters_fp32"] < i["iters"]
+    c = _switch_check(log)
+    kkt = [max(e["rp"], e["rd"], e["gap"]) for e in log]
+    assert kkt[c] <= floor and all(k > floor for k in kkt[:c])
+    assert i["iters_fp32"] == log[c]["iter"]
+    assert oracle.kkt(scuc2k, r["x"], r["y"], r["z"])["kkt"] <= tol * 1.0001
+    # with the default floor (1e-6) the same solve keeps FP32 matvecs throughout
+    d = P.LP(scuc2k).solve(tol=tol, precision="mixed", want=("x",))["info"]
+    assert d["status"] == ST["optimal"] and d["iters_fp32"] == d["iters"]
+
+
 def test_polish_switch_on_stall(P, scuc2k):
     """polish_stall = 2 (and no tolerance trigger): the switch follows the
     stall rule replayed on the logged KKT values (a check that does not cut
