@@ -91,7 +91,11 @@ struct Partition {
 // most of their rows, so the lanes of a slice gather nearby vector
 // entries); slices run longest first.  A row shorter than its slice is
 // padded with its last column and a zero value.
-constexpr int kSellWindow = 256;
+constexpr int kSellWindow = 4096;
+// rows longer than this are cut into kChunk-entry chunks (one warp each) in
+// the partitions of a single LP; the sliced ELL copies hold the others (a
+// lane walks its row alone, so longer rows would serialise their slice)
+constexpr int kSellMaxLen = 512;
 struct Sell {
   int nslice = 0;
   int64_t nent = 0;       // entries incl. padding (= sptr[nslice] * 32)

@@ -25,11 +25,13 @@ struct PartPlan {
   int cls_blk[5] = {0, 0, 0, 0, 0};
   int cls_row[5] = {0, 0, 0, 0, 0};
 };
-int build_partition(const std::vector<int>& rp, int m, Partition* P);
+int build_partition(const std::vector<int>& rp, int m, Partition* P, int long_min = kGroupRowMax);
 // sliced ELL structure of a CSR matrix with row pointers rp (values filled
 // on the device by k_sell_fill); freed with the handle's allocations
-int build_sell(const std::vector<int>& rp, int m, Sell* S, std::vector<void*>* allocs);
-void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan);
+// (rows longer than max_len are left out: their sums come from elsewhere)
+int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vector<void*>* allocs);
+void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan,
+                    int long_min = kGroupRowMax);
 int upload_partition(const PartPlan& plan, Partition* P);
 void free_partition(Partition* P);
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s);
@@ -47,7 +49,7 @@ struct Handle {
   double *val = nullptr, *valt = nullptr, *vs = nullptr, *vst = nullptr;
   float *vs32 = nullptr, *vst32 = nullptr;
   Partition pA, pT;
-  Sell sT;  // sliced ELL copy of A^T for the primal step (nslice = 0: none)
+  Sell sT;  // sliced ELL copy of A^T's rows of <= kSellMaxLen nonzeros (primal step)
   // problem data (unscaled and scaled)
   double *c = nullptr, *xl = nullptr, *xu = nullptr, *lo = nullptr, *hi = nullptr;
   double *Dr = nullptr, *Dc = nullptr, *cs = nullptr, *xls = nullptr, *xus = nullptr,

@@ -199,70 +199,94 @@ __global__ void __launch_bounds__(kBlock) k_primal_sum(DevLP L) {
   }
 }
 
-// g = A^T y on the sliced ELL copy of A^T (one LP): one warp per slice of 32
-// columns, one column per lane, summed in row order.  FP32 values: batches
-// of 16 entries per lane (one 8-byte {column, value} load each, all issued
-// before the products), even and odd entries in two accumulators, the last
-// partial batch predicated; FP64 values: batches of 8 into one accumulator
-// (the FP64 pipe, not the loads, bounds the FP64 products).
+// Sum of lane `lane`'s row of slice sl of a sliced ELL copy (Sell), in the
+// row's entry order.  FP32 values: batches of 16 entries per lane (one
+// 8-byte {column, value} load each, all issued before the products), even
+// and odd entries in two accumulators, the last partial batch predicated;
+// FP64 values: batches of 8 into one accumulator (the FP64 pipe, not the
+// loads, bounds the FP64 products).
+__device__ __forceinline__ float sell_sum(const Sell& S, const float* __restrict__ x, int sl, int lane) {
+  constexpr int U = 16;
+  const int steps = S.sptr[sl + 1] - S.sptr[sl];
+  const int2* __restrict__ cv = S.cv32 + (int64_t)S.sptr[sl] * 32 + lane;
+  float a0 = 0.f, a1 = 0.f;
+  int k = 0;
+  for (; k + U <= steps; k += U) {
+    int2 e[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) e[u] = ldcs(cv + (int64_t)(k + u) * 32);
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      a0 = fma_t(__int_as_float(e[u].y), ldg(x + e[u].x), a0);
+      a1 = fma_t(__int_as_float(e[u + 1].y), ldg(x + e[u + 1].x), a1);
+    }
+  }
+  if (k < steps) {
+    int2 e[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) e[u] = k + u < steps ? ldcs(cv + (int64_t)(k + u) * 32) : make_int2(-1, 0);
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      if (e[u].x >= 0) a0 = fma_t(__int_as_float(e[u].y), ldg(x + e[u].x), a0);
+      if (e[u + 1].x >= 0) a1 = fma_t(__int_as_float(e[u + 1].y), ldg(x + e[u + 1].x), a1);
+    }
+  }
+  return a0 + a1;
+}
+
+__device__ __forceinline__ double sell_sum(const Sell& S, const double* __restrict__ x, int sl, int lane) {
+  constexpr int U = 8;
+  const int steps = S.sptr[sl + 1] - S.sptr[sl];
+  const int64_t base = (int64_t)S.sptr[sl] * 32 + lane;
+  const int* __restrict__ cc = S.col + base;
+  const double* __restrict__ vv = S.v64 + base;
+  double a = 0.0;
+  int k = 0;
+  for (; k + U <= steps; k += U) {
+    int c[U];
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      c[u] = ldcs(cc + (int64_t)(k + u) * 32);
+      v[u] = ldcs(vv + (int64_t)(k + u) * 32);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) a = fma_t(v[u], ldg(x + c[u]), a);
+  }
+  for (; k < steps; k++) a = fma_t(ldcs(vv + (int64_t)k * 32), ldg(x + ldcs(cc + (int64_t)k * 32)), a);
+  return a;
+}
+
+// g = A^T y on the sliced ELL copy of A^T (one LP): blocks [0, nsb) take one
+// slice of 32 columns per warp, one column per lane; the blocks after them
+// give each chunked column one thread that adds its chunk sums (the chunk
+// launch ran before) in chunk order, as the CSR kernel does.
 template <int PREC>
 __global__ void __launch_bounds__(kBlock) k_primal_sell(DevLP L) {
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
-  const Sell& S = L.sT;
-  const int sl = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (sl >= S.nslice) return;
-  const int r = S.rows[(size_t)sl * 32 + lane];
-  const int steps = S.sptr[sl + 1] - S.sptr[sl];
-  const int64_t base = (int64_t)S.sptr[sl] * 32 + lane;
-  if (!phase64(ctrl, PREC)) {
-    constexpr int U = 16;
-    const int2* __restrict__ cv = S.cv32 + base;
-    const float* __restrict__ y = L.y32;
-    float a0 = 0.f, a1 = 0.f;
-    int k = 0;
-    for (; k + U <= steps; k += U) {
-      int2 e[U];
-#pragma unroll
-      for (int u = 0; u < U; u++) e[u] = ldcs(cv + (int64_t)(k + u) * 32);
-#pragma unroll
-      for (int u = 0; u < U; u += 2) {
-        a0 = fma_t(__int_as_float(e[u].y), ldg(y + e[u].x), a0);
-        a1 = fma_t(__int_as_float(e[u + 1].y), ldg(y + e[u + 1].x), a1);
-      }
+  const bool fp64 = phase64(ctrl, PREC);
+  const int nsb = (L.sT.nslice + kBlock / 32 - 1) / (kBlock / 32);
+  if ((int)blockIdx.x < nsb) {
+    const int sl = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (sl >= L.sT.nslice) return;
+    const int r = L.sT.rows[(size_t)sl * 32 + lane];
+    if (!fp64) {
+      const float a = sell_sum(L.sT, L.y32, sl, lane);
+      if (r >= 0) L.gsum32[r] = a;
+    } else {
+      const double a = sell_sum(L.sT, L.y, sl, lane);
+      if (r >= 0) L.gsum[r] = a;
     }
-    if (k < steps) {
-      int2 e[U];
-#pragma unroll
-      for (int u = 0; u < U; u++) e[u] = k + u < steps ? ldcs(cv + (int64_t)(k + u) * 32) : make_int2(-1, 0);
-#pragma unroll
-      for (int u = 0; u < U; u += 2) {
-        if (e[u].x >= 0) a0 = fma_t(__int_as_float(e[u].y), ldg(y + e[u].x), a0);
-        if (e[u + 1].x >= 0) a1 = fma_t(__int_as_float(e[u + 1].y), ldg(y + e[u + 1].x), a1);
-      }
-    }
-    if (r >= 0) L.gsum32[r] = a0 + a1;
-  } else {
-    constexpr int U = 8;
-    const int* __restrict__ cc = S.col + base;
-    const double* __restrict__ vv = S.v64 + base;
-    const double* __restrict__ y = L.y;
-    double a = 0.0;
-    int k = 0;
-    for (; k + U <= steps; k += U) {
-      int c[U];
-      double v[U];
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        c[u] = ldcs(cc + (int64_t)(k + u) * 32);
-        v[u] = ldcs(vv + (int64_t)(k + u) * 32);
-      }
-#pragma unroll
-      for (int u = 0; u < U; u++) a = fma_t(v[u], ldg(y + c[u]), a);
-    }
-    for (; k < steps; k++) a = fma_t(ldcs(vv + (int64_t)k * 32), ldg(y + ldcs(cc + (int64_t)k * 32)), a);
-    if (r >= 0) L.gsum[r] = a;
+    return;
   }
+  const int i = ((int)blockIdx.x - nsb) * kBlock + (int)threadIdx.x;
+  if (i >= L.pT.nlong) return;
+  double s = 0.0;
+  for (int c = L.pT.chunk_ptr[i]; c < L.pT.chunk_ptr[i + 1]; c++) s += L.pT.cpart[c];
+  const int r = L.pT.long_rows[i];
+  if (!fp64) L.gsum32[r] = (float)s;
+  else L.gsum[r] = s;
 }
 
 // Primal step, elementwise over the columns of LP blockIdx.y (blockIdx.x of

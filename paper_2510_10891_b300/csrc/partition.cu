@@ -19,16 +19,18 @@ int palloc(T** p, size_t count) {
 }
 }  // namespace
 
-// Host plan of a partition (see Partition): rows with more than kGroupRowMax
-// nonzeros are cut into chunks of kChunk entries when allow_long, else they
-// join the 32-thread list rows; rows of kShortMax+1..kGroupRowMax nonzeros
+// Host plan of a partition (see Partition): rows with more than long_min
+// (<= kGroupRowMax) nonzeros are cut into chunks of kChunk entries when
+// allow_long (otherwise rows above kGroupRowMax join the 32-thread list
+// rows); other rows of kShortMax+1..kGroupRowMax nonzeros
 // get a group of group_size_for(len, shape.ept) threads; runs of at least
 // shape.min_run consecutive short rows are packed into staged blocks of <=
 // kMaxRows rows / <= kNnzCap nonzeros (threads per row = largest power of
 // two with gsz * rows <= kBlock), shorter runs go to 4-thread list rows.
 // List classes run from 32 threads per row down to 4 (longest work first),
 // then the staged blocks, then the long rows.
-void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan) {
+void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan,
+                    int long_min) {
   std::vector<int> G[4];  // G[k]: list rows with 32 >> k threads per row
   *plan = PartPlan{};
   plan->chunk_ptr.assign(1, 0);
@@ -58,7 +60,7 @@ void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, b
     if (len <= kShortMax) continue;
     flush_run(run0, r);
     run0 = r + 1;
-    if (len > kGroupRowMax && allow_long) {
+    if (len > long_min && allow_long) {
       plan->long_rows.push_back(r);
       for (int e = rp[r]; e < rp[r + 1]; e += kChunk)
         plan->chunks.push_back(make_int2(e, std::min(rp[r + 1], e + kChunk)));
@@ -114,33 +116,36 @@ void free_partition(Partition* P) {
   *P = Partition{};
 }
 
-// Sliced ELL structure (Sell, common.cuh): rows sorted by length (longest
-// first, ties by index) within windows of kSellWindow rows, cut into slices
-// of 32; slices ordered longest first (the longest start first, so the
-// launch ends evenly).  Rows longer than kGroupRowMax are not supported
-// (the caller keeps the CSR partition for such matrices).
-int build_sell(const std::vector<int>& rp, int m, Sell* S, std::vector<void*>* allocs) {
+// Sliced ELL structure (Sell, common.cuh): the rows of at most max_len
+// nonzeros (longer rows are left out: no lane computes them), sorted by
+// length (longest first, ties by index) within windows of kSellWindow rows
+// and cut into slices of 32; slices ordered longest first (the longest
+// start first, so the launch ends evenly).
+int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vector<void*>* allocs) {
   *S = Sell{};
   struct Slice {
     int len;
     int first;  // index into order
+    int end;    // end of its window's rows in order
   };
-  std::vector<int> order(m);
+  std::vector<int> order(m > 0 ? m : 1);
   std::vector<Slice> slices;
+  int kept = 0;
   for (int w0 = 0; w0 < m; w0 += kSellWindow) {
     const int w1 = std::min(m, w0 + kSellWindow);
-    for (int r = w0; r < w1; r++) order[r] = r;
-    std::stable_sort(order.begin() + w0, order.begin() + w1,
+    const int k0 = kept;
+    for (int r = w0; r < w1; r++)
+      if (rp[r + 1] - rp[r] <= max_len) order[kept++] = r;
+    std::stable_sort(order.begin() + k0, order.begin() + kept,
                      [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
-    for (int q = w0; q < w1; q += 32) slices.push_back(Slice{rp[order[q] + 1] - rp[order[q]], q});
+    for (int q = k0; q < kept; q += 32) slices.push_back(Slice{rp[order[q] + 1] - rp[order[q]], q, kept});
   }
   std::stable_sort(slices.begin(), slices.end(), [](const Slice& a, const Slice& b) { return a.len > b.len; });
   const int ns = (int)slices.size();
   std::vector<int> sptr(ns + 1, 0), rows((size_t)ns * 32, -1);
   for (int k = 0; k < ns; k++) {
     const Slice& sl = slices[k];
-    const int w1 = std::min(m, (sl.first / kSellWindow + 1) * kSellWindow);
-    for (int l = 0; l < 32 && sl.first + l < w1; l++) rows[(size_t)k * 32 + l] = order[sl.first + l];
+    for (int l = 0; l < 32 && sl.first + l < sl.end; l++) rows[(size_t)k * 32 + l] = order[sl.first + l];
     if ((int64_t)sptr[k] + sl.len > (int64_t)INT32_MAX / 32) {
       set_error("sliced ELL copy of %d rows exceeds 2^31 entries", m);
       return SCUC_E_INVALID;
@@ -164,9 +169,9 @@ int build_sell(const std::vector<int>& rp, int m, Sell* S, std::vector<void*>* a
   return SCUC_OK;
 }
 
-int build_partition(const std::vector<int>& rp, int m, Partition* P) {
+int build_partition(const std::vector<int>& rp, int m, Partition* P, int long_min) {
   PartPlan plan;
-  plan_partition(rp, m, PartShape{}, true, &plan);
+  plan_partition(rp, m, PartShape{}, true, &plan, long_min);
   return upload_partition(plan, P);
 }
 

@@ -1,7 +1,8 @@
 // CSR SpMV core with a per-row epilogue hook (fused into the HPR steps).
 //
-// Rows with more than kGroupRowMax nonzeros ("long rows": the dense PTDF,
-// N-1, balance and reserve rows) are cut into chunks of kChunk entries; a
+// Long rows (more than kSellMaxLen nonzeros in the partitions of one LP:
+// the dense PTDF, N-1, balance and reserve rows) are cut into chunks of
+// kChunk entries; a
 // chunk launch (k_chunk_sums and friends) gives every chunk one warp that
 // streams it with coalesced lane-strided loads (the whole chunk in flight
 // for FP32 values, eight entries per lane at a time for FP64) and stores the

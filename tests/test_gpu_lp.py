@@ -29,7 +29,7 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
 
 
-def _compare_logs(glog, olog, rtol=1e-7):
+def _compare_logs(glog, olog, rtol=1e-7, sigma_rtol=1e-9):
     assert len(glog) == len(olog), (len(glog), len(olog))
     for g, o in zip(glog, olog):
         assert g["iter"] == o["iter"]
@@ -42,7 +42,7 @@ def _compare_logs(glog, olog, rtol=1e-7):
         # relative to the gap
         assert g["gap"] == pytest.approx(o["gap"], rel=rtol, abs=1e-11), ("gap", g, o)
         assert g["pobj"] == pytest.approx(o["pobj"], rel=1e-9, abs=1e-9)
-        assert g["sigma"] == pytest.approx(o["sigma"], rel=1e-9)
+        assert g["sigma"] == pytest.approx(o["sigma"], rel=sigma_rtol)
 
 
 LP_CASES = [
@@ -94,22 +94,23 @@ def test_solve_parity_random(P, case):
 
 @pytest.mark.parametrize("case", LP_CASES + [(5000, 40, 0.002, 4, 0, 1, "GL")])
 def test_spmv_layouts_agree(P, case):
-    """The primal step's A^T y on the sliced ELL copy of A^T (the default) and
-    on the CSR partition (spmv_layout = 1): FP64 solves take the same restart
-    decisions at every check with iterates equal to rounding, and mixed
-    solves reach the tolerance under the oracle's KKT evaluation.  Covers
-    ragged slices, empty columns and a column of 5,000 entries (no sliced
-    copy: both layouts run the CSR partition, bit for bit)."""
+    """The primal step's A^T y on the sliced ELL copy of A^T (the default)
+    and on the CSR partition (spmv_layout = 1): FP64 solves take the same
+    restart decisions at every check with iterates equal to rounding, and
+    mixed solves reach the tolerance under the oracle's KKT evaluation.
+    Covers ragged slices, empty columns, columns of more than 512 entries
+    (chunked, their chunk sums added by the sliced kernel) and a column of
+    5,000 entries."""
     m, n, dens, seed, lr, lc, sen = case
     d = random_lp(m, n, density=dens, seed=seed, long_rows=lr, long_cols=lc, senses=sen)
     lp = P.LP(d)
     kw = dict(tol=1e-6, max_iter=20480, check_every=64)
     a, b = lp.solve(spmv_layout=0, **kw), lp.solve(spmv_layout=1, **kw)
     assert a["info"]["status"] == b["info"]["status"] and a["info"]["iters"] == b["info"]["iters"]
-    _compare_logs(a["log"], b["log"])
+    # sigma is the square root of a ratio of norms of displacements over a
+    # restart cycle: its rounding is amplified like the residuals'
+    _compare_logs(a["log"], b["log"], sigma_rtol=1e-7)
     assert _rel(a["x"], b["x"]) < 1e-8 and _rel(a["y"], b["y"]) < 1e-8
-    if lc and m > 4096:
-        np.testing.assert_array_equal(a["x"], b["x"])
     for layout in (0, 1):
         r = lp.solve(spmv_layout=layout, tol=1e-4, precision="mixed", max_iter=20480)
         assert r["info"]["status"] == 0
