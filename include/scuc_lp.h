@@ -284,7 +284,9 @@ int scuc_lp_matvec(scuc_lp* lp, int32_t transpose, const double* in_dev, double*
  *  infos[count]: per-LP results; setup_ms/solve_ms/launches are those of
  *    the whole batch.  Each handle's check log is replaced by its LP's.
  *  binfo (may be NULL): autotune is read (NULL: on); the chosen SpMV
- *    partition shapes and the batch timings are written.
+ *    partition shapes and the batch timings are written.  Tuned shapes are
+ *    kept for the process, keyed by precision and the LPs' sizes, and a
+ *    later batch with the same key uses them without timing.
  * The call returns after all work has completed.                        */
 typedef struct {
   int32_t autotune;        /* in: 1 = time candidate partition shapes       */
@@ -299,6 +301,12 @@ typedef struct {
   double total_ms;         /* out: whole call                               */
   int64_t launches;        /* out: kernels launched                         */
   int64_t periods;         /* out: check periods run                        */
+  double scale_ms;         /* out: of setup_ms, every LP's scaling and power
+                              method (queued on the LPs' own streams)      */
+  int32_t tune_cached;     /* out: 1 = the shapes came from an earlier batch
+                              of the same precision and LP sizes (no
+                              timing this call)                            */
+  int32_t reserved0;
 } scuc_batch_info;
 
 int scuc_lp_solve_batch(scuc_lp* const* lps, int32_t count, const scuc_solve_params* p,

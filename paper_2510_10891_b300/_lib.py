@@ -47,7 +47,8 @@ class BatchInfo(C.Structure):
                 ("run_T", C.c_int32), ("candidates", C.c_int32), ("blocks_A", C.c_int32),
                 ("blocks_T", C.c_int32), ("setup_ms", C.c_double), ("tune_ms", C.c_double),
                 ("solve_ms", C.c_double), ("total_ms", C.c_double), ("launches", C.c_int64),
-                ("periods", C.c_int64)]
+                ("periods", C.c_int64), ("scale_ms", C.c_double), ("tune_cached", C.c_int32),
+                ("reserved0", C.c_int32)]
 
 
 class CheckLog(C.Structure):

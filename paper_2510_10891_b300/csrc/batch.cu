@@ -12,6 +12,8 @@
 #include <chrono>
 #include <climits>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "lp.h"
@@ -169,6 +171,25 @@ void plan_batch(const std::vector<std::vector<int>>& rps, const std::vector<int>
   for (int q = 0; q < nblk; q++) plan->slot[q] = next[(*blk_lp)[q]]++;
 }
 
+// Shapes chosen for earlier batches, keyed by precision and the sizes of
+// the batch's LPs (m, n, nnz of each, in order).
+std::mutex g_shape_mu;
+std::map<std::vector<int64_t>, std::pair<PartShape, PartShape>> g_shapes;
+
+bool tuned_shapes(const std::vector<int64_t>& key, PartShape* a, PartShape* t) {
+  std::lock_guard<std::mutex> lock(g_shape_mu);
+  auto it = g_shapes.find(key);
+  if (it == g_shapes.end()) return false;
+  *a = it->second.first;
+  *t = it->second.second;
+  return true;
+}
+
+void remember_shapes(const std::vector<int64_t>& key, const PartShape& a, const PartShape& t) {
+  std::lock_guard<std::mutex> lock(g_shape_mu);
+  g_shapes[key] = std::make_pair(a, t);
+}
+
 // Time one SpMV over the candidate partition (median of three launches).
 template <typename VT>
 int time_spmv(const int* rp, const int* col, const VT* val, const VT* in, VT* out, const Partition& P,
@@ -195,9 +216,11 @@ int time_spmv(const int* rp, const int* col, const VT* val, const VT* in, VT* ou
 // upload it: blk / blk0 get the per-block LP table and LP block offsets.
 int tune_partition(Batch& B, bool transpose, const std::vector<std::vector<int>>& rps,
                    const std::vector<int>& off, const std::vector<int64_t>& eoff, bool autotune, Partition* P,
-                   int** blk, int** blk0, PartShape* chosen, int* ncand) {
+                   int** blk, int** blk0, PartShape* chosen, int* ncand, const PartShape* given) {
   std::vector<PartShape> cands;
-  if (autotune) {
+  if (given) {
+    cands.push_back(*given);
+  } else if (autotune) {
     for (int ept : {8, 12, 16})
       for (int run : {16, 64}) {
         PartShape sh;
@@ -343,25 +366,47 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
   const bool mixed = p.precision == SCUC_MIXED;
   int64_t launches = 0;
 
-  // 1. scaling and lambda of every LP, on its own handle (Sec. 3.A, Eq. 9)
+  // 1. scaling and lambda of every LP, on its own handle and stream (Sec.
+  // 3.A, Eq. 9): every LP's scaling and power-method rounds are queued
+  // before any is waited for, so the LPs' small launches overlap
   std::vector<double> lam(nlp, p.lambda_in);
   std::vector<int> piters(nlp, 0);
   std::vector<Ctrl> C(nlp);
+  std::vector<int64_t> l0(nlp);
+  const bool power = !(p.lambda_in > 0.0);
   for (int b = 0; b < nlp; b++) {
     Handle& h = *H[b];
     SCUC_TRY(h.enter());
-    const int64_t l0 = h.nlaunch;
+    l0[b] = h.nlaunch;
     SCUC_TRY(h.setup_scaling(p.use_scaling, mixed));
-    if (!(lam[b] > 0.0)) {
+    if (power) SCUC_TRY(h.power_start(p));
+  }
+  std::vector<char> pdone(nlp, power ? 0 : 1);
+  for (bool all = !power; !all;) {
+    for (int b = 0; b < nlp; b++)
+      if (!pdone[b]) SCUC_TRY(H[b]->power_round(p));
+    all = true;
+    for (int b = 0; b < nlp; b++) {
+      if (pdone[b]) continue;
+      bool d = false;
       double est = 0.0;
-      SCUC_TRY(h.power_method(p, &est, &piters[b]));
-      lam[b] = p.lambda_safety * est;
-      if (!(lam[b] > 0.0)) lam[b] = 1.0;
+      SCUC_TRY(H[b]->power_poll(p, &d, &est, &piters[b]));
+      if (d) {
+        pdone[b] = 1;
+        lam[b] = p.lambda_safety * est;
+        if (!(lam[b] > 0.0)) lam[b] = 1.0;
+      } else {
+        all = false;
+      }
     }
+  }
+  for (int b = 0; b < nlp; b++) {
+    Handle& h = *H[b];
     SCUC_CUDA(cudaMemcpyAsync(&C[b], h.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h.work));
-    launches += h.nlaunch - l0;
+    launches += h.nlaunch - l0[b];
   }
   for (int b = 0; b < nlp; b++) SCUC_CUDA(cudaStreamSynchronize(H[b]->work));
+  const auto ts1 = clk::now();
 
   // 2. the block-diagonal LP
   Batch B;
@@ -458,14 +503,27 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
   SCUC_CUDA(cudaMemcpyAsync(B.col0, B.col0_h.data(), (nlp + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   SCUC_CUDA(cudaStreamSynchronize(s));
 
-  // 3. partitions (autotuned shapes)
+  // 3. partitions (autotuned shapes; a batch of the same LP sizes and
+  // precision reuses the shapes tuned for it before)
   const auto tt0 = clk::now();
   PartShape shA, shT;
   int ncA = 0, ncT = 0;
-  SCUC_TRY(tune_partition(B, false, rps, B.row0_h, B.nnz0_h, autotune, &B.pA, &B.blkA, &B.ablk0, &shA, &ncA));
-  SCUC_TRY(tune_partition(B, true, rpts, B.col0_h, B.nnz0_h, autotune, &B.pT, &B.blkT, &B.tblk0, &shT, &ncT));
+  std::vector<int64_t> key;
+  key.push_back(mixed ? 1 : 0);
+  key.push_back(nlp);
+  for (int b = 0; b < nlp; b++) {
+    key.push_back(H[b]->m);
+    key.push_back(H[b]->n);
+    key.push_back(H[b]->nnz);
+  }
+  const bool cached = autotune && tuned_shapes(key, &shA, &shT);
+  SCUC_TRY(tune_partition(B, false, rps, B.row0_h, B.nnz0_h, autotune && !cached, &B.pA, &B.blkA, &B.ablk0, &shA,
+                          &ncA, cached ? &shA : nullptr));
+  SCUC_TRY(tune_partition(B, true, rpts, B.col0_h, B.nnz0_h, autotune && !cached, &B.pT, &B.blkT, &B.tblk0, &shT,
+                          &ncT, cached ? &shT : nullptr));
+  if (autotune && !cached) remember_shapes(key, shA, shT);
   const double tune_ms = std::chrono::duration<double, std::milli>(clk::now() - tt0).count();
-  if (autotune) launches += 4 * (int64_t)(ncA + ncT);
+  if (autotune && !cached) launches += 4 * (int64_t)(ncA + ncT);
   int maxn = 1;
   for (int b = 0; b < nlp; b++) maxn = std::max(maxn, H[b]->n);
   B.epi_gx = std::max(1, std::min(64, (maxn + kBlock - 1) / kBlock));
@@ -622,7 +680,9 @@ int solve_batch(Handle* const* H, int nlp, const scuc_solve_params& p, double* c
     bi->run_A = shA.min_run;
     bi->ept_T = shT.ept;
     bi->run_T = shT.min_run;
-    bi->candidates = ncA + ncT;
+    bi->candidates = cached ? 0 : ncA + ncT;
+    bi->tune_cached = cached ? 1 : 0;
+    bi->scale_ms = std::chrono::duration<double, std::milli>(ts1 - t0).count();
     bi->setup_ms = setup_ms;
     bi->tune_ms = tune_ms;
     bi->solve_ms = solve_ms;

@@ -72,6 +72,8 @@ Handle::~Handle() {
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   for (auto& e : prof_ev) cudaEventDestroy(e);
   if (ctrl_h) cudaFreeHost(ctrl_h);
+  if (pctrl_host) cudaFreeHost(pctrl_host);
+  if (ev_power) cudaEventDestroy(ev_power);
   if (ev_user) cudaEventDestroy(ev_user);
   if (ev_work) cudaEventDestroy(ev_work);
   for (auto& e : ev_slot)
@@ -543,49 +545,78 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
   return SCUC_OK;
 }
 
-// power method on A_hat (Sec. 3): lambda estimate of lambda_max(A A^T)
-int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters_out) {
+// power method on A_hat (Sec. 3): lambda estimate of lambda_max(A A^T).
+// power_start seeds it, power_round queues 16 iterations and a copy of the
+// state to pinned host memory, power_poll waits for that copy: a batch runs
+// the rounds of all its LPs on their own streams before polling any.
+int Handle::power_start(const scuc_solve_params& p) {
   cudaStream_t s = work;
+  if (!pctrl_host) SCUC_CUDA(cudaMallocHost((void**)&pctrl_host, sizeof(PowerCtrl)));
+  if (!ev_power) SCUC_CUDA(cudaEventCreateWithFlags(&ev_power, cudaEventDisableTiming));
   PowerCtrl P0{};
   P0.tol = p.power_tol;
   P0.max_iter = p.power_max_iter;
-  SCUC_CUDA(cudaMemcpyAsync(pctrl, &P0, sizeof(PowerCtrl), cudaMemcpyHostToDevice, s));
+  *pctrl_host = P0;
+  SCUC_CUDA(cudaMemcpyAsync(pctrl, pctrl_host, sizeof(PowerCtrl), cudaMemcpyHostToDevice, s));
   k_power_seed<<<kNormBlocks, kBlock, 0, s>>>(n, p.power_seed, qv, partRT);
   k_power_seed_norm<<<1, kDecideThreads, 0, s>>>(partRT, kNormBlocks, pctrl);
   // MIXED solves run the products in FP32 (values vs32 / vst32; q in xt32,
   // u = A q in y32: both unused until the iterations start)
-  const bool f32 = p.precision == SCUC_MIXED && vs32 && vst32;
-  float* q32 = f32 ? xt32 : nullptr;
-  k_power_norm_seed<<<grid_for(n), kBlock, 0, s>>>(n, qv, q32, pctrl);
+  power_f32 = p.precision == SCUC_MIXED && vs32 && vst32;
+  k_power_norm_seed<<<grid_for(n), kBlock, 0, s>>>(n, qv, power_f32 ? xt32 : nullptr, pctrl);
   nlaunch += 3;
   SCUC_CUDA(cudaGetLastError());
-  PowerCtrl P{};
-  for (int it = 0; it < p.power_max_iter; it += 16) {
-    for (int j = 0; j < 16; j++) {
-      if (f32) {
-        if (pA.nchunk) k_chunk_sums<float><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs32, q32, pA);
-        if (pA.nblk)
-          k_power_spmv32<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs32, q32, pA, nullptr, y32, partRA, pctrl);
-        if (pT.nchunk) k_chunk_sums<float><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst32, y32, pT);
-        if (pT.nblk)
-          k_power_spmv32<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst32, y32, pT, wv, xt32, partRT, pctrl);
-      } else {
-        if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA);
-        if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
-        if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, uv, pT);
-        if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
-      }
-      k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);
-      k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, q32, pctrl);
-      nlaunch += 2 + (pA.nblk ? 1 : 0) + (pT.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0) + (pT.nchunk ? 1 : 0);
+  power_rounds = 0;
+  return SCUC_OK;
+}
+
+int Handle::power_round(const scuc_solve_params& p) {
+  cudaStream_t s = work;
+  const bool f32 = power_f32;
+  float* q32 = f32 ? xt32 : nullptr;
+  for (int j = 0; j < 16; j++) {
+    if (f32) {
+      if (pA.nchunk) k_chunk_sums<float><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs32, q32, pA);
+      if (pA.nblk)
+        k_power_spmv32<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs32, q32, pA, nullptr, y32, partRA, pctrl);
+      if (pT.nchunk) k_chunk_sums<float><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst32, y32, pT);
+      if (pT.nblk)
+        k_power_spmv32<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst32, y32, pT, wv, xt32, partRT, pctrl);
+    } else {
+      if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA);
+      if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
+      if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, uv, pT);
+      if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
     }
-    SCUC_CUDA(cudaGetLastError());
-    SCUC_CUDA(cudaMemcpyAsync(&P, pctrl, sizeof(PowerCtrl), cudaMemcpyDeviceToHost, s));
-    SCUC_CUDA(cudaStreamSynchronize(s));
-    if (P.done) break;
+    k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);
+    k_power_norm<<<grid_for(n), kBlock, 0, s>>>(n, wv, qv, q32, pctrl);
+    nlaunch += 2 + (pA.nblk ? 1 : 0) + (pT.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0) + (pT.nchunk ? 1 : 0);
   }
-  *lam_out = P.lam;
-  *iters_out = P.it;
+  SCUC_CUDA(cudaGetLastError());
+  SCUC_CUDA(cudaMemcpyAsync(pctrl_host, pctrl, sizeof(PowerCtrl), cudaMemcpyDeviceToHost, s));
+  SCUC_CUDA(cudaEventRecord(ev_power, s));
+  power_rounds++;
+  (void)p;
+  return SCUC_OK;
+}
+
+// after the last queued round: *done once the estimate has converged or
+// max_iter iterations have run (the device stops counting there)
+int Handle::power_poll(const scuc_solve_params& p, bool* done, double* lam, int* iters) {
+  SCUC_CUDA(cudaEventSynchronize(ev_power));
+  *done = pctrl_host->done != 0 || power_rounds * 16 >= p.power_max_iter;
+  *lam = pctrl_host->lam;
+  *iters = pctrl_host->it;
+  return SCUC_OK;
+}
+
+int Handle::power_method(const scuc_solve_params& p, double* lam_out, int* iters_out) {
+  SCUC_TRY(power_start(p));
+  bool done = false;
+  while (!done) {
+    SCUC_TRY(power_round(p));
+    SCUC_TRY(power_poll(p, &done, lam_out, iters_out));
+  }
   return SCUC_OK;
 }
 

@@ -98,6 +98,13 @@ struct Handle {
   DevLP dev() const;
   int setup_scaling(int use_scaling, bool need_f32);
   int power_method(const scuc_solve_params& p, double* lam, int* iters);
+  int power_start(const scuc_solve_params& p);
+  int power_round(const scuc_solve_params& p);
+  int power_poll(const scuc_solve_params& p, bool* done, double* lam, int* iters);
+  PowerCtrl* pctrl_host = nullptr;  // pinned copy of the power method's state
+  cudaEvent_t ev_power = nullptr;
+  bool power_f32 = false;
+  int power_rounds = 0;
   int ensure_log(int cap);
   template <int PREC>
   int launch_iterations(cudaStream_t s, int check_every, bool profile);

@@ -91,9 +91,17 @@ def test_batch_mixed_precision_certified_by_the_oracle(P, mixed_lps):
 def test_autotune_shapes_and_untuned_partition(P, mixed_lps):
     handles = [P.LP(d) for d in mixed_lps]
     r1, b1 = P.solve_batch(handles, autotune=True, tol=1e-6, precision="fp64")
-    assert b1["candidates"] == 12
+    # tuned now (12 shapes timed) or earlier in this process (same sizes)
+    assert (b1["candidates"], b1["tune_cached"]) in ((12, 0), (0, 1))
     assert b1["ept_A"] in (8, 12, 16) and b1["ept_T"] in (8, 12, 16)
     assert b1["run_A"] in (16, 64) and b1["run_T"] in (16, 64)
+    # a second batch of the same sizes reuses the tuned shapes without timing
+    r2, b2 = P.solve_batch(handles, autotune=True, tol=1e-6, precision="fp64")
+    assert b2["tune_cached"] == 1 and b2["candidates"] == 0
+    assert [b2[k] for k in ("ept_A", "run_A", "ept_T", "run_T")] == [b1[k] for k in ("ept_A", "run_A", "ept_T",
+                                                                                        "run_T")]
+    for a, b in zip(r1, r2):
+        assert a["info"]["iters"] == b["info"]["iters"] and a["info"]["pobj"] == b["info"]["pobj"]
     r0, b0 = P.solve_batch(handles, autotune=False, tol=1e-6, precision="fp64")
     assert b0["candidates"] == 2 and (b0["ept_A"], b0["run_A"]) == (12, 32)
     for a, b in zip(r1, r0):

@@ -349,11 +349,17 @@ def test_trained_network_gains_on_the_13k_bus_relaxation(P, W, torch_cuda):
     preds = {"trained": net.predict(Xe), "untrained": untrained.predict(Xe),
              "feature_mean": T.mean_predictor(Y, Xe.shape[0])}
     res = {"cold": cold["iters"]}
+    d = oracle.as_lp(inst)
     for name, pred in preds.items():
         x0, _ = W.assemble(lp, lay, pred)
         xw = torch.empty(lp.n, dtype=torch.float64, device="cuda")
-        info = lp.solve_warm(x0, x_out=xw, **kw)["info"]
+        yw = torch.empty(lp.m, dtype=torch.float64, device="cuda")
+        zw = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+        info = lp.solve_warm(x0, x_out=xw, y_out=yw, z_out=zw, **kw)["info"]
         assert info["kkt"] <= 1e-4
+        # the oracle's FP64 evaluation of the returned point agrees
+        k = oracle.kkt(d, xw.cpu().numpy(), yw.cpu().numpy(), zw.cpu().numpy())
+        assert k["kkt"] <= 1e-4 * 1.0001 and k["kkt"] == pytest.approx(info["kkt"], rel=1e-6), (name, k, info)
         dist = float(torch.linalg.vector_norm(xw - xc) / torch.linalg.vector_norm(xc))
         res[name] = info["iters"]
         print("%s: %d iterations (%s), |x - x_cold| / |x_cold| = %.3g" % (name, info["iters"],
