@@ -517,6 +517,9 @@ def main():
                          "--ncu-precision fp64) on this preset, no JSON line")
     ap.add_argument("--ncu-precision", default="mixed", choices=["mixed", "fp64"],
                     help="matvec precision of the --ncu-case iterations")
+    ap.add_argument("--ncu-ws", type=int, default=0,
+                    help="profiling target: the warm-start network's prediction for this many synthetic "
+                         "generator-hours (twice), no JSON line")
     ap.add_argument("--ncu-fix", default=None,
                     help="profiling target: one fixing round (Round, Algorithm 1, propagation, reduced LP) "
                          "on this preset after a mixed-precision solve to 1e-4, no JSON line")
@@ -530,6 +533,17 @@ def main():
         r = lp.solve(want=("x",), tol=0.0, max_iter=128, use_graph=0, precision=args.ncu_precision,
                      polish_stall=10 ** 6, polish_factor=0.0)
         print("ncu case %s: %d iterations" % (args.ncu_case, r["info"]["iters"]))
+        return 0
+    if args.ncu_ws:
+        import torch
+        from paper_2510_10891_b300 import warmstart as WS
+        net = WS.WarmStartNet.load(WS_WEIGHTS)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        X = torch.randn((args.ncu_ws, net.dims[0]), generator=g, device="cuda", dtype=torch.float32)
+        for _ in range(2):
+            p = net.predict(X)
+        torch.cuda.synchronize()
+        print("ncu ws: %d rows, mean prediction %s" % (args.ncu_ws, p.mean(0).tolist()))
         return 0
     if args.ncu_fix:
         import paper_2510_10891_b300 as P

@@ -60,7 +60,8 @@ enum scuc_err {
   SCUC_E_INVALID = 1,        /* bad argument or malformed input             */
   SCUC_E_CUDA = 2,           /* a CUDA runtime call failed                  */
   SCUC_E_OOM = 3,            /* device allocation failed                    */
-  SCUC_E_DEVICE_TIMEOUT = 4, /* reserved: no kernel of this library waits   */
+  SCUC_E_DEVICE_TIMEOUT = 4, /* a kernel's bounded wait ran out (the warm-
+                                start network's tcgen05 GEMM)               */
   SCUC_E_INFEASIBLE = 5      /* propagation proved the fixed model infeasible */
 };
 

@@ -88,6 +88,18 @@ int scuc_ws_train(scuc_ws* ws, const float* X_dev, const float* Y_dev, int64_t n
                   const int32_t* idx_dev, int32_t batch, int32_t steps, const scuc_ws_train_params* p,
                   double* losses);
 
+/* Kernels of the forward products (no counterpart in the paper; both are
+ * BF16 operands with FP32 accumulation, summed in different orders):
+ * SCUC_WS_GEMM_TCGEN05 (the default) runs the hidden layers whose input
+ * width is a multiple of 64 up to 256 and whose output width is a multiple
+ * of 16 up to 256 on tcgen05 (TMA loads, tensor-memory accumulator, bias and
+ * activation in its epilogue) and the other layers on mma.sync;
+ * SCUC_WS_GEMM_MMA_SYNC runs every layer on mma.sync.  A bounded wait of the
+ * tcgen05 kernel that runs out makes predict / gradients / train return
+ * SCUC_E_DEVICE_TIMEOUT.  SCUC_E_INVALID for another kind.               */
+enum { SCUC_WS_GEMM_TCGEN05 = 0, SCUC_WS_GEMM_MMA_SYNC = 1 };
+int scuc_ws_set_gemm(scuc_ws* ws, int32_t kind);
+
 void scuc_ws_destroy(scuc_ws* ws);
 
 /* ------------------------------------------------------------------------

@@ -117,6 +117,7 @@ _SIGS = {
                                       C.POINTER(SolveInfo), C.POINTER(BatchInfo)]),
     "scuc_lp_kkt_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "scuc_probe_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "scuc_ws_set_gemm": (C.c_int, [C.c_void_p, C.c_int32]),
     "scuc_default_fix_params": (None, [C.POINTER(FixParams)]),
     "scuc_fix_and_propagate": (C.c_int, [C.c_void_p, C.POINTER(ScucMap), C.c_void_p, C.c_void_p,
                                          C.POINTER(FixParams), C.c_void_p, C.POINTER(C.c_void_p),

@@ -1,10 +1,16 @@
 // Warm-start network (scuc_ws_* in include/scuc_ws.h): a multilayer
 // perceptron with hand-written forward, backward and Adam kernels.
 //
-// GEMMs run on the tensor cores (mma m16n8k16, BF16 operands, FP32
-// accumulation); operands are converted to BF16 while they are staged in
-// shared memory, so one kernel serves the forward product (X W), the weight
-// gradient (H^T dZ, split over the batch) and the input gradient (dZ W^T).
+// GEMMs run on the tensor cores with BF16 operands and FP32 accumulation.
+// The hidden layers' forward products H W (K and N up to 256: all but a
+// few per cent of the network's flops) run on the fifth-generation tensor
+// cores: operands brought into shared memory by TMA, tcgen05.mma issued by
+// one thread with the accumulator in tensor memory, and an epilogue that
+// reads it back with tcgen05.ld and adds the bias, the ReLU and the BF16
+// copy for the next layer.  The other products (the first layer's 12
+// inputs, the 3 outputs, the weight gradient H^T dZ split over the batch
+// and the input gradient dZ W^T with FP32 dZ) use one mma.sync kernel whose
+// operands are converted to BF16 while they are staged in shared memory.
 // Master weights, biases and Adam moments are FP32.  Every reduction (batch
 // loss, bias gradient, split-K partial products) has a fixed order, so
 // training is deterministic.
@@ -12,6 +18,7 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime)
 #include <cuda_bf16.h>
 
 #include "../../include/scuc_ws.h"
@@ -108,6 +115,197 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(int M, int N, int K, int 
       if (c < N) C[(int64_t)(r + 8) * ldc + c] = acc[t][2];
       if (c + 1 < N) C[(int64_t)(r + 8) * ldc + c + 1] = acc[t][3];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM on tcgen05: Z[rows x N] = act(H[rows x K] W[K x N] + b)
+// for K a multiple of 64 up to 256 and N a multiple of 16 up to 256.  One
+// CTA of 4 warps takes 128 rows.  Thread 0 loads the CTA's H rows and all of
+// W^T (K-major, BF16) with TMA in 128-byte-swizzled chunks of 64 K values
+// (one mbarrier counts the bytes), then issues K/16 tcgen05.mma of
+// 128 x N x 16 into a TMEM accumulator of 128 lanes x N columns and commits
+// them to a second mbarrier.  Each warp then reads its 32 lanes (rows) with
+// tcgen05.ld and writes Z (FP32; null: not kept) and the BF16 copy.  Waits are bounded: a
+// wait that runs out sets *err, waits once more for the copies in flight,
+// skips the products and frees the TMEM.
+// ---------------------------------------------------------------------------
+constexpr int kTcM = 128, kTcThreads = 128, kTcKc = 64;
+constexpr int kTcMaxK = 256, kTcMaxN = 256;
+constexpr long long kTcSpin = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// true once the phase with the given parity has completed; false after
+// kTcSpin polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kTcSpin; i++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in 128-byte
+// swizzle: rows of 128 bytes (64 BF16), 8-row atoms of 1,024 bytes (the
+// stride between atoms), leading offset unused in this mode.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmap_h,
+                                                          const __grid_constant__ CUtensorMap tmap_w, int rows,
+                                                          int N, int K, uint32_t tmem_cols,
+                                                          const float* __restrict__ bias, int relu,
+                                                          float* __restrict__ Z, __nv_bfloat16* __restrict__ Hb,
+                                                          int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_ok;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1,024-byte alignment
+  const int nk = K / kTcKc;
+  const uint32_t a_bytes = kTcM * 128u, b_bytes = (uint32_t)N * 128u;
+  const uint32_t sa = base, sb = base + (uint32_t)nk * a_bytes;
+  const int m0 = blockIdx.x * kTcM;
+  const uint32_t btma = smem_u32(&bar_tma), bmma = smem_u32(&bar_mma);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    mbar_init(btma, 1);
+    mbar_init(bmma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    mbar_expect_tx(btma, (uint32_t)nk * (a_bytes + b_bytes));
+    for (int kc = 0; kc < nk; kc++) {
+      tma_load_2d(sa + (uint32_t)kc * a_bytes, &tmap_h, kc * kTcKc, m0, btma);
+      tma_load_2d(sb + (uint32_t)kc * b_bytes, &tmap_w, kc * kTcKc, 0, btma);
+    }
+    if (!mbar_wait(btma, 0)) {
+      ok = 0;
+      atomicOr(err, 1);
+      mbar_wait(btma, 0);  // once more for the copies in flight
+    }
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = idesc_bf16(kTcM, N);
+      for (int kc = 0; kc < nk; kc++)
+        for (int ks = 0; ks < kTcKc / 16; ks++) {
+          const uint64_t ad = umma_desc_sw128(sa + (uint32_t)kc * a_bytes + (uint32_t)ks * 32u);
+          const uint64_t bd = umma_desc_sw128(sb + (uint32_t)kc * b_bytes + (uint32_t)ks * 32u);
+          const uint32_t acc = (kc | ks) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bmma)
+                   : "memory");
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  bool ok = s_ok != 0;
+  if (ok && !mbar_wait(bmma, 0)) {
+    atomicOr(err, 2);
+    mbar_wait(bmma, 0);
+    ok = false;
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < rows) {
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+          float t = __uint_as_float(r[q]) + bias[c0 + q];
+          v[q] = relu ? fmaxf(t, 0.f) : t;
+        }
+        if (Z) {
+          float4* zp = reinterpret_cast<float4*>(Z + (int64_t)row * N + c0);
+#pragma unroll
+          for (int q = 0; q < 4; q++) zp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        if (Hb) {
+          __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+          for (int q = 0; q < 16; q++) h[q] = __float2bfloat16_rn(v[q]);
+          uint4* hp = reinterpret_cast<uint4*>(Hb + (int64_t)row * N + c0);
+          hp[0] = reinterpret_cast<const uint4*>(h)[0];
+          hp[1] = reinterpret_cast<const uint4*>(h)[1];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// Wt[j][k] = W[k][j] (BF16, K x N -> N x K)
+__global__ void k_transpose_bf16(int K, int N, const __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wt) {
+  const int64_t total = (int64_t)K * N, step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += step) {
+    const int64_t j = e / K, k = e - j * K;
+    Wt[e] = W[k * N + j];
   }
 }
 
@@ -270,6 +468,39 @@ int grid_e(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 148 * 8));
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 2-D tensor map of a row-major BF16 matrix [rows x cols] (cols contiguous,
+// a multiple of 8) read in boxes of 64 columns x box_rows rows with
+// 128-byte swizzle; rows past the end read as zero.
+int bf16_tmap(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int cols, int box_rows) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f) {
+      set_error("cuTensorMapEncodeTiled is not available");
+      return SCUC_E_CUDA;
+    }
+    encode = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcKc, (cuuint32_t)box_rows};
+  const cuuint32_t estride[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dim, stride,
+                            box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %d BF16 matrix", (int)r, (long long)rows, cols);
+    return SCUC_E_CUDA;
+  }
+  return SCUC_OK;
+}
+
 }  // namespace
 
 struct Mlp {
@@ -279,6 +510,9 @@ struct Mlp {
   int device = 0;
   std::vector<float*> W, b, gW, gb, mW, vW, mb, vb;
   std::vector<__nv_bfloat16*> Wb;
+  std::vector<__nv_bfloat16*> Wt;  // W_l^T (BF16, N x K) of the layers on tcgen05, else null
+  int* tc_err = nullptr;           // bounded waits of k_gemm_tc that ran out
+  int gemm_kind = 0;               // 0: tcgen05 for the eligible layers, 1: mma.sync for all
   float *mean = nullptr, *scale = nullptr;
   // activations for up to cap rows; activation gradients for up to tcap rows
   std::vector<float*> Z;
@@ -375,11 +609,56 @@ struct Mlp {
     return SCUC_OK;
   }
 
-  // Z_l for every layer from the standardized input Xs
-  int forward(int rows) {
+  // layers whose forward product runs on tcgen05: BF16 input (not the
+  // first layer), K a multiple of 64 up to 256, N a multiple of 16 up to 256
+  bool tc_layer(int l) const {
+    const int K = dims[l], N = dims[l + 1];
+    return l > 0 && K % kTcKc == 0 && K <= kTcMaxK && N % 16 == 0 && N >= 16 && N <= kTcMaxN;
+  }
+  static uint32_t tmem_cols(int N) {
+    uint32_t c = 32;
+    while ((int)c < N) c <<= 1;
+    return c;
+  }
+  int forward_tc(int l, int rows, bool keep_z) {
+    const int K = dims[l], N = dims[l + 1];
+    k_transpose_bf16<<<grid_e((int64_t)K * N), 256, 0, s>>>(K, N, Wb[l], Wt[l]);
+    CUtensorMap th, tw;
+    SCUC_TRY(bf16_tmap(&th, Hb[l - 1], rows, K, kTcM));
+    SCUC_TRY(bf16_tmap(&tw, Wt[l], N, K, N));
+    const int smem = 1024 + (K / kTcKc) * (kTcM * 128 + N * 128);
+    SCUC_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_gemm_tc<<<(rows + kTcM - 1) / kTcM, kTcThreads, smem, s>>>(th, tw, rows, N, K, tmem_cols(N), b[l],
+                                                                  l < nl - 1 ? 1 : 0,
+                                                                  keep_z || l == nl - 1 ? Z[l] : nullptr,
+                                                                  l < nl - 1 ? Hb[l] : nullptr, tc_err);
+    SCUC_CUDA(cudaGetLastError());
+    return SCUC_OK;
+  }
+  // after the stream has drained: a bounded wait of k_gemm_tc that ran out
+  int tc_check() {
+    int e = 0;
+    SCUC_CUDA(cudaMemcpyAsync(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+      SCUC_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
+      set_error("tensor-core GEMM: a TMA or MMA completion wait ran out (flags %d)", e);
+      return SCUC_E_DEVICE_TIMEOUT;
+    }
+    return SCUC_OK;
+  }
+
+  // Z_l for every layer from the standardized input Xs; keep_z = false
+  // (prediction) keeps only the BF16 activations of the hidden layers that
+  // run on tcgen05 (their FP32 Z is needed by the backward pass only)
+  int forward(int rows, bool keep_z = true) {
     for (int l = 0; l < nl; l++) {
       const int K = dims[l], N = dims[l + 1];
       const dim3 g((N + kTN - 1) / kTN, (rows + kTM - 1) / kTM, 1);
+      if (gemm_kind == 0 && tc_layer(l)) {
+        SCUC_TRY(forward_tc(l, rows, keep_z));  // bias and activation in its epilogue
+        continue;
+      }
       if (l == 0)
         k_gemm<float, __nv_bfloat16><<<g, kGemmThreads, 0, s>>>(rows, N, K, K, Xs, K, 1, Wb[l], N, 1, Z[l], N, 0);
       else
@@ -543,7 +822,14 @@ int scuc_ws_create(scuc_ws** out, int32_t nlayers, const int32_t* dims, void* cu
   M.mW.assign(nlayers, nullptr); M.vW.assign(nlayers, nullptr);
   M.mb.assign(nlayers, nullptr); M.vb.assign(nlayers, nullptr);
   M.Wb.assign(nlayers, nullptr);
+  M.Wt.assign(nlayers, nullptr);
+  rc = M.alloc(&M.tc_err, 1);
+  if (rc == SCUC_OK && cudaMemsetAsync(M.tc_err, 0, sizeof(int), M.s) != cudaSuccess) {
+    scuc::set_error("scuc_ws_create: cudaMemsetAsync failed");
+    rc = SCUC_E_CUDA;
+  }
   for (int l = 0; l < nlayers && rc == SCUC_OK; l++) {
+    if (M.tc_layer(l) && (rc = M.alloc(&M.Wt[l], (size_t)dims[l] * dims[l + 1]))) break;
     const size_t nw = (size_t)dims[l] * dims[l + 1], nb = dims[l + 1];
     if ((rc = M.alloc(&M.W[l], nw)) || (rc = M.alloc(&M.b[l], nb)) || (rc = M.alloc(&M.gW[l], nw)) ||
         (rc = M.alloc(&M.gb[l], nb)) || (rc = M.alloc(&M.mW[l], nw)) || (rc = M.alloc(&M.vW[l], nw)) ||
@@ -666,11 +952,11 @@ int scuc_ws_predict(scuc_ws* w, const float* X_dev, int32_t rows, float* out_dev
   SCUC_TRY(dg.rc);
   SCUC_TRY(M.ensure(rows, false));
   SCUC_TRY(M.standardize(rows, X_dev, nullptr, nullptr));
-  SCUC_TRY(M.forward(rows));
+  SCUC_TRY(M.forward(rows, false));
   scuc::k_heads<<<scuc::grid_e(rows), 256, 0, M.s>>>(rows, M.Z[M.nl - 1], out_dev);
   SCUC_CUDA(cudaGetLastError());
   SCUC_CUDA(cudaStreamSynchronize(M.s));
-  return SCUC_OK;
+  return M.tc_check();
 }
 
 int scuc_ws_gradients(scuc_ws* w, const float* X_dev, const float* Y_dev, int32_t rows,
@@ -701,7 +987,7 @@ int scuc_ws_gradients(scuc_ws* w, const float* X_dev, const float* Y_dev, int32_
     }
   }
   SCUC_CUDA(cudaStreamSynchronize(M.s));
-  return SCUC_OK;
+  return M.tc_check();
 }
 
 int scuc_ws_train(scuc_ws* w, const float* X_dev, const float* Y_dev, int64_t nsamples, const int32_t* idx_dev,
@@ -738,6 +1024,15 @@ int scuc_ws_train(scuc_ws* w, const float* X_dev, const float* Y_dev, int64_t ns
   }
   if (losses) SCUC_CUDA(cudaMemcpyAsync(losses, M.loss_d, steps * sizeof(double), cudaMemcpyDeviceToHost, M.s));
   SCUC_CUDA(cudaStreamSynchronize(M.s));
+  return M.tc_check();
+}
+
+int scuc_ws_set_gemm(scuc_ws* w, int32_t kind) {
+  if (!w || (kind != SCUC_WS_GEMM_TCGEN05 && kind != SCUC_WS_GEMM_MMA_SYNC)) {
+    scuc::set_error("scuc_ws_set_gemm: invalid arguments");
+    return SCUC_E_INVALID;
+  }
+  w->m.gemm_kind = kind;
   return SCUC_OK;
 }
 

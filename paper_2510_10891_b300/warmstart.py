@@ -78,6 +78,12 @@ class WarmStartNet:
         L.check(L.lib().scuc_ws_get_params(self.h, C.c_void_p(out.ctypes.data)))
         return out
 
+    def set_gemm(self, kind):
+        """Forward-product kernels: "tcgen05" (default: the eligible hidden
+        layers on the fifth-generation tensor cores) or "mma_sync" (all
+        layers on mma.sync)."""
+        L.check(L.lib().scuc_ws_set_gemm(self.h, {"tcgen05": 0, "mma_sync": 1}[kind]))
+
     def set_input_norm(self, mean, scale):
         self.mean = np.ascontiguousarray(mean, dtype=np.float32)
         self.scale = np.ascontiguousarray(scale, dtype=np.float32)

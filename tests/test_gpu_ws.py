@@ -87,6 +87,35 @@ def test_predict_matches_oracle(W, torch_cuda, rows):
     assert np.median(err) < 0.004
 
 
+@pytest.mark.parametrize("rows", [1, 127, 128, 4096 + 37])
+def test_tcgen05_forward_matches_mma_sync(W, torch_cuda, rows):
+    """The hidden layers' products on tcgen05 (TMA, tensor-memory accumulator,
+    fused bias and ReLU: the default) against the same network on mma.sync:
+    both multiply the same BF16 operands with FP32 accumulation, so they
+    differ by the order of the FP32 sums (and a rare BF16 rounding of an
+    activation that this moves); ragged row counts around the 128-row tile.
+    Gradients of a batch agree the same way."""
+    torch = torch_cuda
+    X, Y = _features(rows, 11)
+    mean = X.mean(0).astype(np.float32) if rows > 1 else np.zeros(DIMS[0], np.float32)
+    scale = np.full(DIMS[0], 2.0, np.float32)
+    net, _ = _net(W, 13, mean, scale)
+    Xd = torch.as_tensor(X, device="cuda")
+    net.set_gemm("mma_sync")
+    ref = net.predict(Xd).cpu().numpy()
+    net.set_gemm("tcgen05")
+    out = net.predict(Xd).cpu().numpy()
+    err = np.abs(out - ref)
+    assert err.max() < 5e-3 and err.mean() < 1e-4, (err.max(), err.mean())
+    if rows > 1:
+        Yd = torch.as_tensor(Y, device="cuda")
+        l1, g1 = net.gradients(Xd, Yd)
+        net.set_gemm("mma_sync")
+        l0, g0 = net.gradients(Xd, Yd)
+        assert l1 == pytest.approx(l0, rel=1e-4)
+        assert np.linalg.norm(g1 - g0) <= 1e-3 * np.linalg.norm(g0)
+
+
 def test_gradients_match_oracle(W, torch_cuda):
     torch = torch_cuda
     rows = 1000 + 13
