@@ -392,12 +392,13 @@ int Handle::setup_solver(const std::vector<int>& rp32, const std::vector<int>& r
   // ELL copies below hold the rest for the iteration products
   SCUC_TRY(build_partition(rp32, m, &pA, kSellMaxLen));
   SCUC_TRY(build_partition(rpt_h, n, &pT, kSellMaxLen));
-  // sliced ELL copy of the rows of A^T that are not chunked (primal step;
-  // its values follow each scaling).  The dual step stays on the CSR
-  // partition: its short rows are staged runs, its long rows chunks
-  // (measured faster than a sliced copy of A's short rows plus an
+  // the sliced ELL copy of A^T (primal step) is built at the first solve
+  // that uses it (a reduced LP that is only exported or batched never
+  // needs it); the row pointers are kept until then.  The dual step stays
+  // on the CSR partition: its short rows are staged runs, its long rows
+  // chunks (measured faster than a sliced copy of A's short rows plus an
   // elementwise update on the 13k-bus LP: 0.199 vs 0.210 ms).
-  if (m > 0 && n > 0) SCUC_TRY(build_sell(rpt_h, n, kSellMaxLen, &sT, &allocs));
+  rpt_plan = rpt_h;
   for (Partition* P : {&pA, &pT})
     for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
                     (void*)P->cpart, (void*)P->slot})
@@ -801,6 +802,13 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
     }
   }
 
+  if (!sell_planned && p.spmv_layout == 0) {
+    // sliced ELL copy of the rows of A^T that are not chunked; its values
+    // are filled after every scaling
+    if (m > 0 && n > 0) SCUC_TRY(build_sell(rpt_plan, n, kSellMaxLen, &sT, &allocs));
+    sell_planned = true;
+    std::vector<int>().swap(rpt_plan);
+  }
   SCUC_TRY(setup_scaling(p.use_scaling, mixed));
   double lambda = p.lambda_in;
   int piters = 0;

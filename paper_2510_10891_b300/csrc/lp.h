@@ -50,6 +50,8 @@ struct Handle {
   float *vs32 = nullptr, *vst32 = nullptr;
   Partition pA, pT;
   Sell sT;  // sliced ELL copy of A^T's rows of <= kSellMaxLen nonzeros (primal step)
+  std::vector<int> rpt_plan;  // row pointers of A^T until sT is built (at the first solve)
+  bool sell_planned = false;
   // problem data (unscaled and scaled)
   double *c = nullptr, *xl = nullptr, *xu = nullptr, *lo = nullptr, *hi = nullptr;
   double *Dr = nullptr, *Dc = nullptr, *cs = nullptr, *xls = nullptr, *xus = nullptr,
