@@ -282,8 +282,7 @@ __global__ void __launch_bounds__(kBlock) k_primal_sell(DevLP L) {
   }
   const int i = ((int)blockIdx.x - nsb) * kBlock + (int)threadIdx.x;
   if (i >= L.pT.nlong) return;
-  double s = 0.0;
-  for (int c = L.pT.chunk_ptr[i]; c < L.pT.chunk_ptr[i + 1]; c++) s += L.pT.cpart[c];
+  const double s = chunk_total(L.pT, i);
   const int r = L.pT.long_rows[i];
   if (!fp64) L.gsum32[r] = (float)s;
   else L.gsum[r] = s;

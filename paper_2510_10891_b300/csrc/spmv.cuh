@@ -210,6 +210,24 @@ __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT
   if (lane == 0) part.cpart[w] = (double)s;
 }
 
+// Sum of long row li's chunk sums, in chunk order: loaded eight at a time
+// so a row of many chunks (a 21,000-entry row has 41) waits for one batch,
+// not one load per chunk; the adds keep their order (the same result).
+__device__ __forceinline__ double chunk_total(const Partition& part, int li) {
+  int c = part.chunk_ptr[li];
+  const int ce = part.chunk_ptr[li + 1];
+  double s = 0.0;
+  for (; c + 8 <= ce; c += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) v[u] = part.cpart[c + u];
+#pragma unroll
+    for (int u = 0; u < 8; u++) s += v[u];
+  }
+  for (; c < ce; c++) s += part.cpart[c];
+  return s;
+}
+
 // What a block of the main launch needs to know about its rows, loaded
 // before the value type is chosen.
 struct BlockPlan {
@@ -273,11 +291,7 @@ __device__ __forceinline__ void spmv_run(const BlockPlan& bp, const int* __restr
                                          Epi& epi) {
   const int tid = threadIdx.x;
   if (bp.kind == 2) {
-    if (bp.li >= 0) {
-      double s = 0.0;
-      for (int c = part.chunk_ptr[bp.li]; c < part.chunk_ptr[bp.li + 1]; c++) s += part.cpart[c];
-      epi.row(bp.er, (VT)s);
-    }
+    if (bp.li >= 0) epi.row(bp.er, (VT)chunk_total(part, bp.li));
     return;
   }
   VT* s_sum = reinterpret_cast<VT*>(smem + kNnzCap * 12);

@@ -7,7 +7,7 @@ to 1e-4 KKT; the targets of every unit-hour are extracted from the solution
 on the GPU (scuc_ws_targets).  Training runs the library's own forward,
 backward and Adam kernels (scuc_ws_train).
 
-    python -m paper_2510_10891_b300.ws_train --instances 48 --steps 3000 \\
+    python -m paper_2510_10891_b300.ws_train --instances 2000 --steps 20000 \\
         --out paper_2510_10891_b300/weights/ws_mlp.npz
 """
 from __future__ import annotations
@@ -67,6 +67,31 @@ def collect(items, tol=1e-4, precision="mixed"):
     return torch.cat(Xs), torch.cat(Ys), infos
 
 
+def collect_batched(items, group=64, tol=1e-4, precision="mixed"):
+    """The same targets from batched cold solves (scuc_lp_solve_batch) of
+    consecutive groups of instances, in order, on the default partition
+    shapes (timed shapes could differ between runs and change the rounding
+    of the solutions, so the weights would not be reproducible)."""
+    import torch
+    from .lp import solve_batch
+    Xs, Ys, infos = [], [], []
+    for g0 in range(0, len(items), group):
+        grp = items[g0:g0 + group]
+        lps = [LP(inst) for inst, _, _ in grp]
+        outs = [(torch.empty(lp.n, dtype=torch.float64, device="cuda"),
+                 torch.empty(lp.m, dtype=torch.float64, device="cuda"), None) for lp in lps]
+        res, _ = solve_batch(lps, outputs=outs, autotune=False, tol=tol, precision=precision)
+        for (inst, feats, arrays), lp, (x, y, _), r in zip(grp, lps, outs, res):
+            if r["info"]["status"] != 0:
+                continue  # only solutions that reached the tolerance are kept
+            Ys.append(W.targets(lp, W.Layout(arrays), x, y))
+            Xs.append(torch.as_tensor(feats, device="cuda"))
+            infos.append(r["info"])
+        for lp in lps:
+            lp.close()
+    return torch.cat(Xs), torch.cat(Ys), infos
+
+
 def fit(X, Y, steps=3000, batch=4096, seed=0, dims=W.DEFAULT_DIMS, **tp):
     """Standardisation from the training features, seeded initial weights and
     sample draws (one permutation per epoch), then training on the GPU."""
@@ -97,9 +122,9 @@ def mean_predictor(Y, rows):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--instances", type=int, default=48)
+    ap.add_argument("--instances", type=int, default=2000)
     ap.add_argument("--first-seed", type=int, default=10000)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workers", type=int, default=16)
@@ -109,7 +134,7 @@ def main(argv=None):
     t0 = time.time()
     items = generate(batch_configs(a.instances, a.first_seed), a.workers)
     t1 = time.time()
-    X, Y, infos = collect(items)
+    X, Y, infos = collect_batched(items)
     t2 = time.time()
     net, losses = fit(X, Y, a.steps, a.batch, a.seed)
     t3 = time.time()
