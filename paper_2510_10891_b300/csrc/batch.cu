@@ -86,7 +86,7 @@ struct Batch {
       if (e) cudaEventDestroy(e);
     free_partition(&pA);
     free_partition(&pT);
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) dev_free(p);
     if (ctrl_h) cudaFreeHost(ctrl_h);
     if (s) cudaStreamDestroy(s);
   }

@@ -101,13 +101,15 @@ int Handle::row_violations(const double* x_in, int on_device, double tol, int32_
   int *flag = nullptr, *pos = nullptr, *rows = nullptr;
   unsigned long long* worst = nullptr;
   SCUC_TRY(dev_alloc_bytes((void**)&flag, (m + 1) * sizeof(int)));
-  struct Free {
+  struct Free {  // after the stream's work that uses them
+    cudaStream_t s;
     void** p[4];
     ~Free() {
+      cudaStreamSynchronize(s);
       for (void** q : p)
-        if (*q) cudaFree(*q);
+        if (*q) dev_free(*q);
     }
-  } freer{{(void**)&flag, (void**)&pos, (void**)&rows, (void**)&worst}};
+  } freer{s, {(void**)&flag, (void**)&pos, (void**)&rows, (void**)&worst}};
   SCUC_TRY(dev_alloc_bytes((void**)&pos, (m + 1) * sizeof(int)));
   SCUC_TRY(dev_alloc_bytes((void**)&rows, (m + 1) * sizeof(int)));
   SCUC_TRY(dev_alloc_bytes((void**)&worst, sizeof(unsigned long long)));
@@ -154,13 +156,15 @@ int Handle::add_rows(const Handle& pool, const int32_t* sel_h, int32_t count, Ha
   cudaStream_t s = work;
   int *sel = nullptr, *len = nullptr, *off = nullptr;
   SCUC_TRY(dev_alloc_bytes((void**)&sel, (count + 1) * sizeof(int)));
-  struct Free {
+  struct Free {  // after the stream's work that uses them
+    cudaStream_t s;
     void** p[3];
     ~Free() {
+      cudaStreamSynchronize(s);
       for (void** q : p)
-        if (*q) cudaFree(*q);
+        if (*q) dev_free(*q);
     }
-  } freer{{(void**)&sel, (void**)&len, (void**)&off}};
+  } freer{s, {(void**)&sel, (void**)&len, (void**)&off}};
   SCUC_TRY(dev_alloc_bytes((void**)&len, (count + 1) * sizeof(int)));
   SCUC_TRY(dev_alloc_bytes((void**)&off, (count + 1) * sizeof(int)));
   if (count) SCUC_CUDA(cudaMemcpyAsync(sel, sel_h, count * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -181,12 +185,14 @@ int Handle::add_rows(const Handle& pool, const int32_t* sel_h, int32_t count, Ha
   void *d_rp = nullptr, *d_col = nullptr, *d_val = nullptr, *d_c = nullptr, *d_xl = nullptr, *d_xu = nullptr,
        *d_lo = nullptr, *d_hi = nullptr;
   std::vector<void*> owned;
-  struct FreeOwned {
+  struct FreeOwned {  // arrays not passed to a new handle, after the stream's work
+    cudaStream_t s;
     std::vector<void*>& v;
     ~FreeOwned() {
-      for (void* q : v) cudaFree(q);
+      if (!v.empty()) cudaStreamSynchronize(s);
+      for (void* q : v) dev_free(q);
     }
-  } free_owned{owned};
+  } free_owned{s, owned};
   auto oalloc = [&](void** q, size_t bytes) -> int {
     SCUC_TRY(dev_alloc_bytes(q, bytes));
     owned.push_back(*q);

@@ -181,22 +181,37 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
     const double lmax = a > 0.0 ? oxu : oxl;
     const double hii = hi[i], loi = lo[i], mni = mn[i], mxi = mx[i];
     const int cmni = cmn[i], cmxi = cmx[i];
+    // A candidate b = q / a replaces the lane's running bound only if it is
+    // strictly tighter, and that needs q below (or above) the exact product
+    // bound * a (rounding is monotone and the bound is representable).  The
+    // rounded product is within 2^-53 of the exact one (plus 2^-1074 when it
+    // underflows), so a q beyond it by more than 1e-15 of its size plus
+    // 1e-300 cannot tighten the bound: the (slow) FP64 division is skipped
+    // and the result is unchanged.
     if (isfinite(hii) && !(cmxi == 0 && mxi <= hii)) {  // a x_j <= hi - (min activity of the rest)
       const bool ok = isinf(lmin) ? (cmni == 1) : (cmni == 0);
       if (ok) {
         const double rest = isinf(lmin) ? mni : __dsub_rn(mni, __dmul_rn(a, lmin));
-        const double b = __ddiv_rn(__dsub_rn(hii, rest), a);
-        if (a > 0.0) { if (b < nhi) nhi = b; }
-        else { if (b > nlo) nlo = b; }
+        const double q = __dsub_rn(hii, rest);
+        const double p = __dmul_rn(a > 0.0 ? nhi : nlo, a);  // b < nhi (a > 0) or b > nlo (a < 0) needs q < p
+        if (!(q > p + 1e-15 * fabs(p) + 1e-300)) {
+          const double b = __ddiv_rn(q, a);
+          if (a > 0.0) { if (b < nhi) nhi = b; }
+          else { if (b > nlo) nlo = b; }
+        }
       }
     }
     if (isfinite(loi) && !(cmni == 0 && mni >= loi)) {  // a x_j >= lo - (max activity of the rest)
       const bool ok = isinf(lmax) ? (cmxi == 1) : (cmxi == 0);
       if (ok) {
         const double rest = isinf(lmax) ? mxi : __dsub_rn(mxi, __dmul_rn(a, lmax));
-        const double b = __ddiv_rn(__dsub_rn(loi, rest), a);
-        if (a > 0.0) { if (b > nlo) nlo = b; }
-        else { if (b < nhi) nhi = b; }
+        const double q = __dsub_rn(loi, rest);
+        const double p = __dmul_rn(a > 0.0 ? nlo : nhi, a);  // b > nlo (a > 0) or b < nhi (a < 0) needs q > p
+        if (!(q < p - 1e-15 * fabs(p) - 1e-300)) {
+          const double b = __ddiv_rn(q, a);
+          if (a > 0.0) { if (b > nlo) nlo = b; }
+          else { if (b < nhi) nhi = b; }
+        }
       }
     }
   }
@@ -433,12 +448,14 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q);
     return SCUC_OK;
   };
-  struct Free {
+  struct Free {  // temporaries, after the stream's work that uses them
+    cudaStream_t s;
     std::vector<void*>& v;
     ~Free() {
-      for (void* q : v) cudaFree(q);
+      if (!v.empty()) cudaStreamSynchronize(s);
+      for (void* q : v) dev_free(q);
     }
-  } freer{tmp};
+  } freer{s, tmp};
 
   int *ui = nullptr, *vi = nullptr, *wi = nullptr, *flags = nullptr;
   int8_t *uinit = nullptr, *fixd = nullptr;
@@ -557,12 +574,14 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
          *d_lo = nullptr, *d_hi = nullptr, *d_rpt = nullptr, *d_colt = nullptr, *d_permt = nullptr,
          *d_valt = nullptr;
     std::vector<void*> owned;
-    struct FreeOwned {
+    struct FreeOwned {  // arrays not passed to the reduced handle, after the stream's work
+      cudaStream_t s;
       std::vector<void*>& v;
       ~FreeOwned() {
-        for (void* q : v) cudaFree(q);
+        if (!v.empty()) cudaStreamSynchronize(s);
+        for (void* q : v) dev_free(q);
       }
-    } free_owned{owned};
+    } free_owned{s, owned};
     auto oalloc = [&](void** q, size_t bytes) -> int {
       SCUC_TRY(dev_alloc_bytes(q, bytes));
       owned.push_back(*q);

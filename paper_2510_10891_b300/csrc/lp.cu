@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <chrono>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -25,17 +26,77 @@ void set_error(const char* fmt, ...) {
   g_err = buf;
 }
 
-template <typename T>
-static int dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  SCUC_CUDA(cudaMalloc((void**)p, count * sizeof(T) + 64));  // padding: aligned bulk copies
+// Device memory of the library comes from one stream-ordered pool per
+// device that keeps freed blocks for reuse (release threshold: never), so
+// the handles and temporaries of successive fixing rounds are served from
+// memory already mapped, and a free does not synchronise the device as
+// cudaFree does.  Allocations and frees are ordered on an internal stream;
+// an allocation waits for that stream (usually idle) so the block can be
+// used from any stream at once.  A caller frees a block only after the work
+// that uses it has completed.
+namespace {
+constexpr int kMaxPoolDevices = 256;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+cudaStream_t g_pool_stream[kMaxPoolDevices] = {};
+
+int pool_for(int dev, cudaMemPool_t* pool, cudaStream_t* st) {
+  if (dev < 0 || dev >= kMaxPoolDevices) {
+    set_error("device ordinal %d out of range", dev);
+    return SCUC_E_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t q = nullptr;
+    SCUC_CUDA(cudaMemPoolCreate(&q, &props));
+    uint64_t keep = UINT64_MAX;
+    SCUC_CUDA(cudaMemPoolSetAttribute(q, cudaMemPoolAttrReleaseThreshold, &keep));
+    SCUC_CUDA(cudaStreamCreateWithFlags(&g_pool_stream[dev], cudaStreamNonBlocking));
+    g_pool[dev] = q;
+  }
+  *pool = g_pool[dev];
+  *st = g_pool_stream[dev];
   return SCUC_OK;
 }
+}  // namespace
 
 int dev_alloc_bytes(void** p, size_t bytes) {
   *p = nullptr;
-  SCUC_CUDA(cudaMalloc(p, bytes + 64));
+  int dev = 0;
+  SCUC_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  cudaStream_t st;
+  SCUC_TRY(pool_for(dev, &pool, &st));
+  SCUC_CUDA(cudaMallocFromPoolAsync(p, bytes + 64, pool, st));  // padding: aligned bulk copies
+  SCUC_CUDA(cudaStreamSynchronize(st));
+  return SCUC_OK;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return;
+  }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != a.device) cudaSetDevice(a.device);
+  cudaMemPool_t pool;
+  cudaStream_t st;
+  if (pool_for(a.device, &pool, &st) == SCUC_OK) cudaFreeAsync(p, st);
+  if (cur >= 0 && cur != a.device) cudaSetDevice(cur);
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+  void* q = nullptr;
+  SCUC_TRY(dev_alloc_bytes(&q, (count ? count : 1) * sizeof(T)));
+  *p = static_cast<T*>(q);
   return SCUC_OK;
 }
 
@@ -68,7 +129,10 @@ int exclusive_scan(const int* in, int n, int* out, cudaStream_t s) {
 }
 
 Handle::~Handle() {
-  for (void* p : allocs) cudaFree(p);
+  // the handle's kernels run on work (and graphs launched on it); none may
+  // still read its memory when it returns to the pool
+  if (work) cudaStreamSynchronize(work);
+  for (void* p : allocs) dev_free(p);
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   for (auto& e : prof_ev) cudaEventDestroy(e);
   if (ctrl_h) cudaFreeHost(ctrl_h);
@@ -88,6 +152,10 @@ int Handle::alloc(T** p, size_t count) {
   allocs.push_back((void*)*p);
   return SCUC_OK;
 }
+// element types other files allocate through a handle
+template int Handle::alloc<int>(int**, size_t);
+template int Handle::alloc<double>(double**, size_t);
+template int Handle::alloc<float>(float**, size_t);
 
 // ---------------------------------------------------------------------------
 // validation (host, before any launch)

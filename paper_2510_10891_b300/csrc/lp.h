@@ -35,7 +35,8 @@ void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, b
 int upload_partition(const PartPlan& plan, Partition* P);
 void free_partition(Partition* P);
 int exclusive_scan(const int* in, int n, int* out, cudaStream_t s);
-int dev_alloc_bytes(void** p, size_t bytes);
+int dev_alloc_bytes(void** p, size_t bytes);  // from the device's pool (lp.cu)
+void dev_free(void* p);                       // back to the pool; the caller has drained its users
 
 struct Handle {
   int32_t m = 0, n = 0;

@@ -26,6 +26,7 @@
 
 namespace scuc {
 int dev_alloc_bytes(void** p, size_t bytes);
+void dev_free(void* p);
 
 namespace {
 
@@ -527,7 +528,8 @@ struct Mlp {
   std::vector<void*> allocs;
 
   ~Mlp() {
-    for (void* p : allocs) cudaFree(p);
+    if (s) cudaStreamSynchronize(s);
+    for (void* p : allocs) dev_free(p);
   }
   template <typename T>
   int alloc(T** p, size_t count) {
@@ -544,7 +546,7 @@ struct Mlp {
       auto it = std::find(allocs.begin(), allocs.end(), p);
       if (it != allocs.end()) {
         allocs.erase(it);
-        cudaFree(p);
+        dev_free(p);
       }
     }
     return SCUC_OK;

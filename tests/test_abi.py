@@ -48,3 +48,16 @@ def test_binding_has_a_signature_for_every_declared_function():
 def test_last_error_is_callable_without_a_gpu(so):
     so.scuc_last_error.restype = ctypes.c_char_p
     assert isinstance(so.scuc_last_error(), bytes)
+
+
+def test_library_leaves_none_of_its_own_symbols_undefined(so):
+    """Every function of the library is defined in it (a template used by
+    one file and defined in another must be instantiated there), so loading
+    with immediate binding succeeds on a machine without a GPU."""
+    import subprocess
+    from paper_2510_10891_b300 import build
+    out = subprocess.run(["nm", "-D", "-C", "--undefined-only", build.SO], capture_output=True, text=True,
+                         check=True).stdout
+    own = [line for line in out.splitlines() if "scuc::" in line or " scuc_" in line]
+    assert not own, own
+    ctypes.CDLL(build.SO, mode=ctypes.RTLD_GLOBAL | os.RTLD_NOW)
