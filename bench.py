@@ -61,6 +61,11 @@ def spmv_bytes(m, n, nnz_a, kind, prec):
 # partition planner): the stored DRAM traffic is valid while they are
 SPMV_SOURCES = ("common.cuh", "spmv.cuh", "lp_kernels.cuh", "partition.cu")
 TRAFFIC_FILE = "spmv_traffic_scuc6k.json"
+# the launches of one half-step, timed together by the profiled solves
+STEP_KERNELS = {
+    "primal": "primal step: k_primal_sell (update fused) on plain iterations, + k_primal_epi on checks",
+    "dual": "dual step: k_dual_fused + k_dual_long on plain iterations, k_chunks_iter + k_dual on checks",
+}
 
 
 def csrc_hash():
@@ -673,7 +678,7 @@ def main():
             traffic_note = "ncu DRAM bytes of the %s launch on the %s LP x %.3f (algorithmic-bytes ratio)" % (
                 key, t["workload"], scale)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_source": traffic_note, "kernel": "k_%s (%s matvec)" % ({"dual": "dual", "primal": "primal"}[dk], dp),
+            "traffic": traffic, "traffic_source": traffic_note, "kernel": "%s (%s matvec)" % (STEP_KERNELS[dk], dp),
             "bytes_per_launch": byts, "avg_launch_ms": avg_ms, "launches": dn, "peak_source": peak_src,
             "all_kernels": {"%s_%s" % k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
                                           "GBps": spmv_bytes(m, n, nnz_a, k[0], "fp64" if k[1] == "fp64" else "fp32")

@@ -150,7 +150,18 @@ typedef struct {
                              lane) when the handle has one (every column of
                              A holds <= 4096 nonzeros); 1: on the CSR
                              partition, like every other product          */
-  int32_t reserved0;      /* 0 */
+  int32_t split_steps;    /* scuc_lp_solve with spmv_layout 0 (batches keep
+                             separate launches): 0: on plain (non-check)
+                             iterations the primal update runs in the sliced
+                             ELL product's launch (iterates bit-identical to
+                             1), and, when A has rows above 512 nonzeros,
+                             the dual step runs A's other rows on a sliced
+                             ELL copy of A in the launch of the long rows'
+                             chunk warps, their updates fused (their sums in
+                             row order: iterates equal to rounding); 1: the
+                             product and the update as separate launches on
+                             the CSR partition of A, as on check
+                             iterations                                   */
   double polish_floor;    /* 1e-6: MIXED moves to FP64 matvecs once kkt <=
                              this (the accuracy FP32 matvecs were measured to
                              reach without extra iterations), so tolerances

@@ -24,7 +24,7 @@ class SolveParams(C.Structure):
                 ("polish_stall", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("device_ptrs", C.c_int32), ("restart_ref", C.c_int32),
                 ("restart_metric", C.c_int32), ("sigma_update", C.c_int32), ("algo", C.c_int32),
-                ("infeas_tol", C.c_double), ("spmv_layout", C.c_int32), ("reserved0", C.c_int32),
+                ("infeas_tol", C.c_double), ("spmv_layout", C.c_int32), ("split_steps", C.c_int32),
                 ("polish_floor", C.c_double)]
 
 

@@ -467,6 +467,7 @@ int Handle::setup_solver(const std::vector<int>& rp32, const std::vector<int>& r
   // chunks (measured faster than a sliced copy of A's short rows plus an
   // elementwise update on the 13k-bus LP: 0.199 vs 0.210 ms).
   rpt_plan = rpt_h;
+  if (pA.nchunk) rp_plan = rp32;
   for (Partition* P : {&pA, &pT})
     for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
                     (void*)P->cpart, (void*)P->slot})
@@ -536,6 +537,7 @@ DevLP Handle::dev() const {
   L.x = x; L.x0 = x0; L.xt = xt; L.xbar = xbar; L.zbar = zbar; L.y = y; L.y0 = y0; L.ybar = ybar;
   L.xt32 = xt32; L.y32 = y32;
   L.sT = sT;
+  L.sA = sA;
   L.qchk = uv; L.dychk = dychk;  // uv: power-method scratch, free during iterations
   L.dxchk = dxchk;
   L.coef = coef; L.coef_w = coef;
@@ -607,6 +609,12 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
   if (sT.nslice) {
     k_sell_fill<<<(sT.nslice + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(sT, rpt, colt, vst,
                                                                               need_f32 ? vst32 : nullptr);
+    nlaunch += 1;
+    SCUC_CUDA(cudaGetLastError());
+  }
+  if (sA.nslice) {
+    k_sell_fill<<<(sA.nslice + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(sA, rp, col, vs,
+                                                                              need_f32 ? vs32 : nullptr);
     nlaunch += 1;
     SCUC_CUDA(cudaGetLastError());
   }
@@ -709,22 +717,30 @@ int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
   for (int j = 0; j < check_every; j++) {
     const bool chk = (j == check_every - 1);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 0], s));
+    // plain iterations: the update fused into the product's launch
+    const bool fuse_p = !chk && !split_steps && use_sell;
+    const bool fuse_d = !chk && !split_steps && use_sell_dual;
+    if (pT.nchunk) k_chunks_iter<kChunksPrimal, PREC><<<pT.nchunkblk, kBlock, 0, s>>>(L);
     if (use_sell) {
-      if (pT.nchunk) k_chunks_iter<kChunksPrimal, PREC><<<pT.nchunkblk, kBlock, 0, s>>>(L);
       const int g = (sT.nslice + kBlock / 32 - 1) / (kBlock / 32) + (pT.nlong + kBlock - 1) / kBlock;
-      if (g) k_primal_sell<PREC><<<g, kBlock, 0, s>>>(L);
-    } else {
-      if (pT.nchunk) k_chunks_iter<kChunksPrimal, PREC><<<pT.nchunkblk, kBlock, 0, s>>>(L);
-      if (pT.nblk) k_primal_sum<PREC><<<pT.nblk, kBlock, pT.smem, s>>>(L);
+      if (g && fuse_p) k_primal_sell<PREC, true><<<g, kBlock, 0, s>>>(L, j);
+      else if (g) k_primal_sell<PREC, false><<<g, kBlock, 0, s>>>(L, j);
+    } else if (pT.nblk) {
+      k_primal_sum<PREC><<<pT.nblk, kBlock, pT.smem, s>>>(L);
     }
     if (chk) k_primal_epi<true, PREC><<<epi_gx, kBlock, 0, s>>>(L, j);
-    else k_primal_epi<false, PREC><<<epi_gx, kBlock, 0, s>>>(L, j);
+    else if (!fuse_p) k_primal_epi<false, PREC><<<epi_gx, kBlock, 0, s>>>(L, j);
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 1], s));
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 2], s));
-    if (pA.nchunk) k_chunks_iter<kChunksDual, PREC><<<pA.nchunkblk, kBlock, 0, s>>>(L);
-    if (pA.nblk) {
-      if (chk) k_dual<true, PREC><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
-      else k_dual<false, PREC><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
+    if (fuse_d) {
+      k_dual_fused<PREC><<<(sA.nslice + kBlock / 32 - 1) / (kBlock / 32) + pA.nchunkblk, kBlock, 0, s>>>(L, j);
+      k_dual_long<PREC><<<(pA.nlong + 63) / 64, 64, 0, s>>>(L, j);
+    } else {
+      if (pA.nchunk) k_chunks_iter<kChunksDual, PREC><<<pA.nchunkblk, kBlock, 0, s>>>(L);
+      if (pA.nblk) {
+        if (chk) k_dual<true, PREC><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
+        else k_dual<false, PREC><<<pA.nblk, kBlock, pA.smem, s>>>(L, j);
+      }
     }
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 3], s));
   }
@@ -737,7 +753,10 @@ int64_t Handle::period_kernels(int check_every) const {
   const int la = (pA.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0), lt = (pT.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0);
   const int gt = (sT.nslice + kBlock / 32 - 1) / (kBlock / 32) + (pT.nlong + kBlock - 1) / kBlock;
   const int lt_iter = use_sell ? (pT.nchunk ? 1 : 0) + (gt ? 1 : 0) : lt;
-  return 2 + (int64_t)check_every * (la + lt_iter + 1) + (la + lt) * (detect ? 2 : 1);
+  // a plain iteration: primal product (+ update unless fused), dual step
+  const int plain_p = lt_iter + (!split_steps && use_sell ? 0 : 1);
+  const int plain_d = la;  // the fused dual step is two launches as well
+  return 2 + (int64_t)(check_every - 1) * (plain_p + plain_d) + (la + lt_iter + 1) + (la + lt) * (detect ? 2 : 1);
 }
 
 // check SpMVs (FP64) and the decide kernel of a period
@@ -842,7 +861,8 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
       (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1 ||
       (p.algo != SCUC_ALGO_HPR && p.algo != SCUC_ALGO_PDHG_AVG) || !(p.infeas_tol >= 0.0 && p.infeas_tol < 1.0) ||
-      (p.spmv_layout != 0 && p.spmv_layout != 1) || !(p.polish_floor >= 0.0)) {
+      (p.spmv_layout != 0 && p.spmv_layout != 1) || (p.split_steps != 0 && p.split_steps != 1) ||
+      !(p.polish_floor >= 0.0)) {
     set_error("invalid solve parameters");
     return SCUC_E_INVALID;
   }
@@ -874,8 +894,12 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
     // sliced ELL copy of the rows of A^T that are not chunked; its values
     // are filled after every scaling
     if (m > 0 && n > 0) SCUC_TRY(build_sell(rpt_plan, n, kSellMaxLen, &sT, &allocs));
+    // and of A's rows when A has chunked rows (the dual step of plain
+    // iterations runs them beside the chunk warps)
+    if (m > 0 && n > 0 && pA.nchunk) SCUC_TRY(build_sell(rp_plan, m, kSellMaxLen, &sA, &allocs));
     sell_planned = true;
     std::vector<int>().swap(rpt_plan);
+    std::vector<int>().swap(rp_plan);
   }
   SCUC_TRY(setup_scaling(p.use_scaling, mixed));
   double lambda = p.lambda_in;
@@ -906,6 +930,8 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   algo = p.algo;
   detect = p.infeas_tol > 0.0;
   use_sell = sT.nslice > 0 && p.spmv_layout == 0;
+  split_steps = p.split_steps != 0;
+  use_sell_dual = sA.nslice > 0 && pA.nchunk > 0 && p.spmv_layout == 0;
   C.s_step = 1.0 / (lambda * p.sigma0);
   C.polish_factor = p.polish_factor;
   C.max_iter = ((p.max_iter + ce - 1) / ce) * ce;
@@ -960,9 +986,10 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   int64_t n_p = 0, n_d = 0, n_p32 = 0, n_d32 = 0;
   int timed_out = 0;
   if (use_graph) {
-    const void* key[8] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
+    const void* key[9] = {(const void*)(intptr_t)p.check_every, (const void*)vs32, (const void*)log_d,
                           (const void*)coef, (const void*)(intptr_t)(mixed ? 0 : 1), (const void*)(intptr_t)algo,
-                          (const void*)(intptr_t)(detect ? 1 : 0), (const void*)(intptr_t)(use_sell ? 1 : 0)};
+                          (const void*)(intptr_t)(detect ? 1 : 0), (const void*)(intptr_t)(use_sell ? 1 : 0),
+                          (const void*)(intptr_t)(split_steps ? 1 : 0)};
     if (!graph_exec || memcmp(key, graph_key, sizeof(key)) != 0) {
       if (graph_exec) {
         cudaGraphExecDestroy(graph_exec);

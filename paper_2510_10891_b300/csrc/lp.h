@@ -51,7 +51,9 @@ struct Handle {
   float *vs32 = nullptr, *vst32 = nullptr;
   Partition pA, pT;
   Sell sT;  // sliced ELL copy of A^T's rows of <= kSellMaxLen nonzeros (primal step)
+  Sell sA;  // the same of A's rows when A has chunked rows (dual step of plain iterations)
   std::vector<int> rpt_plan;  // row pointers of A^T until sT is built (at the first solve)
+  std::vector<int> rp_plan;   // row pointers of A until sA is built (A with chunked rows)
   bool sell_planned = false;
   // problem data (unscaled and scaled)
   double *c = nullptr, *xl = nullptr, *xu = nullptr, *lo = nullptr, *hi = nullptr;
@@ -75,7 +77,7 @@ struct Handle {
   int log_cap = 0, last_nlog = 0;
   cudaGraphExec_t graph_exec = nullptr;
   // check_every, FP32 values, log, coef, initial phase, algorithm, detection, layout
-  const void* graph_key[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const void* graph_key[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t aux = nullptr;  // capture stream of the graph's conditional bodies
   double* coef = nullptr;
   int64_t nlaunch = 0, graph_nodes = 0;  // kernels launched by this handle; nodes of the period graph
@@ -115,6 +117,8 @@ struct Handle {
   int64_t period_kernels(int check_every) const;
   int algo = SCUC_ALGO_HPR;  // of the current solve (kernels launched by the checks)
   bool use_sell = false;     // the current solve's primal products run on sT
+  bool split_steps = false;  // the current solve keeps product and update apart on plain iterations
+  bool use_sell_dual = false;  // the current solve's plain dual steps run k_dual_fused
   bool detect = false;       // infeasibility detection in the current solve
   int launch_period(int check_every, bool profile, bool fp64);
   int build_solve_graph(int check_every, int phase64);

@@ -28,6 +28,7 @@ struct DevLP {
   int epi_gx;                  // blocks per LP of the primal epilogue (partP: epi_gx * nlp slots)
   Partition pA, pT;
   Sell sT;                     // sliced ELL copy of A^T (one LP; nslice = 0: none)
+  Sell sA;                     // sliced ELL copy of A's rows of <= kSellMaxLen nonzeros (one LP)
   Ctrl* ctrl;
   scuc_check_log* log;
   // A batch of nlp LPs stored as one block-diagonal LP (nlp = 1: one LP).
@@ -260,12 +261,18 @@ __device__ __forceinline__ double sell_sum(const Sell& S, const double* __restri
 // g = A^T y on the sliced ELL copy of A^T (one LP): blocks [0, nsb) take one
 // slice of 32 columns per warp, one column per lane; the blocks after them
 // give each chunked column one thread that adds its chunk sums (the chunk
-// launch ran before) in chunk order, as the CSR kernel does.
-template <int PREC>
-__global__ void __launch_bounds__(kBlock) k_primal_sell(DevLP L) {
+// launch ran before) in chunk order, as the CSR kernel does.  EPI (plain
+// iterations): the thread that owns a column runs the primal update on it
+// (operands loaded before the sum) instead of storing g for the elementwise
+// launch; g is rounded as it would have been stored, so the iterates are
+// bit-identical to the two-launch form that check iterations keep.
+template <int PREC, bool EPI>
+__global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_primal_sell(DevLP L, int j) {
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
   const bool fp64 = phase64(ctrl, PREC);
+  PrimalEpi<false> epi{L, ctrl->sigma, EPI ? L.coef[2 * j] : 0.0, EPI ? L.coef[2 * j + 1] : 0.0, fp64,
+                       ctrl->algo == SCUC_ALGO_PDHG_AVG, false, {0.0, 0.0, 0.0, 0.0}, 0.0, 0.0, 0.0, 0.0, 0.0};
   const int nsb = (L.sT.nslice + kBlock / 32 - 1) / (kBlock / 32);
   if ((int)blockIdx.x < nsb) {
     const int sl = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -273,18 +280,28 @@ __global__ void __launch_bounds__(kBlock) k_primal_sell(DevLP L) {
     const int r = L.sT.rows[(size_t)sl * 32 + lane];
     if (!fp64) {
       const float a = sell_sum(L.sT, L.y32, sl, lane);
-      if (r >= 0) L.gsum32[r] = a;
+      if (EPI && r >= 0) epi.load(r);
+      if (r >= 0) {
+        if (EPI) epi.row(r, (double)a);
+        else L.gsum32[r] = a;
+      }
     } else {
       const double a = sell_sum(L.sT, L.y, sl, lane);
-      if (r >= 0) L.gsum[r] = a;
+      if (EPI && r >= 0) epi.load(r);
+      if (r >= 0) {
+        if (EPI) epi.row(r, a);
+        else L.gsum[r] = a;
+      }
     }
     return;
   }
   const int i = ((int)blockIdx.x - nsb) * kBlock + (int)threadIdx.x;
   if (i >= L.pT.nlong) return;
-  const double s = chunk_total(L.pT, i);
   const int r = L.pT.long_rows[i];
-  if (!fp64) L.gsum32[r] = (float)s;
+  if (EPI) epi.load(r);
+  const double s = chunk_total(L.pT, i);
+  if (EPI) epi.row(r, fp64 ? s : (double)(float)s);
+  else if (!fp64) L.gsum32[r] = (float)s;
   else L.gsum[r] = s;
 }
 
@@ -374,6 +391,69 @@ __global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_dual(DevLP L, int j)
     spmv_run<float>(bp, L.rp, L.col, L.vs32, L.xt32, L.pA, smem, w);
   }
   if (CHECK) block_store<2>(epi.acc, L.partD, L.pA);
+}
+
+// Dual step of a plain iteration of one LP whose A has chunked long rows,
+// in two launches: k_dual_fused runs the chunk warps of the long rows and
+// the other rows on the sliced ELL copy of A (one warp per slice of 32 rows,
+// the row's update in the lane that summed it: no shared memory, so the
+// chunk warps' gathers keep the whole L1), interleaved evenly in one grid
+// (block b is a slice block when floor((b + 1) ns / nb) > floor(b ns / nb)),
+// so that warps streaming the long rows and warps running the short rows'
+// FP64 updates share every SM; k_dual_long then adds each long row's chunk
+// sums and runs its update.  Check iterations keep the chunk launch +
+// k_dual form (its block partials feed the check).
+template <int PREC>
+__global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_dual_fused(DevLP L, int j) {
+  const int ns = (L.sA.nslice + kBlock / 32 - 1) / (kBlock / 32);
+  const int nb = ns + L.pA.nchunkblk;
+  const int b = (int)blockIdx.x;
+  const int sb = (int)((int64_t)b * ns / nb);  // slice blocks before this one
+  const bool slices = (int64_t)(b + 1) * ns / nb > sb;
+  const Ctrl* ctrl = L.ctrl;
+  if (ctrl->done) return;
+  const bool fp64 = phase64(ctrl, PREC);
+  if (!slices) {
+    if (fp64) chunk_warp<double>(L.col, L.vs, L.xt, L.pA, b - sb);
+    else chunk_warp<float>(L.col, L.vs32, L.xt32, L.pA, b - sb);
+    return;
+  }
+  const int sl = sb * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (sl >= L.sA.nslice) return;
+  const int r = L.sA.rows[(size_t)sl * 32 + lane];
+  DualEpi<false> epi{L, ctrl->s_step, L.coef[2 * j], L.coef[2 * j + 1], fp64, ctrl->algo == SCUC_ALGO_PDHG_AVG,
+                     {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
+  if (!fp64) {
+    const float a = sell_sum(L.sA, L.xt32, sl, lane);
+    if (r >= 0) {
+      epi.load(r);
+      epi.row(r, (double)a);
+    }
+  } else {
+    const double a = sell_sum(L.sA, L.xt, sl, lane);
+    if (r >= 0) {
+      epi.load(r);
+      epi.row(r, a);
+    }
+  }
+}
+
+// The long rows' updates after k_dual_fused: one thread per long row adds
+// the row's chunk sums in chunk order (as the main launch's long-row blocks
+// do), in blocks of 64 threads so that the few long rows spread over many
+// SMs (the launch is a chain of dependent loads, not a stream).
+template <int PREC>
+__global__ void __launch_bounds__(64) k_dual_long(DevLP L, int j) {
+  const Partition& P = L.pA;
+  const int li = (int)blockIdx.x * 64 + (int)threadIdx.x;
+  const int r = li < P.nlong ? P.long_rows[li] : -1;
+  const Ctrl* ctrl = L.ctrl;
+  if (ctrl->done || r < 0) return;
+  DualEpi<false> epi{L, ctrl->s_step, L.coef[2 * j], L.coef[2 * j + 1], phase64(ctrl, PREC),
+                     ctrl->algo == SCUC_ALGO_PDHG_AVG, {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
+  epi.load(r);
+  const double t = chunk_total(P, li);
+  epi.row(r, epi.fp64 ? t : (double)(float)t);
 }
 
 // ---------------------------------------------------------------------------

@@ -198,10 +198,13 @@ __device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT
 // bound: eight accumulators cost seven combining adds per 16 products, 20%
 // of the dual step); then a fixed warp tree; the sum goes to part.cpart[w]
 // in FP64.
+// cb: the block's index among the chunk blocks (blockIdx.x unless a launch
+// interleaves them with other work).
 template <typename VT>
 __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT* __restrict__ val,
-                                           const VT* __restrict__ x, const Partition& part) {
-  const int w = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+                                           const VT* __restrict__ x, const Partition& part,
+                                           int cb = -1) {
+  const int w = (cb < 0 ? (int)blockIdx.x : cb) * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= part.nchunk) return;
   const int2 c = part.chunks[w];
   VT s = sizeof(VT) == 4 ? batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32)
@@ -241,10 +244,12 @@ struct BlockPlan {
 
 // WITH_ER: also load the epilogue row of each thread (not needed when the
 // group leaders store their sums directly).
+// b: the block's index among the partition's main blocks (blockIdx.x
+// unless a launch interleaves them with other work).
 template <bool WITH_ER = true>
-__device__ __forceinline__ BlockPlan spmv_plan(const Partition& part) {
+__device__ __forceinline__ BlockPlan spmv_plan(const Partition& part, int b) {
   BlockPlan bp;
-  const int b = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int nlist = part.cls_blk[4];
   bp.er = -1;
   bp.li = -1;
@@ -277,6 +282,11 @@ __device__ __forceinline__ BlockPlan spmv_plan(const Partition& part) {
     }
   }
   return bp;
+}
+
+template <bool WITH_ER = true>
+__device__ __forceinline__ BlockPlan spmv_plan(const Partition& part) {
+  return spmv_plan<WITH_ER>(part, (int)blockIdx.x);
 }
 
 // Runs the SpMV of the block planned in bp; calls epi.row(r, acc) once per

@@ -117,6 +117,75 @@ def test_spmv_layouts_agree(P, case):
         assert oracle.kkt(d, r["x"], r["y"], r["z"])["kkt"] <= 1e-4 * 1.0001
 
 
+def _same_log(la, lb):
+    """Check logs equal entry by entry, bit for bit (NaN equal to NaN)."""
+    assert len(la) == len(lb)
+    for ea, eb in zip(la, lb):
+        assert ea.keys() == eb.keys()
+        for k in ea:
+            assert np.array_equal(np.float64(ea[k]), np.float64(eb[k]), equal_nan=True), (k, ea, eb)
+
+
+FUSE_CASES = [
+    (300, 200, 0.02, 1, 3, 2, "GLER"),       # sliced ELL primal step, no chunked rows
+    (513, 1025, 0.01, 3, 2, 0, "LR"),        # rows of 1,025 entries: 3 chunks each
+    (5000, 40, 0.002, 4, 0, 1, "GL"),        # a column of 5,000 entries (chunked primal)
+    (2000, 3000, 0.003, 7, 20, 3, "GLER"),   # 20 rows of 6 chunks, 3 columns of 4 chunks
+]
+
+
+@pytest.mark.parametrize("case", FUSE_CASES)
+@pytest.mark.parametrize("algo", ["hpr", "pdhg_avg"])
+def test_fused_steps_agree(P, case, algo):
+    """Plain iterations with the updates fused into the products' launches
+    (the default) against separate launches on the CSR partition
+    (split_steps = 1), through the solve graph and period by period.  With
+    no row of A above 512 entries only the primal update moves (same sums):
+    bit-identical iterates, logs and outputs.  Otherwise the dual step sums
+    A's short rows on its sliced ELL copy, in row order: FP64 solves take
+    the same restart decisions at every check with iterates equal to
+    rounding, and FP32-matvec solves reach the tolerance under the oracle's
+    KKT evaluation."""
+    m, n, dens, seed, lr, lc, sen = case
+    d = random_lp(m, n, density=dens, seed=seed, long_rows=lr, long_cols=lc, senses=sen)
+    lp = P.LP(d)
+    chunked_rows = max(np.diff(d["row_ptr"])) > 512
+    for graph in (1, 0):
+        kw = dict(tol=1e-7, max_iter=4096, check_every=64, algo=algo, precision="fp64", use_graph=graph)
+        a, b = lp.solve(split_steps=0, **kw), lp.solve(split_steps=1, **kw)
+        assert a["info"]["iters"] == b["info"]["iters"] and a["info"]["status"] == b["info"]["status"]
+        if not chunked_rows:
+            _same_log(a["log"], b["log"])
+            for k in ("x", "y", "z"):
+                assert np.array_equal(a[k], b[k]), (graph, k)
+        else:
+            _compare_logs(a["log"], b["log"], sigma_rtol=1e-7)
+            assert _rel(a["x"], b["x"]) < 1e-8 and _rel(a["y"], b["y"]) < 1e-8
+        kw.update(precision="mixed", tol=1e-4, max_iter=20480)
+        a, b = lp.solve(split_steps=0, **kw), lp.solve(split_steps=1, **kw)
+        if not chunked_rows:
+            _same_log(a["log"], b["log"])
+            assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["y"], b["y"])
+        for r in (a, b):
+            assert r["info"]["status"] == 0
+            assert oracle.kkt(d, r["x"], r["y"], r["z"])["kkt"] <= 1e-4 * 1.0001
+
+
+def test_fused_steps_scuc2k(P):
+    """The same on the 2,000-bus relaxation (dense PTDF and N-1 rows chunked,
+    sliced ELL copies of A and A^T), mixed precision to 1e-4 as the
+    benchmark runs it: both points certified by the oracle, objectives
+    within the tolerance's reach of each other."""
+    inst = make_preset("scuc2k")
+    lp = P.LP(inst)
+    a = lp.solve(tol=1e-4, precision="mixed")
+    b = lp.solve(tol=1e-4, precision="mixed", split_steps=1)
+    for r in (a, b):
+        assert r["info"]["status"] == 0
+        assert oracle.kkt(inst, r["x"], r["y"], r["z"])["kkt"] <= 1e-4 * 1.0001
+    assert abs(a["info"]["pobj"] - b["info"]["pobj"]) <= 1e-3 * abs(b["info"]["pobj"])
+
+
 def test_solve_parity_scuc14(P):
     inst = make_preset("scuc14")
     kw = dict(tol=1e-4, max_iter=100000)
