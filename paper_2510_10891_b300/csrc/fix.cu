@@ -92,6 +92,43 @@ __device__ __forceinline__ double lanes_total(double v) {
 
 __device__ __forceinline__ int lanes_count(int c) { return __reduce_add_sync(0xffffffffu, c); }
 
+// Sign and infinity tests on the bit pattern (integer pipe; B300's FP64 pipe
+// bounds these kernels).  pos(a) == (a > 0) and inf(a) == isinf(a) for
+// every non-NaN double (NaN values are rejected when an LP is created).
+__device__ __forceinline__ bool pos(double a) { return __double_as_longlong(a) > 0; }
+__device__ __forceinline__ bool inf(double a) {
+  return ((unsigned long long)__double_as_longlong(a) << 1) == 0xFFE0000000000000ull;
+}
+
+// Rounding margin of the row-level skip of k_col_propagate (far above the
+// few units of 2^-53 that the candidate's three roundings can cost).
+constexpr double kSkipRel = 1e-13;
+
+// Safe slack of one side of a row for that skip: a candidate bound from
+// this side can tighten column j (coefficient a, bounds [l, u]) only if the
+// slack (hi - min activity, or max activity - lo) is below |a| (u - l)
+// exactly; slack_safe is the computed slack less a margin that covers the
+// rounding of the candidate's computation, so slack_safe >= |a| c_j (c_j,
+// column_skip_range below) proves that the computed candidate cannot move
+// the bound.  +inf: the side implies no bound (infinite row bound, the
+// other activity within the bound, or two or more infinite contributions);
+// -inf: exactly one infinite contribution (only its column gets a bound;
+// never skipped).
+__device__ __forceinline__ double slack_safe(double bound, double act, int cinf, bool active) {
+  if (!active || cinf >= 2) return INFINITY;
+  if (cinf == 1) return -INFINITY;
+  const double d = __dsub_rn(bound, act);
+  return __dsub_rn(d, __dadd_rn(kSkipRel * (fabs(bound) + fabs(act) + fabs(d)), 1e-300));
+}
+
+// c_j of the skip test: (u - l) and the size of the bounds, inflated by the
+// margin; +inf for a column with an infinite bound (never skipped).
+__device__ __forceinline__ double column_skip_range(double l, double u) {
+  if (inf(l) || inf(u)) return INFINITY;
+  return __dadd_rn(__dmul_rn(__dsub_rn(u, l), 1.0 + kSkipRel),
+                   __dadd_rn(kSkipRel * (fabs(l) + fabs(u)), 1e-300));
+}
+
 // Activity range of each row over the current bounds: finite parts in the
 // lane order above, plus the number of infinite contributions (warp per row).
 // After the first pass a row is recomputed only when one of its columns
@@ -102,7 +139,9 @@ __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict
                                                            const double* __restrict__ xl,
                                                            const double* __restrict__ xu, double* __restrict__ mn,
                                                            double* __restrict__ mx, int* __restrict__ cmn,
-                                                           int* __restrict__ cmx, const uint8_t* __restrict__ chg,
+                                                           int* __restrict__ cmx, const double* __restrict__ lo,
+                                                           const double* __restrict__ hi, double2* __restrict__ slk,
+                                                           const uint8_t* __restrict__ chg,
                                                            uint8_t* __restrict__ dirty, int first) {
   const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= m) return;
@@ -120,11 +159,12 @@ __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict
   for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
     const double a = val[e];
     const int j = col[e];
-    const double lmin = a > 0.0 ? xl[j] : xu[j];
-    const double lmax = a > 0.0 ? xu[j] : xl[j];
-    if (isinf(lmin)) c_mn++;
+    const bool ap = pos(a);
+    const double lmin = ap ? xl[j] : xu[j];
+    const double lmax = ap ? xu[j] : xl[j];
+    if (inf(lmin)) c_mn++;
     else a_mn = __dadd_rn(a_mn, __dmul_rn(a, lmin));
-    if (isinf(lmax)) c_mx++;
+    if (inf(lmax)) c_mx++;
     else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
   }
   a_mn = lanes_total(a_mn);
@@ -136,6 +176,11 @@ __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict
     mx[i] = a_mx;
     cmn[i] = c_mn;
     cmx[i] = c_mx;
+    const double hii = hi[i], loi = lo[i];
+    // the same side tests as k_col_propagate's
+    const bool hi_act = !inf(hii) && !(c_mx == 0 && a_mx <= hii);
+    const bool lo_act = !inf(loi) && !(c_mn == 0 && a_mn >= loi);
+    slk[i] = make_double2(slack_safe(hii, a_mn, c_mn, hi_act), slack_safe(a_mx, loi, c_mx, lo_act));
   }
 }
 
@@ -157,6 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
                                                             const double* __restrict__ mx,
                                                             const int* __restrict__ cmn,
                                                             const int* __restrict__ cmx,
+                                                            const double2* __restrict__ slk,
                                                             const uint8_t* __restrict__ is_int,
                                                             double* __restrict__ xl, double* __restrict__ xu,
                                                             int* __restrict__ flags,
@@ -173,12 +219,24 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
     if (!any) return;  // chg[j] stays 0
   }
   const double oxl = xl[j], oxu = xu[j];
+  const double cj = column_skip_range(oxl, oxu);
   double nlo = oxl, nhi = oxu;
   for (int e = rpt[j] + lane; e < rpt[j + 1]; e += 32) {
     const int i = colt[e];
     const double a = valt[e];
-    const double lmin = a > 0.0 ? oxl : oxu;
-    const double lmax = a > 0.0 ? oxu : oxl;
+    // Row-level skip: a side whose safe slack is at least |a| c_j gives a
+    // candidate that cannot move column j's bound (for a > 0 on the hi side
+    // the computed b = (hi - (mn - a l)) / a is then >= u, for a < 0 it is
+    // <= l; likewise on the lo side), so its computation is left out and
+    // the bounds are exactly those of the full computation.  Rows that
+    // cannot bind (most dense network rows) take only this test.
+    const double2 sk = slk[i];
+    const double need = __dmul_rn(fabs(a), cj);
+    const bool hi_skip = sk.x >= need, lo_skip = sk.y >= need;
+    if (hi_skip && lo_skip) continue;
+    const bool ap = pos(a);
+    const double lmin = ap ? oxl : oxu;
+    const double lmax = ap ? oxu : oxl;
     const double hii = hi[i], loi = lo[i], mni = mn[i], mxi = mx[i];
     const int cmni = cmn[i], cmxi = cmx[i];
     // A candidate b = q / a replaces the lane's running bound only if it is
@@ -188,28 +246,28 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
     // underflows), so a q beyond it by more than 1e-15 of its size plus
     // 1e-300 cannot tighten the bound: the (slow) FP64 division is skipped
     // and the result is unchanged.
-    if (isfinite(hii) && !(cmxi == 0 && mxi <= hii)) {  // a x_j <= hi - (min activity of the rest)
-      const bool ok = isinf(lmin) ? (cmni == 1) : (cmni == 0);
+    if (!hi_skip && !inf(hii) && !(cmxi == 0 && mxi <= hii)) {  // a x_j <= hi - (min activity of the rest)
+      const bool ok = inf(lmin) ? (cmni == 1) : (cmni == 0);
       if (ok) {
-        const double rest = isinf(lmin) ? mni : __dsub_rn(mni, __dmul_rn(a, lmin));
+        const double rest = inf(lmin) ? mni : __dsub_rn(mni, __dmul_rn(a, lmin));
         const double q = __dsub_rn(hii, rest);
-        const double p = __dmul_rn(a > 0.0 ? nhi : nlo, a);  // b < nhi (a > 0) or b > nlo (a < 0) needs q < p
+        const double p = __dmul_rn(ap ? nhi : nlo, a);  // b < nhi (a > 0) or b > nlo (a < 0) needs q < p
         if (!(q > p + 1e-15 * fabs(p) + 1e-300)) {
           const double b = __ddiv_rn(q, a);
-          if (a > 0.0) { if (b < nhi) nhi = b; }
+          if (ap) { if (b < nhi) nhi = b; }
           else { if (b > nlo) nlo = b; }
         }
       }
     }
-    if (isfinite(loi) && !(cmni == 0 && mni >= loi)) {  // a x_j >= lo - (max activity of the rest)
-      const bool ok = isinf(lmax) ? (cmxi == 1) : (cmxi == 0);
+    if (!lo_skip && !inf(loi) && !(cmni == 0 && mni >= loi)) {  // a x_j >= lo - (max activity of the rest)
+      const bool ok = inf(lmax) ? (cmxi == 1) : (cmxi == 0);
       if (ok) {
-        const double rest = isinf(lmax) ? mxi : __dsub_rn(mxi, __dmul_rn(a, lmax));
+        const double rest = inf(lmax) ? mxi : __dsub_rn(mxi, __dmul_rn(a, lmax));
         const double q = __dsub_rn(loi, rest);
-        const double p = __dmul_rn(a > 0.0 ? nlo : nhi, a);  // b > nlo (a > 0) or b < nhi (a < 0) needs q > p
+        const double p = __dmul_rn(ap ? nlo : nhi, a);  // b > nlo (a > 0) or b < nhi (a < 0) needs q > p
         if (!(q < p - 1e-15 * fabs(p) - 1e-300)) {
           const double b = __ddiv_rn(q, a);
-          if (a > 0.0) { if (b > nlo) nlo = b; }
+          if (ap) { if (b > nlo) nlo = b; }
           else { if (b < nhi) nhi = b; }
         }
       }
@@ -265,11 +323,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce_rows(const int* __restrict_
       shift = __dadd_rn(shift, __dmul_rn(a, l));
     } else {
       kept++;
-      const double lmin = a > 0.0 ? l : u;
-      const double lmax = a > 0.0 ? u : l;
-      if (isinf(lmin)) c_mn++;
+      const bool ap = pos(a);
+      const double lmin = ap ? l : u;
+      const double lmax = ap ? u : l;
+      if (inf(lmin)) c_mn++;
       else a_mn = __dadd_rn(a_mn, __dmul_rn(a, lmin));
-      if (isinf(lmax)) c_mx++;
+      if (inf(lmax)) c_mx++;
       else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
     }
   }
@@ -502,6 +561,8 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
   double *mn = nullptr, *mx = nullptr;
   int *cmn = nullptr, *cmx = nullptr;
   uint8_t *chg = nullptr, *dirty = nullptr;
+  double2* slk = nullptr;
+  SCUC_TRY(talloc(&slk, m));
   SCUC_TRY(talloc(&mn, m));
   SCUC_TRY(talloc(&mx, m));
   SCUC_TRY(talloc(&cmn, m));
@@ -514,10 +575,11 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     SCUC_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));  // changed; flags[1] (infeasible) persists
     const int first = pass == 0 ? 1 : 0;
     if (m)
-      k_row_activity<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx, chg, dirty, first);
+      k_row_activity<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx, lo, hi, slk, chg,
+                                                    dirty, first);
     if (n)
-      k_col_propagate<<<grid_w(n), kThreads, 0, s>>>(rpt, colt, valt, n, lo, hi, mn, mx, cmn, cmx, isint, xl, xu,
-                                                   flags, dirty, chg, first);
+      k_col_propagate<<<grid_w(n), kThreads, 0, s>>>(rpt, colt, valt, n, lo, hi, mn, mx, cmn, cmx, slk, isint, xl,
+                                                   xu, flags, dirty, chg, first);
     SCUC_CUDA(cudaGetLastError());
     SCUC_CUDA(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaStreamSynchronize(s));

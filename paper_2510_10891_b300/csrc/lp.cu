@@ -856,7 +856,7 @@ int Handle::build_solve_graph(int check_every, int phase64) {
 }
 
 int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double* y0_in, double* xo,
-                  double* yo, double* zo, scuc_solve_info* info, double reject_kkt) {
+                  double* yo, double* zo, scuc_solve_info* info, double reject_kkt, bool keep_scaling) {
   using clk = std::chrono::steady_clock;
   if (!(p.tol >= 0.0) || p.check_every < 1 || p.max_iter < 1 || !(p.sigma0 > 0.0) ||
       (p.precision != SCUC_FP64 && p.precision != SCUC_MIXED) || p.power_max_iter < 1 ||
@@ -901,7 +901,12 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
     std::vector<int>().swap(rpt_plan);
     std::vector<int>().swap(rp_plan);
   }
-  SCUC_TRY(setup_scaling(p.use_scaling, mixed));
+  const int scale_key = p.use_scaling + (mixed ? 256 : 0);
+  if (!(keep_scaling && scaled_for == scale_key)) {
+    scaled_for = -1;
+    SCUC_TRY(setup_scaling(p.use_scaling, mixed));
+    scaled_for = scale_key;
+  }
   double lambda = p.lambda_in;
   int piters = 0;
   if (!(lambda > 0.0)) {

@@ -122,8 +122,14 @@ struct Handle {
   bool detect = false;       // infeasibility detection in the current solve
   int launch_period(int check_every, bool profile, bool fp64);
   int build_solve_graph(int check_every, int phase64);
+  // keep_scaling: the caller has changed nothing since this handle's last
+  // solve, so its scaled data (set up for the same use_scaling and
+  // precision) is reused instead of recomputed (the warm-start path's
+  // solves after its cold reference period)
   int solve(const scuc_solve_params& p, const double* x0, const double* y0, double* xo,
-            double* yo, double* zo, scuc_solve_info* info, double reject_kkt = 0.0);
+            double* yo, double* zo, scuc_solve_info* info, double reject_kkt = 0.0,
+            bool keep_scaling = false);
+  int scaled_for = -1;  // use_scaling + 256 * (FP32 copies) of the scaled data; -1: none
   int* pt_flag = nullptr;  // index checks of scuc_ws_assemble / scuc_ws_targets
   int matvec(int transpose, const double* in, double* out);
   int kkt_noalloc(const double* x, const double* y, const double* z, double* out);

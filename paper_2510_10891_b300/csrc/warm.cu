@@ -277,7 +277,8 @@ int scuc_lp_solve_warm(scuc_lp* lp, const scuc_solve_params* p, const double* x0
   }
   if (wp.warm_max_iter > 0) pw.max_iter = std::min<int64_t>(p->max_iter, wp.warm_max_iter);
   scuc_solve_info iw;
-  SCUC_TRY(h.solve(pw, x0, y0, x_out, y_out, z_out, &iw, wp.first_check ? ref : 0.0));
+  // the reference period left the scaled data of this same model in place
+  SCUC_TRY(h.solve(pw, x0, y0, x_out, y_out, z_out, &iw, wp.first_check ? ref : 0.0, ir.iters > 0));
   auto add = [](scuc_solve_info& a, const scuc_solve_info& b) {
     a.iters += b.iters;
     a.iters_fp32 += b.iters_fp32;
@@ -309,7 +310,7 @@ int scuc_lp_solve_warm(scuc_lp* lp, const scuc_solve_params* p, const double* x0
   scuc_solve_params pc = *p;
   if (!(pc.lambda_in > 0.0)) pc.lambda_in = iw.lambda;
   scuc_solve_info ic;
-  SCUC_TRY(h.solve(pc, nullptr, nullptr, x_out, y_out, z_out, &ic));
+  SCUC_TRY(h.solve(pc, nullptr, nullptr, x_out, y_out, z_out, &ic, 0.0, true));
   if (info) {
     scuc_solve_info out = ic;
     if (ic.status == SCUC_ST_OPTIMAL) out.status = SCUC_ST_FALLBACK_COLD;

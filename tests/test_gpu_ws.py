@@ -325,6 +325,26 @@ def test_first_check_rejection_is_consistent(P, instances):
     assert r2["info"]["iters"] == info["iters"] - 64
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_warm_solve_reuses_the_reference_period_scaling(P, instances, precision):
+    """The warm solve after the cold reference period keeps the scaled data
+    that period set up (nothing changed in between): its result is
+    bit-identical to a warm solve given the same reference KKT, which sets
+    the scaling (and lambda) up afresh."""
+    inst = instances["batch0"]
+    lp = P.LP(inst)
+    cold = lp.solve(tol=1e-4, precision=precision)
+    x0 = 0.9 * cold["x"] + 0.1 * np.clip(0.0, inst.xl, inst.xu)
+    r1 = lp.solve_warm(x0, tol=1e-4, precision=precision)
+    kc = r1["info"]["cold_first_kkt"]
+    r2 = lp.solve_warm(x0, cold_first_kkt=kc, tol=1e-4, precision=precision)
+    assert r1["info"]["ref_iters"] == 64 and r2["info"]["ref_iters"] == 0
+    assert r1["info"]["status"] == r2["info"]["status"]
+    assert r1["info"]["iters"] - 64 == r2["info"]["iters"]
+    for k in ("x", "y", "z"):
+        np.testing.assert_array_equal(r1[k], r2[k])
+
+
 def test_warm_solve_matches_oracle_warm_solve(P, W, torch_cuda, instances):
     torch = torch_cuda
     from scuc_gen.features import ws_layout_arrays
