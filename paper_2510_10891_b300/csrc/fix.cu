@@ -3,12 +3,13 @@
 // LP (fixed columns folded into the row bounds, redundant rows dropped).
 //
 // Row activities, candidate bounds and the folded row bounds use explicitly
-// rounded FP64 operations (no contraction); a row's sums are taken by one
-// warp in a fixed order (entry q of the row into lane q mod 32, each lane in
-// entry order, lanes combined by halving 16, 8, 4, 2, 1), so propagated
-// bounds and reduced-LP data are bit-identical run to run and to a CPU loop
-// that takes the same order; min/max over a column's candidates is
-// order-free.  Every fixing and presolve decision is made from those values.
+// rounded FP64 operations (no contraction); a row of at most 32 entries is
+// summed by one thread in entry order, a longer row by one warp in a fixed
+// order (entry q of the row into lane q mod 32, each lane in entry order,
+// lanes combined by halving 16, 8, 4, 2, 1), so propagated bounds and
+// reduced-LP data are bit-identical run to run; min/max over a column's
+// candidates is order-free.  Every fixing and presolve decision is made
+// from those values.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -129,13 +130,58 @@ __device__ __forceinline__ double column_skip_range(double l, double u) {
                    __dadd_rn(kSkipRel * (fabs(l) + fabs(u)), 1e-300));
 }
 
-// Activity range of each row over the current bounds: finite parts in the
-// lane order above, plus the number of infinite contributions (warp per row).
-// After the first pass a row is recomputed only when one of its columns
-// changed bounds in the previous pass (chg); otherwise its activity range is
-// the one already stored.  dirty[i] records whether row i was recomputed.
-__global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict__ rp, const int* __restrict__ col,
-                                                           const double* __restrict__ val, int m,
+// Rows and columns of at most kShortItem entries (all but the dense network
+// rows and the columns in them) take one thread each, their sums in entry
+// order; longer ones one warp each (entry q in lane q mod 32, lanes combined
+// by halving).  On B300 a warp instruction on the FP64 pipe costs its
+// issue slot whatever the active lanes, so a warp per short item would pay
+// the warp's reductions and its lane-0 tail for a handful of entries.
+constexpr int kShortItem = 32;
+
+// Item k of list (thread or warp per item): list index, lane, entry stride.
+template <bool WARP>
+struct Item {
+  int k, lane;
+  static constexpr int step = WARP ? 32 : 1;
+  __device__ Item() {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    k = WARP ? (int)(t >> 5) : (int)t;
+    lane = WARP ? (int)(threadIdx.x & 31) : 0;
+  }
+};
+
+// whether any of entries [e0, e1) has flag[idx[e]] set (the whole warp's
+// answer for WARP)
+template <bool WARP>
+__device__ __forceinline__ bool any_flagged(const int* __restrict__ idx, const uint8_t* __restrict__ flag, int e0,
+                                            int e1, int lane) {
+  bool any = false;
+  if (WARP) {
+    for (int b = e0; b < e1 && !any; b += 32) {
+      const int e = b + lane;
+      any = __any_sync(0xffffffffu, e < e1 && flag[idx[e]]);
+    }
+  } else {
+    for (int e = e0; e < e1 && !any; e++) any = flag[idx[e]] != 0;
+  }
+  return any;
+}
+
+template <bool WARP>
+__device__ __forceinline__ double item_total(double v) { return WARP ? lanes_total(v) : v; }
+template <bool WARP>
+__device__ __forceinline__ int item_count(int c) { return WARP ? lanes_count(c) : c; }
+
+// Activity range of each row of list over the current bounds: finite parts
+// (in the order above) plus the number of infinite contributions, and the
+// rows' safe slacks for k_col_propagate's skip.  After the first pass a row
+// is recomputed only when one of its columns changed bounds in the previous
+// pass (chg); otherwise its activity range is the one already stored.
+// dirty[i] records whether row i was recomputed.
+template <bool WARP>
+__global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict__ list, int cnt,
+                                                           const int* __restrict__ rp, const int* __restrict__ col,
+                                                           const double* __restrict__ val,
                                                            const double* __restrict__ xl,
                                                            const double* __restrict__ xu, double* __restrict__ mn,
                                                            double* __restrict__ mx, int* __restrict__ cmn,
@@ -143,20 +189,18 @@ __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict
                                                            const double* __restrict__ hi, double2* __restrict__ slk,
                                                            const uint8_t* __restrict__ chg,
                                                            uint8_t* __restrict__ dirty, int first) {
-  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (i >= m) return;
+  const Item<WARP> it;
+  if (it.k >= cnt) return;
+  const int i = list[it.k], lane = it.lane;
+  const int e0 = rp[i], e1 = rp[i + 1];
   if (!first) {
-    bool any = false;
-    for (int e0 = rp[i]; e0 < rp[i + 1] && !any; e0 += 32) {
-      const int e = e0 + lane;
-      any = __any_sync(0xffffffffu, e < rp[i + 1] && chg[col[e]]);
-    }
+    const bool any = any_flagged<WARP>(col, chg, e0, e1, lane);
     if (lane == 0) dirty[i] = any ? 1 : 0;
     if (!any) return;
   }
   double a_mn = 0.0, a_mx = 0.0;
   int c_mn = 0, c_mx = 0;
-  for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+  for (int e = e0 + lane; e < e1; e += it.step) {
     const double a = val[e];
     const int j = col[e];
     const bool ap = pos(a);
@@ -167,10 +211,10 @@ __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict
     if (inf(lmax)) c_mx++;
     else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
   }
-  a_mn = lanes_total(a_mn);
-  a_mx = lanes_total(a_mx);
-  c_mn = lanes_count(c_mn);
-  c_mx = lanes_count(c_mx);
+  a_mn = item_total<WARP>(a_mn);
+  a_mx = item_total<WARP>(a_mx);
+  c_mn = item_count<WARP>(c_mn);
+  c_mx = item_count<WARP>(c_mx);
   if (lane == 0) {
     mn[i] = a_mn;
     mx[i] = a_mx;
@@ -184,18 +228,21 @@ __global__ void __launch_bounds__(kThreads) k_row_activity(const int* __restrict
   }
 }
 
-// One Jacobi pass for each column (warp per column over its A^T entries):
-// candidate bounds from every row that can bind, integer rounding,
-// acceptance thresholds.  Only column j's own bounds are read and written by
-// warp j; row activities come from the previous kernel, so the pass is
-// Jacobi.  A row whose maximum activity cannot exceed hi (minimum cannot
-// fall below lo) implies no bound from that side and is skipped.  After the
-// first pass a column whose own bounds did not change in the previous pass
-// (chg) and none of whose rows were recomputed (dirty) would repeat the
-// previous pass's candidates and decisions exactly, so it is skipped;
-// chg[j] then records whether column j changed in this pass.
-__global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restrict__ rpt, const int* __restrict__ colt,
-                                                            const double* __restrict__ valt, int n,
+// One Jacobi pass for each column of list (thread or warp per column, over
+// its A^T entries): candidate bounds from every row that can bind, integer
+// rounding, acceptance thresholds.  Only column j's own bounds are read and
+// written by its thread or warp; row activities come from the previous
+// kernel, so the pass is Jacobi.  A row whose maximum activity cannot
+// exceed hi (minimum cannot fall below lo) implies no bound from that side
+// and is skipped.  After the first pass a column whose own bounds did not
+// change in the previous pass (chg) and none of whose rows were recomputed
+// (dirty) would repeat the previous pass's candidates and decisions
+// exactly, so it is skipped; chg[j] then records whether column j changed in
+// this pass.
+template <bool WARP>
+__global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restrict__ list, int cnt,
+                                                            const int* __restrict__ rpt, const int* __restrict__ colt,
+                                                            const double* __restrict__ valt,
                                                             const double* __restrict__ lo,
                                                             const double* __restrict__ hi,
                                                             const double* __restrict__ mn,
@@ -208,20 +255,15 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
                                                             int* __restrict__ flags,
                                                             const uint8_t* __restrict__ dirty,
                                                             uint8_t* __restrict__ chg, int first) {
-  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (j >= n) return;
-  if (!first && !chg[j]) {
-    bool any = false;
-    for (int e0 = rpt[j]; e0 < rpt[j + 1] && !any; e0 += 32) {
-      const int e = e0 + lane;
-      any = __any_sync(0xffffffffu, e < rpt[j + 1] && dirty[colt[e]]);
-    }
-    if (!any) return;  // chg[j] stays 0
-  }
+  const Item<WARP> it;
+  if (it.k >= cnt) return;
+  const int j = list[it.k], lane = it.lane;
+  const int e0 = rpt[j], e1 = rpt[j + 1];
+  if (!first && !chg[j] && !any_flagged<WARP>(colt, dirty, e0, e1, lane)) return;  // chg[j] stays 0
   const double oxl = xl[j], oxu = xu[j];
   const double cj = column_skip_range(oxl, oxu);
   double nlo = oxl, nhi = oxu;
-  for (int e = rpt[j] + lane; e < rpt[j + 1]; e += 32) {
+  for (int e = e0 + lane; e < e1; e += it.step) {
     const int i = colt[e];
     const double a = valt[e];
     // Row-level skip: a side whose safe slack is at least |a| c_j gives a
@@ -239,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
     const double lmax = ap ? oxu : oxl;
     const double hii = hi[i], loi = lo[i], mni = mn[i], mxi = mx[i];
     const int cmni = cmn[i], cmxi = cmx[i];
-    // A candidate b = q / a replaces the lane's running bound only if it is
+    // A candidate b = q / a replaces the running bound only if it is
     // strictly tighter, and that needs q below (or above) the exact product
     // bound * a (rounding is monotone and the bound is representable).  The
     // rounded product is within 2^-53 of the exact one (plus 2^-1074 when it
@@ -273,23 +315,31 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
       }
     }
   }
+  if (WARP) {
+    // min/max are order-free; lanes that kept the column's own bounds leave
+    // nothing to combine, so the tree runs only when some lane moved one
+    const bool moved = __any_sync(0xffffffffu, __double_as_longlong(nlo) != __double_as_longlong(oxl) ||
+                                                   __double_as_longlong(nhi) != __double_as_longlong(oxu));
+    if (moved) {
 #pragma unroll
-  for (int w = 16; w > 0; w >>= 1) {
-    const double ol = __shfl_down_sync(0xffffffffu, nlo, w), oh = __shfl_down_sync(0xffffffffu, nhi, w);
-    if (ol > nlo) nlo = ol;
-    if (oh < nhi) nhi = oh;
+      for (int w = 16; w > 0; w >>= 1) {
+        const double ol = __shfl_down_sync(0xffffffffu, nlo, w), oh = __shfl_down_sync(0xffffffffu, nhi, w);
+        if (ol > nlo) nlo = ol;
+        if (oh < nhi) nhi = oh;
+      }
+    }
+    if (lane != 0) return;
   }
-  if (lane != 0) return;
   double l = nlo, u = nhi, nxl = oxl, nxu = oxu;
   int changed = 0;
   if (is_int[j]) {
-    if (isfinite(u)) u = floor(__dadd_rn(u, 1e-6));
-    if (isfinite(l)) l = ceil(__dsub_rn(l, 1e-6));
+    if (!inf(u)) u = floor(__dadd_rn(u, 1e-6));
+    if (!inf(l)) l = ceil(__dsub_rn(l, 1e-6));
     if (l > nxl) { nxl = l; changed = 1; }
     if (u < nxu) { nxu = u; changed = 1; }
   } else {
-    const double tl = 1e-9 * fmax(1.0, isfinite(oxl) ? fabs(oxl) : 1.0);
-    const double tu = 1e-9 * fmax(1.0, isfinite(oxu) ? fabs(oxu) : 1.0);
+    const double tl = 1e-9 * fmax(1.0, !inf(oxl) ? fabs(oxl) : 1.0);
+    const double tu = 1e-9 * fmax(1.0, !inf(oxu) ? fabs(oxu) : 1.0);
     if (l > __dadd_rn(oxl, tl)) { nxl = l; changed = 1; }
     if (u < __dsub_rn(oxu, tu)) { nxu = u; changed = 1; }
   }
@@ -302,21 +352,25 @@ __global__ void __launch_bounds__(kThreads) k_col_propagate(const int* __restric
   if (nxl > __dadd_rn(nxu, 1e-6)) atomicOr(flags + 1, 1);
 }
 
-// Reduced-LP rows (warp per row): fixed columns folded into the row bounds,
-// activity range over the free columns (lane order), redundancy test.
-__global__ void __launch_bounds__(kThreads) k_reduce_rows(const int* __restrict__ rp, const int* __restrict__ col,
-                                                          const double* __restrict__ val, int m,
+// Reduced-LP rows of list (thread or warp per row): fixed columns folded
+// into the row bounds, activity range over the free columns, redundancy
+// test.
+template <bool WARP>
+__global__ void __launch_bounds__(kThreads) k_reduce_rows(const int* __restrict__ list, int cnt,
+                                                          const int* __restrict__ rp, const int* __restrict__ col,
+                                                          const double* __restrict__ val,
                                                           const double* __restrict__ lo,
                                                           const double* __restrict__ hi,
                                                           const double* __restrict__ xl,
                                                           const double* __restrict__ xu, int* __restrict__ keep,
                                                           int* __restrict__ knz, double* __restrict__ lo_r,
                                                           double* __restrict__ hi_r, int* __restrict__ flags) {
-  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (i >= m) return;
+  const Item<WARP> it;
+  if (it.k >= cnt) return;
+  const int i = list[it.k], lane = it.lane;
   double shift = 0.0, a_mn = 0.0, a_mx = 0.0;
   int kept = 0, c_mn = 0, c_mx = 0;
-  for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+  for (int e = rp[i] + lane; e < rp[i + 1]; e += it.step) {
     const int j = col[e];
     const double a = val[e], l = xl[j], u = xu[j];
     if (l == u) {
@@ -332,12 +386,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce_rows(const int* __restrict_
       else a_mx = __dadd_rn(a_mx, __dmul_rn(a, lmax));
     }
   }
-  shift = lanes_total(shift);
-  a_mn = lanes_total(a_mn);
-  a_mx = lanes_total(a_mx);
-  kept = lanes_count(kept);
-  c_mn = lanes_count(c_mn);
-  c_mx = lanes_count(c_mx);
+  shift = item_total<WARP>(shift);
+  a_mn = item_total<WARP>(a_mn);
+  a_mx = item_total<WARP>(a_mx);
+  kept = item_count<WARP>(kept);
+  c_mn = item_count<WARP>(c_mn);
+  c_mx = item_count<WARP>(c_mx);
   if (lane != 0) return;
   const double l = __dsub_rn(lo[i], shift), u = __dsub_rn(hi[i], shift);
   lo_r[i] = l;
@@ -348,10 +402,25 @@ __global__ void __launch_bounds__(kThreads) k_reduce_rows(const int* __restrict_
     knz[i] = 0;
     return;
   }
-  const bool lo_red = !isfinite(l) || (c_mn == 0 && a_mn >= l);
-  const bool hi_red = !isfinite(u) || (c_mx == 0 && a_mx <= u);
+  const bool lo_red = inf(l) || (c_mn == 0 && a_mn >= l);
+  const bool hi_red = inf(u) || (c_mx == 0 && a_mx <= u);
   keep[i] = (lo_red && hi_red) ? 0 : 1;
   knz[i] = keep[i] ? kept : 0;
+}
+
+// items (rows of a CSR) of at most kShortItem entries first, then the
+// others, each group in index order: flag pass, then scatter by the scan
+__global__ void k_short_flag(const int* __restrict__ rp, int m, int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) flag[i] = rp[i + 1] - rp[i] <= kShortItem ? 1 : 0;
+}
+
+__global__ void k_split_list(int m, const int* __restrict__ flag, const int* __restrict__ pos, int nshort,
+                             int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  if (flag[i]) out[pos[i]] = i;
+  else out[nshort + (i - pos[i])] = i;
 }
 
 __global__ void k_col_keep(int n, const double* __restrict__ xl, const double* __restrict__ xu,
@@ -460,24 +529,74 @@ __global__ void k_scatter_cols(int n, const int* __restrict__ keepc, const int* 
 }
 
 // objective of the fixed columns (one block, fixed order)
-__global__ void __launch_bounds__(1024) k_fixed_obj(int n, const double* __restrict__ c,
-                                                    const double* __restrict__ xl,
-                                                    const double* __restrict__ xu, double* __restrict__ out) {
-  __shared__ double s_w[32];
+// objective of the fixed columns, sum_j c_j x_j over xl_j == xu_j: block b
+// sums columns [b * per, (b + 1) * per) (thread-strided, then a fixed warp
+// and block tree) into part[b]; k_sum_parts adds the blocks in order
+constexpr int kObjBlocks = 296;
+__global__ void __launch_bounds__(kThreads) k_fixed_obj(int n, const double* __restrict__ c,
+                                                        const double* __restrict__ xl,
+                                                        const double* __restrict__ xu, double* __restrict__ part) {
+  __shared__ double s_w[kThreads / 32];
+  const int per = (n + kObjBlocks - 1) / kObjBlocks;
+  const int j0 = (int)blockIdx.x * per, j1 = min(n, j0 + per);
   double s = 0.0;
-  for (int j = threadIdx.x; j < n; j += 1024)
+  for (int j = j0 + (int)threadIdx.x; j < j1; j += kThreads)
     if (xl[j] == xu[j]) s += c[j] * xl[j];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double r = 0.0;
-    for (int w = 0; w < 32; w++) r += s_w[w];
-    *out = r;
+    for (int w = 0; w < kThreads / 32; w++) r += s_w[w];
+    part[blockIdx.x] = r;
   }
 }
 
+__global__ void k_sum_parts(const double* __restrict__ part, int k, double* __restrict__ out) {
+  double r = 0.0;
+  for (int b = 0; b < k; b++) r += part[b];
+  *out = r;
+}
+
 }  // namespace
+
+int Handle::build_fix_lists() {
+  if (fix_lists) return SCUC_OK;
+  cudaStream_t s = work;
+  int* lists = nullptr;
+  SCUC_TRY(alloc(&lists, (size_t)m + n + 1));
+  void *fq = nullptr, *pq = nullptr;
+  SCUC_TRY(dev_alloc_bytes(&fq, ((size_t)std::max(m, n) + 1) * sizeof(int)));
+  struct Free {  // after the stream's work that uses them
+    cudaStream_t s;
+    void *a, *b;
+    ~Free() {
+      cudaStreamSynchronize(s);
+      if (a) dev_free(a);
+      if (b) dev_free(b);
+    }
+  } fr{s, fq, nullptr};
+  SCUC_TRY(dev_alloc_bytes(&pq, ((size_t)std::max(m, n) + 1) * sizeof(int)));
+  fr.b = pq;
+  int *flag = static_cast<int*>(fq), *pos = static_cast<int*>(pq);
+  int counts[2] = {0, 0};
+  for (int t = 0; t < 2; t++) {
+    const int k = t == 0 ? m : n;
+    const int* ptr = t == 0 ? rp : rpt;
+    if (k == 0) continue;
+    k_short_flag<<<grid1(k), kThreads, 0, s>>>(ptr, k, flag);
+    SCUC_TRY(exclusive_scan(flag, k, pos, s));
+    SCUC_CUDA(cudaMemcpyAsync(&counts[t], pos + k, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    k_split_list<<<grid1(k), kThreads, 0, s>>>(k, flag, pos, counts[t], lists + (t == 0 ? 0 : m));
+    SCUC_CUDA(cudaGetLastError());
+  }
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  fix_lists = lists;
+  fix_short_rows = counts[0];
+  fix_short_cols = counts[1];
+  return SCUC_OK;
+}
 
 int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, const double* x_in,
                               const scuc_fix_params& p, int8_t* fix_out_h, Handle** reduced,
@@ -498,6 +617,7 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     }
   }
   SCUC_TRY(enter());
+  SCUC_TRY(build_fix_lists());
   cudaStream_t s = work;
   std::vector<void*> tmp;
   auto talloc = [&](auto** ptr, size_t count) -> int {
@@ -571,15 +691,24 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
   SCUC_TRY(talloc(&dirty, m));
   int passes = 0, infeasible = 0;
   int hflags[2] = {0, 0};
+  const int *rows_s = fix_lists, *rows_l = fix_lists + fix_short_rows;
+  const int *cols_s = fix_lists + m, *cols_l = fix_lists + m + fix_short_cols;
+  const int nrs = fix_short_rows, nrl = m - fix_short_rows, ncs = fix_short_cols, ncl = n - fix_short_cols;
   for (int pass = 0; pass < p.max_passes; pass++) {
     SCUC_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));  // changed; flags[1] (infeasible) persists
     const int first = pass == 0 ? 1 : 0;
-    if (m)
-      k_row_activity<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, xl, xu, mn, mx, cmn, cmx, lo, hi, slk, chg,
-                                                    dirty, first);
-    if (n)
-      k_col_propagate<<<grid_w(n), kThreads, 0, s>>>(rpt, colt, valt, n, lo, hi, mn, mx, cmn, cmx, slk, isint, xl,
-                                                   xu, flags, dirty, chg, first);
+    if (nrl)
+      k_row_activity<true><<<grid_w(nrl), kThreads, 0, s>>>(rows_l, nrl, rp, col, val, xl, xu, mn, mx, cmn, cmx,
+                                                             lo, hi, slk, chg, dirty, first);
+    if (nrs)
+      k_row_activity<false><<<grid1(nrs), kThreads, 0, s>>>(rows_s, nrs, rp, col, val, xl, xu, mn, mx, cmn, cmx,
+                                                             lo, hi, slk, chg, dirty, first);
+    if (ncl)
+      k_col_propagate<true><<<grid_w(ncl), kThreads, 0, s>>>(cols_l, ncl, rpt, colt, valt, lo, hi, mn, mx, cmn,
+                                                              cmx, slk, isint, xl, xu, flags, dirty, chg, first);
+    if (ncs)
+      k_col_propagate<false><<<grid1(ncs), kThreads, 0, s>>>(cols_s, ncs, rpt, colt, valt, lo, hi, mn, mx, cmn,
+                                                              cmx, slk, isint, xl, xu, flags, dirty, chg, first);
     SCUC_CUDA(cudaGetLastError());
     SCUC_CUDA(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SCUC_CUDA(cudaStreamSynchronize(s));
@@ -610,11 +739,16 @@ int Handle::fix_and_propagate(const scuc_map& map, const uint8_t* is_int_h, cons
     SCUC_TRY(talloc(&offs, m + 1));
     SCUC_TRY(talloc(&lo_t, m));
     SCUC_TRY(talloc(&hi_t, m));
-    SCUC_TRY(talloc(&objc, 1));
-    if (m)
-      k_reduce_rows<<<grid_w(m), kThreads, 0, s>>>(rp, col, val, m, lo, hi, xl, xu, keep, knz, lo_t, hi_t, flags);
+    SCUC_TRY(talloc(&objc, 1 + kObjBlocks));
+    if (nrl)
+      k_reduce_rows<true><<<grid_w(nrl), kThreads, 0, s>>>(rows_l, nrl, rp, col, val, lo, hi, xl, xu, keep, knz,
+                                                            lo_t, hi_t, flags);
+    if (nrs)
+      k_reduce_rows<false><<<grid1(nrs), kThreads, 0, s>>>(rows_s, nrs, rp, col, val, lo, hi, xl, xu, keep, knz,
+                                                            lo_t, hi_t, flags);
     if (n) k_col_keep<<<grid1(n), kThreads, 0, s>>>(n, xl, xu, keepc);
-    k_fixed_obj<<<1, 1024, 0, s>>>(n, c, xl, xu, objc);
+    k_fixed_obj<<<kObjBlocks, kThreads, 0, s>>>(n, c, xl, xu, objc + 1);
+    k_sum_parts<<<1, 1, 0, s>>>(objc + 1, kObjBlocks, objc);
     SCUC_CUDA(cudaGetLastError());
     SCUC_TRY(exclusive_scan(keep, m, newrow, s));   // reduced row of each kept row; newrow[m] = rows kept
     SCUC_TRY(exclusive_scan(keepc, n, newcol, s));  // reduced column of each free column

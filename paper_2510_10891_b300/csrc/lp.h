@@ -131,6 +131,11 @@ struct Handle {
             bool keep_scaling = false);
   int scaled_for = -1;  // use_scaling + 256 * (FP32 copies) of the scaled data; -1: none
   int* pt_flag = nullptr;  // index checks of scuc_ws_assemble / scuc_ws_targets
+  // rows [0, m) then columns [m, m + n): short ones (<= 32 entries) first,
+  // each group in index order (built at the first fixing call)
+  int* fix_lists = nullptr;
+  int fix_short_rows = 0, fix_short_cols = 0;
+  int build_fix_lists();
   int matvec(int transpose, const double* in, double* out);
   int kkt_noalloc(const double* x, const double* y, const double* z, double* out);
   int fix_and_propagate(const scuc_map& map, const uint8_t* is_int, const double* x, const scuc_fix_params& p,
