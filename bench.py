@@ -47,14 +47,28 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def spmv_bytes(m, n, nnz_a, kind, prec):
+def spmv_bytes(m, n, nnz_a, kind, prec, lay=None):
     """Algorithmic bytes of one fused SpMV launch (each matrix entry and each
-    vector element touched once)."""
+    vector element touched once).  FP32 products read the matrix entries in
+    the storage scuc_lp_layout reports (lay): 6 bytes (value + 16-bit
+    offset) for entries of chunks and of a compressed sliced copy of A^T
+    (with a 16-byte record per column), 8 bytes (value + 32-bit index) for
+    the others; lay None: 8 bytes per entry and a 4-byte row pointer per
+    row."""
     vb = 8 if prec == "fp64" else 4
     if kind == "dual":   # A x_t, then y/y0/lo/hi in, y out (+ FP32 shadow of y)
-        return (vb + 4) * nnz_a + 4 * (m + 1) + vb * n + 32 * m + 8 * m + (4 * m if vb == 4 else 0)
+        mat = (vb + 4) * nnz_a + 4 * (m + 1)
+        if vb == 4 and lay:
+            mat -= 2 * lay["a_chunk16"]
+        return mat + vb * n + 32 * m + 8 * m + (4 * m if vb == 4 else 0)
     # primal: A^T y, then x/x0/c/xl/xu in, x and x_t out
-    return (vb + 4) * nnz_a + 4 * (n + 1) + vb * m + 40 * n + 8 * n + (8 * n if vb == 8 else 4 * n)
+    mat = (vb + 4) * nnz_a + 4 * (n + 1)
+    if vb == 4 and lay:
+        if lay["t_sell_compressed"]:
+            mat = 6 * nnz_a + 2 * lay["t_chunk32"] + 16 * n
+        else:
+            mat -= 2 * lay["t_chunk16"]
+    return mat + vb * m + 40 * n + 8 * n + (8 * n if vb == 8 else 4 * n)
 
 
 # sources the iteration SpMV kernels are built from (kernels and the
@@ -554,7 +568,7 @@ def main():
         lp = P.LP(make_preset(args.ncu_case))
         r = lp.solve(want=("x",), tol=0.0, max_iter=128, use_graph=0, precision=args.ncu_precision,
                      polish_stall=10 ** 6, polish_factor=0.0)
-        print("ncu case %s: %d iterations" % (args.ncu_case, r["info"]["iters"]))
+        print("ncu case %s: %d iterations; layout %s" % (args.ncu_case, r["info"]["iters"], json.dumps(lp.layout())))
         return 0
     if args.ncu_ws:
         import torch
@@ -678,7 +692,8 @@ def main():
                 a[0] += tt; a[1] += nn
     (dk, dp), (dms, dn) = max(agg.items(), key=lambda kv: kv[1][0])
     nnz_a = nnz
-    byts = spmv_bytes(m, n, nnz_a, dk, "fp64" if dp == "fp64" else "fp32")
+    lay = lp.layout()
+    byts = spmv_bytes(m, n, nnz_a, dk, "fp64" if dp == "fp64" else "fp32", lay)
     avg_ms = dms / max(dn, 1)
     achieved = byts / (avg_ms * 1e-3) / 1e9
     traffic, traffic_note = None, None
@@ -690,7 +705,8 @@ def main():
         if t.get("csrc_sha") == csrc_hash() and key in t.get("dram_bytes_per_launch", {}):
             # captured on the 6.5k-bus LP (the capture size rule), scaled to
             # this launch by the ratio of algorithmic bytes
-            scale = spmv_bytes(m, n, nnz, dk, dp) / spmv_bytes(t["m"], t["n"], t["nnz"], dk, dp)
+            scale = spmv_bytes(m, n, nnz, dk, dp, lay) / spmv_bytes(t["m"], t["n"], t["nnz"], dk, dp,
+                                                                     t.get("layout"))
             traffic = t["dram_bytes_per_launch"][key] * scale
             traffic_note = "ncu DRAM bytes of the %s launch on the %s LP x %.3f (algorithmic-bytes ratio)" % (
                 key, t["workload"], scale)
@@ -698,7 +714,8 @@ def main():
             "traffic": traffic, "traffic_source": traffic_note, "kernel": "%s (%s matvec)" % (STEP_KERNELS[dk], dp),
             "bytes_per_launch": byts, "avg_launch_ms": avg_ms, "launches": dn, "peak_source": peak_src,
             "all_kernels": {"%s_%s" % k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
-                                          "GBps": spmv_bytes(m, n, nnz_a, k[0], "fp64" if k[1] == "fp64" else "fp32")
+                                          "GBps": spmv_bytes(m, n, nnz_a, k[0], "fp64" if k[1] == "fp64" else "fp32",
+                                                             lay)
                                           / (v[0] / max(v[1], 1) * 1e-3) / 1e9 if v[1] else None}
                             for k, v in agg.items()}}
 

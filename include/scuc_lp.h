@@ -233,6 +233,30 @@ int scuc_lp_create_box(scuc_lp** out, int32_t m, int32_t n, int64_t nnz, const i
 /* Dimensions of a handle. */
 int scuc_lp_dims(const scuc_lp* lp, int32_t* m, int32_t* n, int64_t* nnz);
 
+/* Storage of the matrix entries that the FP32 iteration products (Eq. 9
+ * with FP32 matrix-vector products, Sec. 3.B) read, for byte accounting.
+ * Valid after the handle's first solve with FP32 products (0 before).
+ * out[8] (host):
+ *   0  entries of A's chunked rows read with 16-bit column offsets
+ *      (6 bytes each: FP32 value + offset from the chunk's first column)
+ *   1  entries of A's chunked rows read with 32-bit columns (8 bytes)
+ *   2  entries (incl. padding) of the sliced copy of A's other rows
+ *      (8 bytes each)
+ *   3  entries (incl. padding) of the sliced copy of A^T
+ *   4  1 if that copy stores 16-bit row offsets (6 bytes per entry and a
+ *      16-byte record per column), 0 if 32-bit rows (8 bytes per entry)
+ *   5  lanes (columns incl. empty lanes) of the sliced copy of A^T
+ *   6, 7  as 0, 1 for A^T's chunked columns
+ * Returns SCUC_E_INVALID for a null handle or output.                    */
+int scuc_lp_layout(const scuc_lp* lp, int64_t* out);
+
+/* on = 1 (the default): FP32 products read the matrix's column (row)
+ * indices as 16-bit offsets where the layout allows (scuc_lp_layout);
+ * 0: 32-bit indices everywhere (the same sums: an A/B switch).  Set before
+ * the handle's first solve; afterwards, or for on not 0/1, SCUC_E_INVALID.
+ * This storage format is this library's, not the paper's.                */
+int scuc_lp_set_index16(scuc_lp* lp, int32_t on);
+
 /* Solve with restarted HPR (Eq. 9), or restarted PDHG with ergodic
  * averaging (p->algo).
  *  x0[n], y0[m]: optional warm start (NULL = cold start from x = Pi_K(0),

@@ -108,6 +108,8 @@ _SIGS = {
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "scuc_lp_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int64)]),
+    "scuc_lp_layout": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "scuc_lp_set_index16": (C.c_int, [C.c_void_p, C.c_int32]),
     "scuc_lp_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveParams), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
     "scuc_lp_get_log": (C.c_int, [C.c_void_p, C.POINTER(CheckLog), C.c_int32, C.POINTER(C.c_int32)]),

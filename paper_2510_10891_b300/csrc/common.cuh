@@ -52,6 +52,7 @@ struct PartShape {
 };
 
 constexpr int kChunk = 512;             // entries per chunk of a long row (one warp each)
+constexpr int kSpan16 = 65535;          // widest column span a 16-bit offset covers
 // staging (values + indices), row sums, row pointers of a staged run
 constexpr int kStagedSmem = kNnzCap * 12 + kBlock * 8 + (kMaxRows + 1) * 4;
 
@@ -73,6 +74,7 @@ struct Partition {
   int nlong = 0;
   int nchunk = 0;
   int nchunkblk = 0;
+  int64_t nchunk_ent = 0;        // entries in chunks
   int smem = kStagedSmem;        // dynamic shared memory of a main launch
   int4* listx = nullptr;         // list rows {row, first entry, end entry, 0}; row -1 pads a block
   int4* desc = nullptr;          // staged runs {first row, first entry, end entry, (rows << 8) | gsz}
@@ -81,6 +83,14 @@ struct Partition {
   int* chunk_ptr = nullptr;      // [nlong + 1] first chunk of each long row
   double* cpart = nullptr;       // [nchunk] chunk sums
   int* slot = nullptr;           // [nblk] partial-sum slot of each block, or nullptr
+  // 16-bit column offsets of the chunks for FP32 products (filled at the
+  // first FP32 set-up; nullptr until then): a chunk's columns (sorted) fall
+  // into at most two clusters of span <= kSpan16, crec[w] = {base0, base1,
+  // split, 0}: entry e of chunk w has column (e < split ? base0 : base1) +
+  // c16[e]; base0 = -1 marks a chunk that needs more clusters (it reads the
+  // 32-bit column array)
+  unsigned short* c16 = nullptr; // [nnz of the matrix] (chunk entries only)
+  int4* crec = nullptr;          // [nchunk]
 };
 
 // Sliced ELL copy of a CSR matrix (used for A^T in the primal step): rows
@@ -101,9 +111,24 @@ struct Sell {
   int64_t nent = 0;       // entries incl. padding (= sptr[nslice] * 32)
   int* sptr = nullptr;    // [nslice + 1] first step of each slice
   int* rows = nullptr;    // [nslice * 32] row of each lane, -1: none
-  int2* cv32 = nullptr;   // [nent] {column, FP32 value bits}
+  int2* cv32 = nullptr;   // [nent] {column, FP32 value bits} (not compressed)
   int* col = nullptr;     // [nent] column (FP64 values)
   double* v64 = nullptr;  // [nent] FP64 value
+  // Compressed FP32 form (compressed = 1; then cv32 is not allocated): the
+  // columns of a row fall into at most two clusters, each spanning at most
+  // 65,535, so an entry is its FP32 value and a 16-bit offset from its
+  // cluster's first column.  lrec[lane of slice] = {row, base0, base1,
+  // kjump}: steps k < kjump are offsets from base0, the others from base1.
+  // Steps go in pairs: pair p of lane r of slice s sits at (pptr[s] + p) *
+  // 32 + r in v2 (the two FP32 values) and o2 (the two offsets, step 2p in
+  // the low half), so a warp reads one pair of steps with two coalesced
+  // requests (256 + 128 bytes).
+  int compressed = 0;
+  int* pptr = nullptr;        // [nslice + 1] first pair of each slice
+  int4* lrec = nullptr;       // [nslice * 32]
+  float2* v2 = nullptr;       // [pptr[nslice] * 32]
+  unsigned* o2 = nullptr;     // [pptr[nslice] * 32]
+  int64_t npair = 0;          // pptr[nslice]
 };
 
 // Device-resident solver state.  Parameters are written by the host before a

@@ -598,6 +598,9 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
     if (!vs32) {
       SCUC_TRY(alloc(&vs32, nnz));
       SCUC_TRY(alloc(&vst32, nnz));
+      // the FP32 chunk products read 16-bit column offsets (once per handle)
+      SCUC_TRY(chunk_offsets(&pA, col, 0));
+      SCUC_TRY(chunk_offsets(&pT, colt, 1));
     }
     if (nnz) {
       k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vs, nnz, vs32);
@@ -619,6 +622,61 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
     SCUC_CUDA(cudaGetLastError());
   }
 
+  return SCUC_OK;
+}
+
+int Handle::chunk_offsets(Partition* P, const int* col_d, int which) {
+  cudaStream_t s = work;
+  if (!P->nchunk || P->c16 || !index16) return SCUC_OK;
+  if (!n16_d) {
+    void* q = nullptr;
+    SCUC_TRY(dev_alloc_bytes(&q, 2 * sizeof(unsigned long long)));
+    allocs.push_back(q);
+    n16_d = static_cast<unsigned long long*>(q);
+    SCUC_CUDA(cudaMemsetAsync(n16_d, 0, 2 * sizeof(unsigned long long), s));
+  }
+  void* q = nullptr;
+  SCUC_TRY(dev_alloc_bytes(&q, (size_t)(nnz > 0 ? nnz : 1) * sizeof(unsigned short)));
+  P->c16 = static_cast<unsigned short*>(q);  // freed with the partition
+  k_chunk_c16<<<P->nchunkblk, kBlock, 0, s>>>(col_d, *P, n16_d + which);
+  nlaunch += 1;
+  SCUC_CUDA(cudaGetLastError());
+  // pageable destination: returns once the count has arrived (once per handle)
+  SCUC_CUDA(cudaMemcpyAsync(&n16_h[which], n16_d + which, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  SCUC_CUDA(cudaStreamSynchronize(s));
+  return SCUC_OK;
+}
+
+int Handle::sell_values(Sell* S, const int* rp_d, const int* col_d, bool compress) {
+  cudaStream_t s = work;
+  if (!S->nslice) return SCUC_OK;
+  if (compress && index16) {
+    int* rec = nullptr;
+    int* bad = nullptr;
+    SCUC_TRY(alloc(&rec, (size_t)S->nslice * 32 * 4));
+    SCUC_TRY(alloc(&bad, 1));
+    S->lrec = reinterpret_cast<int4*>(rec);
+    SCUC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    k_sell_lrec<<<(S->nslice + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(*S, rp_d, col_d, bad);
+    nlaunch += 1;
+    SCUC_CUDA(cudaGetLastError());
+    int bad_h = 0;
+    SCUC_CUDA(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCUC_CUDA(cudaStreamSynchronize(s));
+    if (!bad_h) {
+      float* v = nullptr;
+      int* o = nullptr;
+      SCUC_TRY(alloc(&v, (size_t)S->npair * 64));
+      SCUC_TRY(alloc(&o, (size_t)S->npair * 32));
+      S->v2 = reinterpret_cast<float2*>(v);
+      S->o2 = reinterpret_cast<unsigned*>(o);
+      S->compressed = 1;
+      return SCUC_OK;
+    }
+  }
+  int* cv = nullptr;
+  SCUC_TRY(alloc(&cv, (size_t)S->nent * 2));
+  S->cv32 = reinterpret_cast<int2*>(cv);
   return SCUC_OK;
 }
 
@@ -893,11 +951,21 @@ int Handle::solve(const scuc_solve_params& p, const double* x0_in, const double*
   if (!sell_planned && p.spmv_layout == 0) {
     // sliced ELL copy of the rows of A^T that are not chunked; its values
     // are filled after every scaling
-    if (m > 0 && n > 0) SCUC_TRY(build_sell(rpt_plan, n, kSellMaxLen, &sT, &allocs));
+    if (m > 0 && n > 0) {
+      SCUC_TRY(build_sell(rpt_plan, n, kSellMaxLen, &sT, &allocs));
+      // FP32 values with 16-bit row offsets where every column allows
+      SCUC_TRY(sell_values(&sT, rpt, colt, true));
+    }
     // and of A's rows when A has chunked rows (the dual step of plain
-    // iterations runs them beside the chunk warps)
-    if (m > 0 && n > 0 && pA.nchunk) SCUC_TRY(build_sell(rp_plan, m, kSellMaxLen, &sA, &allocs));
+    // iterations runs them beside the chunk warps); these rows are short
+    // (a few entries), so a per-row record would cost more than 16-bit
+    // offsets save: the 32-bit form
+    if (m > 0 && n > 0 && pA.nchunk) {
+      SCUC_TRY(build_sell(rp_plan, m, kSellMaxLen, &sA, &allocs));
+      SCUC_TRY(sell_values(&sA, rp, col, false));
+    }
     sell_planned = true;
+    scaled_for = -1;  // the copies' values are filled by the next set-up
     std::vector<int>().swap(rpt_plan);
     std::vector<int>().swap(rp_plan);
   }
@@ -1179,6 +1247,32 @@ int scuc_lp_create_box(scuc_lp** out, int32_t m, int32_t n, int64_t nnz, const i
   Handle* h = nullptr;
   SCUC_TRY(scuc::create_handle(&h, m, n, nnz, row_ptr, col, val, c, xl, xu, lo, hi, cuda_stream));
   *out = new scuc_lp{h};
+  return SCUC_OK;
+}
+
+int scuc_lp_layout(const scuc_lp* lp, int64_t* out) {
+  if (!lp || !out) { scuc::set_error("null handle or output"); return SCUC_E_INVALID; }
+  const Handle* h = lp->h;
+  out[0] = (int64_t)h->n16_h[0];
+  out[1] = h->pA.nchunk_ent - out[0];
+  out[2] = h->sA.nent;
+  out[3] = h->sT.compressed ? h->sT.npair * 64 : h->sT.nent;
+  out[4] = h->sT.compressed;
+  out[5] = (int64_t)h->sT.nslice * 32;
+  out[6] = (int64_t)h->n16_h[1];
+  out[7] = h->pT.nchunk_ent - out[6];
+  return SCUC_OK;
+}
+
+int scuc_lp_set_index16(scuc_lp* lp, int32_t on) {
+  if (!lp) { scuc::set_error("null handle"); return SCUC_E_INVALID; }
+  Handle* h = lp->h;
+  if (on != 0 && on != 1) { scuc::set_error("index16 must be 0 or 1"); return SCUC_E_INVALID; }
+  if (h->vs32 || h->sell_planned) {
+    scuc::set_error("index16 is set before the handle's first solve");
+    return SCUC_E_INVALID;
+  }
+  h->index16 = on != 0;
   return SCUC_OK;
 }
 

@@ -26,7 +26,8 @@ struct PartPlan {
   int cls_row[5] = {0, 0, 0, 0, 0};
 };
 int build_partition(const std::vector<int>& rp, int m, Partition* P, int long_min = kGroupRowMax);
-// sliced ELL structure of a CSR matrix with row pointers rp (values filled
+// sliced ELL structure of a CSR matrix with row pointers rp (the FP32 value
+// arrays are chosen and allocated by Handle::sell_values, the values filled
 // on the device by k_sell_fill); freed with the handle's allocations
 // (rows longer than max_len are left out: their sums come from elsewhere)
 int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vector<void*>* allocs);
@@ -98,6 +99,14 @@ struct Handle {
   int setup_device(const std::vector<int>& rp32);
   int build_transpose(std::vector<int>* rpt_h);
   int setup_solver(const std::vector<int>& rp32, const std::vector<int>& rpt_h);
+  // FP32 value form of a sliced ELL copy built by build_sell (compressed
+  // when asked and every row allows it, else the 32-bit form)
+  int sell_values(Sell* S, const int* rp_d, const int* col_d, bool compress);
+  // 16-bit column offsets of a partition's chunks (at the first FP32 set-up)
+  int chunk_offsets(Partition* P, const int* col_d, int which);
+  bool index16 = true;                     // FP32 products may read 16-bit offsets (scuc_lp_set_index16)
+  unsigned long long* n16_d = nullptr;     // [2] entries of A's / A^T's chunks using offsets
+  unsigned long long n16_h[2] = {0, 0};
   int enter();
   int leave();
   DevLP dev() const;

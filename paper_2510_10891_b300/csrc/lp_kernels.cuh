@@ -235,6 +235,72 @@ __device__ __forceinline__ float sell_sum(const Sell& S, const float* __restrict
   return a0 + a1;
 }
 
+// The same sum on the compressed form (Sell::compressed): batches of 8 step
+// pairs (16 entries) per lane, one 8-byte value pair and one 4-byte offset
+// pair per load, step k's column = (k < kjump ? base0 : base1) + offset;
+// even steps into one accumulator, odd steps into the other, as above (the
+// same sum; a padded step of an odd-length slice adds a zero product).
+__device__ __forceinline__ float sell_sum_c(const Sell& S, const float* __restrict__ x, int sl, int lane,
+                                            int4 rec) {
+  constexpr int U = 8;
+  const int np = S.pptr[sl + 1] - S.pptr[sl];
+  const int64_t base = (int64_t)S.pptr[sl] * 32 + lane;
+  const float2* __restrict__ vp = S.v2 + base;
+  const unsigned* __restrict__ op = S.o2 + base;
+  const int b0 = rec.y, b1 = rec.z, kj = rec.w;
+  float a0 = 0.f, a1 = 0.f;
+  int p = 0;
+  for (; p + U <= np; p += U) {
+    float2 v[U];
+    unsigned o[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      v[u] = ldcs(vp + (int64_t)(p + u) * 32);
+      o[u] = ldcs(op + (int64_t)(p + u) * 32);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int k = 2 * (p + u);
+      const int c0 = (k < kj ? b0 : b1) + (int)(o[u] & 0xffffu);
+      const int c1 = (k + 1 < kj ? b0 : b1) + (int)(o[u] >> 16);
+      a0 = fma_t(v[u].x, ldg(x + c0), a0);
+      a1 = fma_t(v[u].y, ldg(x + c1), a1);
+    }
+  }
+  if (p < np) {
+    float2 v[U];
+    unsigned o[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      v[u] = p + u < np ? ldcs(vp + (int64_t)(p + u) * 32) : make_float2(0.f, 0.f);
+      o[u] = p + u < np ? ldcs(op + (int64_t)(p + u) * 32) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (p + u < np) {
+        const int k = 2 * (p + u);
+        const int c0 = (k < kj ? b0 : b1) + (int)(o[u] & 0xffffu);
+        const int c1 = (k + 1 < kj ? b0 : b1) + (int)(o[u] >> 16);
+        a0 = fma_t(v[u].x, ldg(x + c0), a0);
+        a1 = fma_t(v[u].y, ldg(x + c1), a1);
+      }
+    }
+  }
+  return a0 + a1;
+}
+
+// FP32 sum of lane `lane`'s row of slice sl from the FP32 form the copy
+// holds; r receives the row (-1: none).
+__device__ __forceinline__ float sell_sum32(const Sell& S, const float* __restrict__ x, int sl, int lane, int& r) {
+  if (S.compressed) {
+    const int4 rec = S.lrec[(size_t)sl * 32 + lane];
+    r = rec.x;
+    return sell_sum_c(S, x, sl, lane, rec);
+  }
+  r = S.rows[(size_t)sl * 32 + lane];
+  return sell_sum(S, x, sl, lane);
+}
+
 __device__ __forceinline__ double sell_sum(const Sell& S, const double* __restrict__ x, int sl, int lane) {
   constexpr int U = 8;
   const int steps = S.sptr[sl + 1] - S.sptr[sl];
@@ -277,15 +343,16 @@ __global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_primal_sell(DevLP L,
   if ((int)blockIdx.x < nsb) {
     const int sl = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (sl >= L.sT.nslice) return;
-    const int r = L.sT.rows[(size_t)sl * 32 + lane];
     if (!fp64) {
-      const float a = sell_sum(L.sT, L.y32, sl, lane);
+      int r;
+      const float a = sell_sum32(L.sT, L.y32, sl, lane, r);
       if (EPI && r >= 0) epi.load(r);
       if (r >= 0) {
         if (EPI) epi.row(r, (double)a);
         else L.gsum32[r] = a;
       }
     } else {
+      const int r = L.sT.rows[(size_t)sl * 32 + lane];
       const double a = sell_sum(L.sT, L.y, sl, lane);
       if (EPI && r >= 0) epi.load(r);
       if (r >= 0) {
@@ -420,16 +487,17 @@ __global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_dual_fused(DevLP L, 
   }
   const int sl = sb * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (sl >= L.sA.nslice) return;
-  const int r = L.sA.rows[(size_t)sl * 32 + lane];
   DualEpi<false> epi{L, ctrl->s_step, L.coef[2 * j], L.coef[2 * j + 1], fp64, ctrl->algo == SCUC_ALGO_PDHG_AVG,
                      {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
   if (!fp64) {
-    const float a = sell_sum(L.sA, L.xt32, sl, lane);
+    int r;
+    const float a = sell_sum32(L.sA, L.xt32, sl, lane, r);
     if (r >= 0) {
       epi.load(r);
       epi.row(r, (double)a);
     }
   } else {
+    const int r = L.sA.rows[(size_t)sl * 32 + lane];
     const double a = sell_sum(L.sA, L.xt, sl, lane);
     if (r >= 0) {
       epi.load(r);

@@ -89,6 +89,7 @@ int upload_partition(const PartPlan& plan, Partition* P) {
   P->nlong = (int)plan.long_rows.size();
   P->nchunk = (int)plan.chunks.size();
   P->nchunkblk = (P->nchunk + kBlock / 32 - 1) / (kBlock / 32);
+  for (const int2& c : plan.chunks) P->nchunk_ent += c.y - c.x;
   P->nblk = plan.cls_blk[4] + P->nstaged + (P->nlong + kBlock - 1) / kBlock;
   SCUC_TRY(palloc(&P->listx, plan.listx.size()));
   SCUC_TRY(palloc(&P->desc, plan.desc.size()));
@@ -96,6 +97,7 @@ int upload_partition(const PartPlan& plan, Partition* P) {
   SCUC_TRY(palloc(&P->long_rows, plan.long_rows.size()));
   SCUC_TRY(palloc(&P->chunk_ptr, plan.long_rows.size() + 1));
   SCUC_TRY(palloc(&P->cpart, plan.chunks.size()));
+  SCUC_TRY(palloc(&P->crec, plan.chunks.size()));
   if (!plan.slot.empty()) SCUC_TRY(palloc(&P->slot, plan.slot.size()));
   auto up = [](void* dst, const void* src, size_t bytes) {
     return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
@@ -111,7 +113,7 @@ int upload_partition(const PartPlan& plan, Partition* P) {
 
 void free_partition(Partition* P) {
   for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
-                  (void*)P->cpart, (void*)P->slot})
+                  (void*)P->cpart, (void*)P->slot, (void*)P->c16, (void*)P->crec})
     if (q) dev_free(q);
   *P = Partition{};
 }
@@ -142,7 +144,7 @@ int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vec
   }
   std::stable_sort(slices.begin(), slices.end(), [](const Slice& a, const Slice& b) { return a.len > b.len; });
   const int ns = (int)slices.size();
-  std::vector<int> sptr(ns + 1, 0), rows((size_t)ns * 32, -1);
+  std::vector<int> sptr(ns + 1, 0), pptr(ns + 1, 0), rows((size_t)ns * 32, -1);
   for (int k = 0; k < ns; k++) {
     const Slice& sl = slices[k];
     for (int l = 0; l < 32 && sl.first + l < sl.end; l++) rows[(size_t)k * 32 + l] = order[sl.first + l];
@@ -151,6 +153,7 @@ int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vec
       return SCUC_E_INVALID;
     }
     sptr[k + 1] = sptr[k] + sl.len;
+    pptr[k + 1] = pptr[k] + (sl.len + 1) / 2;
   }
   S->nslice = ns;
   S->nent = (int64_t)sptr[ns] * 32;
@@ -158,14 +161,16 @@ int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vec
   allocs->push_back(S->sptr);
   SCUC_TRY(palloc(&S->rows, rows.size()));
   allocs->push_back(S->rows);
-  SCUC_TRY(palloc(&S->cv32, (size_t)S->nent));
-  allocs->push_back(S->cv32);
+  S->npair = pptr[ns];
+  SCUC_TRY(palloc(&S->pptr, pptr.size()));
+  allocs->push_back(S->pptr);
   SCUC_TRY(palloc(&S->col, (size_t)S->nent));
   allocs->push_back(S->col);
   SCUC_TRY(palloc(&S->v64, (size_t)S->nent));
   allocs->push_back(S->v64);
   SCUC_CUDA(cudaMemcpy(S->sptr, sptr.data(), sptr.size() * sizeof(int), cudaMemcpyHostToDevice));
   SCUC_CUDA(cudaMemcpy(S->rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+  SCUC_CUDA(cudaMemcpy(S->pptr, pptr.data(), pptr.size() * sizeof(int), cudaMemcpyHostToDevice));
   return SCUC_OK;
 }
 

@@ -291,7 +291,9 @@ __global__ void k_to_f32(const double* __restrict__ a, int64_t k, float* __restr
 // Values of the sliced ELL copy (Sell) from the CSR arrays of the same
 // matrix: one warp per slice, lane r copies its row's entries in order and
 // pads the slice with its last column and zero.  FP32 values (v32 != null)
-// go to cv32 with their columns, FP64 values (v64 != null) to col / v64.
+// go to cv32 with their columns, or, in the compressed form, to v2 with the
+// 16-bit offsets from the entry's cluster base in o2 (S.lrec filled by
+// k_sell_lrec); FP64 values (v64 != null) to col / v64.
 __global__ void __launch_bounds__(kBlock) k_sell_fill(Sell S, const int* __restrict__ rp,
                                                       const int* __restrict__ col, const double* __restrict__ v64,
                                                       const float* __restrict__ v32) {
@@ -306,11 +308,85 @@ __global__ void __launch_bounds__(kBlock) k_sell_fill(Sell S, const int* __restr
     const int64_t e = base + (int64_t)k * 32;
     const bool in = k < len;
     const int c = in ? col[a + k] : last;
-    if (v32) S.cv32[e] = make_int2(c, __float_as_int(in ? v32[a + k] : 0.0f));
+    if (v32 && !S.compressed) S.cv32[e] = make_int2(c, __float_as_int(in ? v32[a + k] : 0.0f));
     if (v64) {
       S.col[e] = c;
       S.v64[e] = in ? v64[a + k] : 0.0;
     }
+  }
+  if (v32 && S.compressed) {
+    const int4 rec = S.lrec[(size_t)sl * 32 + lane];
+    const int np = S.pptr[sl + 1] - S.pptr[sl];
+    const int64_t pb = (int64_t)S.pptr[sl] * 32 + lane;
+    for (int p = 0; p < np; p++) {
+      float v[2];
+      unsigned o[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int k = 2 * p + h;
+        const bool in = k < len;
+        const int c = in ? col[a + k] : last;
+        v[h] = in ? v32[a + k] : 0.0f;
+        o[h] = (unsigned)(c - (k < rec.w ? rec.y : rec.z));
+      }
+      S.v2[pb + (int64_t)p * 32] = make_float2(v[0], v[1]);
+      S.o2[pb + (int64_t)p * 32] = (o[0] & 0xffffu) | (o[1] << 16);
+    }
+  }
+}
+
+// Cluster bases of the compressed FP32 form (Sell::lrec): lane r of a slice
+// splits its row's columns (sorted) at the first one more than kSpan16 past
+// the row's first column; *bad is set if the second part spans more than
+// kSpan16 as well (the copy then keeps the 32-bit form).  Lanes without a
+// row, and empty rows, get base 0.
+__global__ void __launch_bounds__(kBlock) k_sell_lrec(Sell S, const int* __restrict__ rp,
+                                                      const int* __restrict__ col, int* __restrict__ bad) {
+  const int sl = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (sl >= S.nslice) return;
+  const int r = S.rows[(size_t)sl * 32 + lane];
+  const int a = r >= 0 ? rp[r] : 0, len = r >= 0 ? rp[r + 1] - a : 0;
+  int b0 = len > 0 ? col[a] : 0, b1 = b0, kj = len;
+  for (int k = 1; k < len; k++) {
+    const int c = col[a + k];
+    if (kj == len) {
+      if ((int64_t)c - b0 > kSpan16) {
+        kj = k;
+        b1 = c;
+      }
+    } else if ((int64_t)c - b1 > kSpan16) {
+      *bad = 1;
+      break;
+    }
+  }
+  S.lrec[(size_t)sl * 32 + lane] = make_int4(r, b0, b1, kj);
+}
+
+// 16-bit column offsets of a partition's chunks (Partition::c16 / crec):
+// one warp per chunk; the chunk's columns (sorted) split at the first one
+// more than kSpan16 past the first column; a chunk whose second part spans
+// more than kSpan16 as well gets base0 = -1.  *n16 counts the entries of the
+// chunks that use offsets.
+__global__ void __launch_bounds__(kBlock) k_chunk_c16(const int* __restrict__ col, Partition P,
+                                                      unsigned long long* __restrict__ n16) {
+  const int w = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= P.nchunk) return;
+  const int2 c = P.chunks[w];
+  const int b0 = col[c.x];
+  int split = c.y;
+  for (int e = c.x + lane; e < c.y; e += 32)
+    if ((int64_t)col[e] - b0 > kSpan16) {
+      split = e;
+      break;
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) split = min(split, __shfl_xor_sync(0xffffffffu, split, off));
+  const int b1 = split < c.y ? col[split] : b0;
+  const bool narrow = (int64_t)col[c.y - 1] - b1 <= kSpan16;
+  for (int e = c.x + lane; narrow && e < c.y; e += 32) P.c16[e] = (unsigned short)(col[e] - (e < split ? b0 : b1));
+  if (lane == 0) {
+    P.crec[w] = make_int4(narrow ? b0 : -1, b1, split, 0);
+    if (narrow) atomicAdd(n16, (unsigned long long)(c.y - c.x));
   }
 }
 

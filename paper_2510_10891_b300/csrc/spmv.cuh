@@ -6,7 +6,8 @@
 // chunk launch (k_chunk_sums and friends) gives every chunk one warp that
 // streams it with coalesced lane-strided loads (the whole chunk in flight
 // for FP32 values, eight entries per lane at a time for FP64) and stores the
-// chunk sum.  The main launch gives every long row one
+// chunk sum (FP32 values: columns read as 16-bit offsets from one of two
+// bases per chunk where the chunk's columns allow).  The main launch gives every long row one
 // thread that adds its chunk sums in chunk order and runs the epilogue; its
 // other blocks are
 //  * list blocks: kBlock/gsz rows of similar length, gsz = 32, 16, 8 or 4
@@ -191,6 +192,51 @@ __device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT
                                                                                                a + li, z, nl);
 }
 
+// The FP32 chunk product of batched_dot<float, 16, 2, true> (lanes 32
+// apart, batches of 16, even and odd batch slots in two accumulators, the
+// last batch predicated; the same sums bit for bit) with the columns read as
+// 16-bit offsets: entry q's column is (q < split ? b0 : b1) + c16[q].  6
+// bytes per entry instead of 8 on a product bound by HBM.
+__device__ __forceinline__ float batched_dot16(const unsigned short* __restrict__ c16, int4 rec,
+                                               const float* __restrict__ val, const float* __restrict__ x,
+                                               int e, int z) {
+  constexpr int U = 16, nl = 32;
+  const float* __restrict__ x0 = x + rec.x;
+  const float* __restrict__ x1 = x + rec.y;
+  const int split = rec.z;
+  float s0 = 0.f, s1 = 0.f;
+  for (; e + (U - 1) * nl < z; e += U * nl) {
+    unsigned short c[U];
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      c[u] = ldcs(c16 + e + u * nl);
+      v[u] = ldcs(val + e + u * nl);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      s0 = fma_t(v[u], ldg((e + u * nl < split ? x0 : x1) + c[u]), s0);
+      s1 = fma_t(v[u + 1], ldg((e + (u + 1) * nl < split ? x0 : x1) + c[u + 1]), s1);
+    }
+  }
+  if (e < z) {
+    unsigned short c[U];
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int q = e + u * nl;
+      c[u] = q < z ? ldcs(c16 + q) : (unsigned short)0;
+      v[u] = q < z ? ldcs(val + q) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      if (e + u * nl < z) s0 = fma_t(v[u], ldg((e + u * nl < split ? x0 : x1) + c[u]), s0);
+      if (e + (u + 1) * nl < z) s1 = fma_t(v[u + 1], ldg((e + (u + 1) * nl < split ? x0 : x1) + c[u + 1]), s1);
+    }
+  }
+  return s0 + s1;
+}
+
 // One warp per chunk of a long row (chunk launch): chunk w = blockIdx.x *
 // (kBlock / 32) + warp; lane-strided entries, for FP32 values one predicated
 // batch of 16 per lane (a whole 512-entry chunk; measured faster than two
@@ -207,8 +253,15 @@ __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT
   const int w = (cb < 0 ? (int)blockIdx.x : cb) * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= part.nchunk) return;
   const int2 c = part.chunks[w];
-  VT s = sizeof(VT) == 4 ? batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32)
-                          : batched_dot<VT, 8, 1, false>(col, val, x, c.x + lane, c.y, 32);
+  VT s;
+  if constexpr (sizeof(VT) == 4) {
+    // 16-bit column offsets once they are filled, unless the chunk is wider
+    const int4 rec = part.c16 ? part.crec[w] : make_int4(-1, 0, 0, 0);
+    s = rec.x >= 0 ? batched_dot16(part.c16, rec, val, x, c.x + lane, c.y)
+                   : batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32);
+  } else {
+    s = batched_dot<VT, 8, 1, false>(col, val, x, c.x + lane, c.y, 32);
+  }
   s = warp_sum(s);
   if (lane == 0) part.cpart[w] = (double)s;
 }

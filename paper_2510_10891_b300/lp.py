@@ -173,6 +173,20 @@ class LP:
         self.m, self.n, self.nnz = m.value, n.value, nnz.value
         return self
 
+    def set_index16(self, on):
+        """scuc_lp_set_index16: 16-bit index offsets in FP32 products (before
+        the first solve)."""
+        L.check(L.lib().scuc_lp_set_index16(self.h, int(bool(on))))
+
+    def layout(self):
+        """Storage of the entries the FP32 iteration products read
+        (scuc_lp_layout), valid after the first solve with FP32 products."""
+        out = (C.c_int64 * 8)()
+        L.check(L.lib().scuc_lp_layout(self.h, out))
+        keys = ("a_chunk16", "a_chunk32", "a_sell", "t_sell", "t_sell_compressed", "t_sell_lanes",
+                "t_chunk16", "t_chunk32")
+        return {k: int(v) for k, v in zip(keys, out)}
+
     def fix_and_propagate(self, G, T, u_idx, v_idx, w_idx, u_init, x, tau=0.1, t_first=1,
                           max_passes=100, is_int=None, build_reduced=True):
         """One fixing round (Round + Algorithm 1, propagation, reduced LP).

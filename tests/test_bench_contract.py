@@ -15,7 +15,8 @@ def test_stored_traffic_matches_the_kernel_sources():
     assert set(t["dram_bytes_per_launch"]) >= {"primal_fp32", "dual_fp32"}
     # measured traffic is at least the algorithmic bytes' order (no stale tiny value)
     for kind in ("primal", "dual"):
-        ratio = t["dram_bytes_per_launch"][kind + "_fp32"] / bench.spmv_bytes(t["m"], t["n"], t["nnz"], kind, "fp32")
+        ratio = t["dram_bytes_per_launch"][kind + "_fp32"] / bench.spmv_bytes(t["m"], t["n"], t["nnz"], kind, "fp32",
+                                                                              t.get("layout"))
         assert 0.9 < ratio < 1.5, (kind, ratio)
 
 
