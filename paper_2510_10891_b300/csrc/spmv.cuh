@@ -195,8 +195,11 @@ __device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT
 // The FP32 chunk product of batched_dot<float, 16, 2, true> (lanes 32
 // apart, batches of 16, even and odd batch slots in two accumulators, the
 // last batch predicated; the same sums bit for bit) with the columns read as
-// 16-bit offsets: entry q's column is (q < split ? b0 : b1) + c16[q].  6
-// bytes per entry instead of 8 on a product bound by HBM.
+// 16-bit offsets from a base B: entry q's column is B + c16[q].  6 bytes per
+// entry instead of 8 on a product bound by HBM.  TWO: the chunk's columns
+// have a second cluster from entry `split` on (B = b1 there); otherwise every
+// entry uses b0 (a warp-uniform choice per chunk: most chunks have one).
+template <bool TWO>
 __device__ __forceinline__ float batched_dot16(const unsigned short* __restrict__ c16, int4 rec,
                                                const float* __restrict__ val, const float* __restrict__ x,
                                                int e, int z) {
@@ -215,8 +218,8 @@ __device__ __forceinline__ float batched_dot16(const unsigned short* __restrict_
     }
 #pragma unroll
     for (int u = 0; u < U; u += 2) {
-      s0 = fma_t(v[u], ldg((e + u * nl < split ? x0 : x1) + c[u]), s0);
-      s1 = fma_t(v[u + 1], ldg((e + (u + 1) * nl < split ? x0 : x1) + c[u + 1]), s1);
+      s0 = fma_t(v[u], ldg((TWO && e + u * nl >= split ? x1 : x0) + c[u]), s0);
+      s1 = fma_t(v[u + 1], ldg((TWO && e + (u + 1) * nl >= split ? x1 : x0) + c[u + 1]), s1);
     }
   }
   if (e < z) {
@@ -230,8 +233,9 @@ __device__ __forceinline__ float batched_dot16(const unsigned short* __restrict_
     }
 #pragma unroll
     for (int u = 0; u < U; u += 2) {
-      if (e + u * nl < z) s0 = fma_t(v[u], ldg((e + u * nl < split ? x0 : x1) + c[u]), s0);
-      if (e + (u + 1) * nl < z) s1 = fma_t(v[u + 1], ldg((e + (u + 1) * nl < split ? x0 : x1) + c[u + 1]), s1);
+      if (e + u * nl < z) s0 = fma_t(v[u], ldg((TWO && e + u * nl >= split ? x1 : x0) + c[u]), s0);
+      if (e + (u + 1) * nl < z)
+        s1 = fma_t(v[u + 1], ldg((TWO && e + (u + 1) * nl >= split ? x1 : x0) + c[u + 1]), s1);
     }
   }
   return s0 + s1;
@@ -257,8 +261,9 @@ __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT
   if constexpr (sizeof(VT) == 4) {
     // 16-bit column offsets once they are filled, unless the chunk is wider
     const int4 rec = part.c16 ? part.crec[w] : make_int4(-1, 0, 0, 0);
-    s = rec.x >= 0 ? batched_dot16(part.c16, rec, val, x, c.x + lane, c.y)
-                   : batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32);
+    if (rec.x < 0) s = batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32);
+    else if (rec.z >= c.y) s = batched_dot16<false>(part.c16, rec, val, x, c.x + lane, c.y);
+    else s = batched_dot16<true>(part.c16, rec, val, x, c.x + lane, c.y);
   } else {
     s = batched_dot<VT, 8, 1, false>(col, val, x, c.x + lane, c.y, 32);
   }
