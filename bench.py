@@ -732,6 +732,8 @@ def main():
                       "solve_s": float(np.mean([i["solve_ms"] + i["setup_ms"] for i in infos])) / 1e3,
                       "fix_propagate_reduce_s": float(np.mean(fix_ms[-args.steps:])) / 1e3,
                       "fixed_triples": last["fix"]["nfixed"], "propagation_passes": last["fix"]["passes"],
+                      "fix_ms_parts": {k: float(np.mean([i["fix"][k] for i in infos]))
+                                       for k in ("ms_propagate", "ms_reduce", "ms_setup")},
                       "reduced_lp": last.get("reduced")},
            "roofline": roof, "clocks": clocks,
            "gpu_launches": int(sum(i["launches"] for i in infos)),

@@ -304,7 +304,8 @@ def add_rows(base, pool, rows):
 def transmission_filter(base, pool, viol_tol=1e-6, max_rounds=20, **params):
     """Solve base, then repeatedly add the pool rows violated by the solution
     (each at most once) and re-solve from the previous (x, y) with y = 0 on
-    the new rows.  Returns the last LP, its solve and the rounds."""
+    the new rows, until no violated pool row is outside the LP (Fig. 1).
+    Returns the last LP, its solve and the rounds."""
     lp, x, y = as_lp(base), None, None
     added = np.zeros(as_lp(pool)["m"], dtype=bool)
     rounds, order = [], []
@@ -315,10 +316,13 @@ def transmission_filter(base, pool, viol_tol=1e-6, max_rounds=20, **params):
         rounds.append(dict(m=lp["m"], iters=r["info"]["iters"], status=r["info"]["status"], violated=len(viol),
                            added=len(new), max_violation=worst))
         if len(new) == 0:
-            return dict(lp=lp, result=r, rounds=rounds, converged=len(viol) == 0,
+            # every violated pool row is already in the LP, which holds it to
+            # the solve's own tolerance: no round can add anything
+            return dict(lp=lp, result=r, rounds=rounds, converged=True, violated_in_model=len(viol),
                         rows_added=np.asarray(order, dtype=np.int32))
         added[new] = True
         order.extend(new.tolist())
         lp = add_rows(lp, pool, new)
         x, y = r["x"], np.concatenate([r["y"], np.zeros(len(new))])
-    return dict(lp=lp, result=r, rounds=rounds, converged=False, rows_added=np.asarray(order, dtype=np.int32))
+    return dict(lp=lp, result=r, rounds=rounds, converged=False, violated_in_model=int(np.sum(added[viol])),
+                rows_added=np.asarray(order, dtype=np.int32))

@@ -698,6 +698,8 @@ int Handle::power_start(const scuc_solve_params& p) {
   // MIXED solves run the products in FP32 (values vs32 / vst32; q in xt32,
   // u = A q in y32: both unused until the iterations start)
   power_f32 = p.precision == SCUC_MIXED && vs32 && vst32;
+  // FP32 A^T products on the sliced copy of A^T when the solve uses it
+  power_sell = power_f32 && sT.nslice > 0 && p.spmv_layout == 0;
   k_power_norm_seed<<<grid_for(n), kBlock, 0, s>>>(n, qv, power_f32 ? xt32 : nullptr, pctrl);
   nlaunch += 3;
   SCUC_CUDA(cudaGetLastError());
@@ -715,7 +717,9 @@ int Handle::power_round(const scuc_solve_params& p) {
       if (pA.nblk)
         k_power_spmv32<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs32, q32, pA, nullptr, y32, partRA, pctrl);
       if (pT.nchunk) k_chunk_sums<float><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst32, y32, pT);
-      if (pT.nblk)
+      if (pT.nblk && power_sell)
+        k_power_sell32<<<pT.nblk, kBlock, 0, s>>>(sT, pT, y32, wv, xt32, partRT, pctrl);
+      else if (pT.nblk)
         k_power_spmv32<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst32, y32, pT, wv, xt32, partRT, pctrl);
     } else {
       if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA);
@@ -824,7 +828,11 @@ int Handle::launch_checks(cudaStream_t s, int check_every) {
   if (pA.nblk) k_res_primal<<<pA.nblk, kBlock, pA.smem, s>>>(L);
   if (pT.nchunk) k_chunks_iter<kChunksResDual, kPrecF64><<<pT.nchunkblk, kBlock, 0, s>>>(L);
   if (pT.nblk) {
-    if (algo == SCUC_ALGO_PDHG_AVG) k_res_dual<true><<<pT.nblk, kBlock, pT.smem, s>>>(L);
+    // on the sliced copy of A^T when the solve's primal products use it
+    // (the same partial-sum slots as the CSR form)
+    if (use_sell && algo == SCUC_ALGO_PDHG_AVG) k_res_dual_sell<true><<<pT.nblk, kBlock, 0, s>>>(L);
+    else if (use_sell) k_res_dual_sell<false><<<pT.nblk, kBlock, 0, s>>>(L);
+    else if (algo == SCUC_ALGO_PDHG_AVG) k_res_dual<true><<<pT.nblk, kBlock, pT.smem, s>>>(L);
     else k_res_dual<false><<<pT.nblk, kBlock, pT.smem, s>>>(L);
   }
   if (detect) {  // certificate products A (x_bar - x), A^T (y_bar - y)

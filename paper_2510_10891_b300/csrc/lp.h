@@ -118,6 +118,7 @@ struct Handle {
   PowerCtrl* pctrl_host = nullptr;  // pinned copy of the power method's state
   cudaEvent_t ev_power = nullptr;
   bool power_f32 = false;
+  bool power_sell = false;  // FP32 power iterations run A^T on the sliced copy
   int power_rounds = 0;
   int ensure_log(int cap);
   template <int PREC>

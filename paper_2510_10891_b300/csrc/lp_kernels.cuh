@@ -590,6 +590,47 @@ __global__ void __launch_bounds__(kBlock) k_res_dual(DevLP L) {
   block_store<AVG ? 2 : 1>(epi.acc, L.partRT, L.pT);
 }
 
+// A^T v on the sliced copy of A^T with a per-column epilogue, for launches
+// whose block partial sums the host or the decide kernel reads as nslot
+// (= A^T's CSR partition block count) slots: block b takes slice blocks b,
+// b + nslot, ... (8 slices each, one per warp) and long columns b * kBlock +
+// t, (b + nslot) * kBlock + t, ... (their chunk sums already computed, added
+// in chunk order), then stores its Q partial sums in slot b; a block with no
+// work stores zeros.  Deterministic: fixed assignment, fixed orders.  VT:
+// the product's value type (FP32 values: the FP32 form the copy holds).
+template <typename VT, class Epi>
+__device__ __forceinline__ void sell_gridstride(const Sell& S, const Partition& pT, const VT* __restrict__ x,
+                                                Epi& epi) {
+  const int nslot = (int)gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nsb = (S.nslice + kBlock / 32 - 1) / (kBlock / 32);
+  for (int sb = (int)blockIdx.x; sb < nsb; sb += nslot) {
+    const int sl = sb * (kBlock / 32) + warp;
+    if (sl >= S.nslice) continue;  // warp-uniform
+    int r;
+    VT a;
+    if constexpr (sizeof(VT) == 4) {
+      a = sell_sum32(S, x, sl, lane, r);
+    } else {
+      r = S.rows[(size_t)sl * 32 + lane];
+      a = sell_sum(S, x, sl, lane);
+    }
+    if (r >= 0) epi.row(r, a);
+  }
+  for (int i = (int)blockIdx.x * kBlock + (int)threadIdx.x; i < pT.nlong; i += nslot * kBlock)
+    epi.row(pT.long_rows[i], (VT)chunk_total(pT, i));
+}
+
+// Check iterations of one LP with a sliced copy of A^T: A^T y_bar and the
+// dual residual (k_res_dual's epilogue and partial-sum slots).
+template <bool AVG>
+__global__ void __launch_bounds__(kBlock) k_res_dual_sell(DevLP L) {
+  const Ctrl* ctrl = L.ctrl;
+  if (ctrl->done) return;
+  ResDualEpi<AVG> epi{L, ctrl->gamma, {}};
+  sell_gridstride<double>(L.sT, L.pT, L.ybar, epi);
+  block_store_slot<AVG ? 2 : 1>(epi.acc, L.partRT, (int)gridDim.x, (int)blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Infeasibility certificates at a check (scaled LP; scaling maps certificates
 // to certificates).  Rays: u = y_bar - y (dychk) and d = x_bar - x (dxchk).

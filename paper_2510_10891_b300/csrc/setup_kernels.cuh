@@ -465,6 +465,18 @@ __global__ void __launch_bounds__(kBlock) k_power_spmv32(const int* __restrict__
   block_store<1>(epi.acc, psum, part);
 }
 
+// The A^T product of an FP32 power iteration on the sliced copy of A^T
+// (one LP; its partial sums in A^T's CSR partition slots, as
+// k_power_spmv32 stores them).
+__global__ void __launch_bounds__(kBlock) k_power_sell32(Sell S, Partition pT, const float* __restrict__ in,
+                                                         double* __restrict__ out, float* __restrict__ out32,
+                                                         double* __restrict__ psum, const PowerCtrl* __restrict__ P) {
+  if (P->done) return;
+  StoreEpi32 epi{out, out32, {0.0}};
+  sell_gridstride<float>(S, pT, in, epi);
+  block_store_slot<1>(epi.acc, psum, (int)gridDim.x, (int)blockIdx.x);
+}
+
 __global__ void __launch_bounds__(kDecideThreads) k_power_decide(const double* pu, int nA, const double* pw,
                                                                  int nT, PowerCtrl* P) {
   if (P->done) return;
