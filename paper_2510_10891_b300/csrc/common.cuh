@@ -83,15 +83,23 @@ struct Partition {
   int* chunk_ptr = nullptr;      // [nlong + 1] first chunk of each long row
   double* cpart = nullptr;       // [nchunk] chunk sums
   int* slot = nullptr;           // [nblk] partial-sum slot of each block, or nullptr
-  // 16-bit column offsets of the chunks for FP32 products (filled at the
-  // first FP32 set-up; nullptr until then): a chunk's columns (sorted) fall
-  // into at most two clusters of span <= kSpan16, crec[w] = {base0, base1,
-  // split, 0}: entry e of chunk w has column (e < split ? base0 : base1) +
-  // c16[e]; base0 = -1 marks a chunk that needs more clusters (it reads the
-  // 32-bit column array)
-  unsigned short* c16 = nullptr; // [nnz of the matrix] (chunk entries only)
+  // FP32 chunk stream (allocated at the first FP32 set-up; nullptr until
+  // then): chunk w's entries as one 3,072-byte record at cst + w *
+  // kChunkRec16: its kChunk FP32 values, then kChunk 16-bit column offsets
+  // (a shorter chunk padded with value 0 and its last entry's offset), so a
+  // warp can load a chunk's entries before it knows anything else about the
+  // chunk.  A chunk's columns (sorted) fall into at most two clusters of
+  // span <= kSpan16: crec[w] = {base0, base1, (len << 16) | split, 0},
+  // chunk-local entry i has column (i < split ? base0 : base1) + offset[i];
+  // base0 = -1 marks a chunk that needs more clusters (its FP32 products
+  // read the CSR arrays with 32-bit columns).
+  uint4* cst = nullptr;          // [nchunk * kChunkRec16]
   int4* crec = nullptr;          // [nchunk]
 };
+
+// 16-byte units of a chunk record: kChunk values (4 bytes) + offsets (2 bytes)
+constexpr int kChunkRec16 = kChunk * 6 / 16;
+
 
 // Sliced ELL copy of a CSR matrix (used for A^T in the primal step): rows
 // go in slices of 32, one row per lane; entry k of the row in lane r of

@@ -598,15 +598,19 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
     if (!vs32) {
       SCUC_TRY(alloc(&vs32, nnz));
       SCUC_TRY(alloc(&vst32, nnz));
-      // the FP32 chunk products read 16-bit column offsets (once per handle)
-      SCUC_TRY(chunk_offsets(&pA, col, 0));
-      SCUC_TRY(chunk_offsets(&pT, colt, 1));
+      // the FP32 chunk products read a chunk stream of values and 16-bit
+      // column offsets (its column part once per handle)
+      SCUC_TRY(chunk_stream(&pA, col, 0));
+      SCUC_TRY(chunk_stream(&pT, colt, 1));
     }
     if (nnz) {
       k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vs, nnz, vs32);
       k_to_f32<<<grid_for(nnz), kBlock, 0, s>>>(vst, nnz, vst32);
       nlaunch += 2;
     }
+    if (pA.cst) k_chunk_vals<<<pA.nchunkblk, kBlock, 0, s>>>(vs32, pA);
+    if (pT.cst) k_chunk_vals<<<pT.nchunkblk, kBlock, 0, s>>>(vst32, pT);
+    nlaunch += (pA.cst ? 1 : 0) + (pT.cst ? 1 : 0);
     SCUC_CUDA(cudaGetLastError());
   }
   if (sT.nslice) {
@@ -625,9 +629,9 @@ int Handle::setup_scaling(int use_scaling, bool need_f32) {
   return SCUC_OK;
 }
 
-int Handle::chunk_offsets(Partition* P, const int* col_d, int which) {
+int Handle::chunk_stream(Partition* P, const int* col_d, int which) {
   cudaStream_t s = work;
-  if (!P->nchunk || P->c16 || !index16) return SCUC_OK;
+  if (!P->nchunk || P->cst || !index16) return SCUC_OK;
   if (!n16_d) {
     void* q = nullptr;
     SCUC_TRY(dev_alloc_bytes(&q, 2 * sizeof(unsigned long long)));
@@ -636,9 +640,9 @@ int Handle::chunk_offsets(Partition* P, const int* col_d, int which) {
     SCUC_CUDA(cudaMemsetAsync(n16_d, 0, 2 * sizeof(unsigned long long), s));
   }
   void* q = nullptr;
-  SCUC_TRY(dev_alloc_bytes(&q, (size_t)(nnz > 0 ? nnz : 1) * sizeof(unsigned short)));
-  P->c16 = static_cast<unsigned short*>(q);  // freed with the partition
-  k_chunk_c16<<<P->nchunkblk, kBlock, 0, s>>>(col_d, *P, n16_d + which);
+  SCUC_TRY(dev_alloc_bytes(&q, (size_t)P->nchunk * kChunkRec16 * 16));
+  P->cst = static_cast<uint4*>(q);  // freed with the partition
+  k_chunk_rec<<<P->nchunkblk, kBlock, 0, s>>>(col_d, *P, n16_d + which);
   nlaunch += 1;
   SCUC_CUDA(cudaGetLastError());
   // pageable destination: returns once the count has arrived (once per handle)

@@ -102,8 +102,8 @@ struct Handle {
   // FP32 value form of a sliced ELL copy built by build_sell (compressed
   // when asked and every row allows it, else the 32-bit form)
   int sell_values(Sell* S, const int* rp_d, const int* col_d, bool compress);
-  // 16-bit column offsets of a partition's chunks (at the first FP32 set-up)
-  int chunk_offsets(Partition* P, const int* col_d, int which);
+  // FP32 chunk stream of a partition (at the first FP32 set-up)
+  int chunk_stream(Partition* P, const int* col_d, int which);
   bool index16 = true;                     // FP32 products may read 16-bit offsets (scuc_lp_set_index16)
   unsigned long long* n16_d = nullptr;     // [2] entries of A's / A^T's chunks using offsets
   unsigned long long n16_h[2] = {0, 0};

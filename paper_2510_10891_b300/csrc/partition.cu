@@ -113,7 +113,7 @@ int upload_partition(const PartPlan& plan, Partition* P) {
 
 void free_partition(Partition* P) {
   for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
-                  (void*)P->cpart, (void*)P->slot, (void*)P->c16, (void*)P->crec})
+                  (void*)P->cpart, (void*)P->slot, (void*)P->cst, (void*)P->crec})
     if (q) dev_free(q);
   *P = Partition{};
 }

@@ -362,32 +362,49 @@ __global__ void __launch_bounds__(kBlock) k_sell_lrec(Sell S, const int* __restr
   S.lrec[(size_t)sl * 32 + lane] = make_int4(r, b0, b1, kj);
 }
 
-// 16-bit column offsets of a partition's chunks (Partition::c16 / crec):
-// one warp per chunk; the chunk's columns (sorted) split at the first one
-// more than kSpan16 past the first column; a chunk whose second part spans
-// more than kSpan16 as well gets base0 = -1.  *n16 counts the entries of the
-// chunks that use offsets.
-__global__ void __launch_bounds__(kBlock) k_chunk_c16(const int* __restrict__ col, Partition P,
+// Column part of the FP32 chunk stream (Partition::cst / crec), once per
+// handle: one warp per chunk; the chunk's columns (sorted) split at the
+// first one more than kSpan16 past the first column; a chunk whose second
+// part spans more than kSpan16 as well gets base0 = -1 (32-bit columns).
+// Padding entries repeat the last entry's offset.  *n16 counts the entries
+// of the chunks that use offsets.
+__global__ void __launch_bounds__(kBlock) k_chunk_rec(const int* __restrict__ col, Partition P,
                                                       unsigned long long* __restrict__ n16) {
   const int w = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= P.nchunk) return;
   const int2 c = P.chunks[w];
+  const int len = c.y - c.x;
   const int b0 = col[c.x];
-  int split = c.y;
-  for (int e = c.x + lane; e < c.y; e += 32)
-    if ((int64_t)col[e] - b0 > kSpan16) {
-      split = e;
+  int split = len;
+  for (int i = lane; i < len; i += 32)
+    if ((int64_t)col[c.x + i] - b0 > kSpan16) {
+      split = i;
       break;
     }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) split = min(split, __shfl_xor_sync(0xffffffffu, split, off));
-  const int b1 = split < c.y ? col[split] : b0;
+  const int b1 = split < len ? col[c.x + split] : b0;
   const bool narrow = (int64_t)col[c.y - 1] - b1 <= kSpan16;
-  for (int e = c.x + lane; narrow && e < c.y; e += 32) P.c16[e] = (unsigned short)(col[e] - (e < split ? b0 : b1));
-  if (lane == 0) {
-    P.crec[w] = make_int4(narrow ? b0 : -1, b1, split, 0);
-    if (narrow) atomicAdd(n16, (unsigned long long)(c.y - c.x));
+  unsigned short* offs = reinterpret_cast<unsigned short*>(P.cst + (size_t)w * kChunkRec16) + 2 * kChunk;
+  for (int i = lane; narrow && i < kChunk; i += 32) {
+    const int e = c.x + min(i, len - 1);
+    offs[i] = (unsigned short)(col[e] - (min(i, len - 1) < split ? b0 : b1));
   }
+  if (lane == 0) {
+    P.crec[w] = make_int4(narrow ? b0 : -1, b1, (len << 16) | split, 0);
+    if (narrow) atomicAdd(n16, (unsigned long long)len);
+  }
+}
+
+// Value part of the FP32 chunk stream, after every FP32 scaling: one warp
+// per chunk copies its FP32 values, zero padded to kChunk.
+__global__ void __launch_bounds__(kBlock) k_chunk_vals(const float* __restrict__ v32, Partition P) {
+  const int w = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= P.nchunk) return;
+  const int2 c = P.chunks[w];
+  const int len = c.y - c.x;
+  float* vals = reinterpret_cast<float*>(P.cst + (size_t)w * kChunkRec16);
+  for (int i = lane; i < kChunk; i += 32) vals[i] = i < len ? v32[c.x + i] : 0.0f;
 }
 
 // --------------------------- power method ---------------------------------

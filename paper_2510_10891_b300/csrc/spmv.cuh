@@ -6,8 +6,9 @@
 // chunk launch (k_chunk_sums and friends) gives every chunk one warp that
 // streams it with coalesced lane-strided loads (the whole chunk in flight
 // for FP32 values, eight entries per lane at a time for FP64) and stores the
-// chunk sum (FP32 values: columns read as 16-bit offsets from one of two
-// bases per chunk where the chunk's columns allow).  The main launch gives every long row one
+// chunk sum (FP32 values: from the chunk stream, 16-byte value and 8-byte
+// offset loads, columns as 16-bit offsets from one of two bases per chunk
+// where the chunk's columns allow).  The main launch gives every long row one
 // thread that adds its chunk sums in chunk order and runs the epilogue; its
 // other blocks are
 //  * list blocks: kBlock/gsz rows of similar length, gsz = 32, 16, 8 or 4
@@ -192,62 +193,69 @@ __device__ __forceinline__ VT group_dot_rt(const int* __restrict__ col, const VT
                                                                                                a + li, z, nl);
 }
 
-// The FP32 chunk product of batched_dot<float, 16, 2, true> (lanes 32
-// apart, batches of 16, even and odd batch slots in two accumulators, the
-// last batch predicated; the same sums bit for bit) with the columns read as
-// 16-bit offsets from a base B: entry q's column is B + c16[q].  6 bytes per
-// entry instead of 8 on a product bound by HBM.  TWO: the chunk's columns
-// have a second cluster from entry `split` on (B = b1 there); otherwise every
-// entry uses b0 (a warp-uniform choice per chunk: most chunks have one).
+// FP32 chunk sums (one warp per chunk of at most kChunk = 512 entries).
+// Lane l takes entries i = 128u + 4l + k (groups u = 0..3 in order, k =
+// 0..3), entry k into accumulator k & 1, then adds its two accumulators;
+// the warp sum follows.  Entries past the chunk's end count as value 0 at
+// the chunk's last column.  From the chunk stream (Partition::cst) a lane
+// reads each group's 4 values with one 16-byte load and their 4 column
+// offsets with one 8-byte load (6 bytes per entry instead of 8 on a product
+// bound by HBM), all issued at once from the chunk's index alone (the
+// record's place is fixed), the chunk's bases (crec) alongside; entry i's
+// column is (i < split ? base0 : base1) + offset (TWO: the chunk has a
+// second cluster; otherwise every entry uses base0, a warp-uniform choice
+// per chunk).  chunk32_sum: the same order on the CSR arrays with 32-bit
+// columns (chunks that need them, or no stream), so both give the same sum
+// bit for bit.
+__device__ __forceinline__ void chunk16_load(const Partition& part, int w, int lane, float4 (&v)[kChunk / 128],
+                                             uint2 (&o)[kChunk / 128]) {
+  const float4* __restrict__ vp = reinterpret_cast<const float4*>(part.cst + (size_t)w * kChunkRec16);
+  const uint2* __restrict__ op = reinterpret_cast<const uint2*>(vp + kChunk / 4);
+#pragma unroll
+  for (int u = 0; u < kChunk / 128; u++) {
+    v[u] = ldcs(vp + 32 * u + lane);
+    o[u] = ldcs(op + 32 * u + lane);
+  }
+}
+
 template <bool TWO>
-__device__ __forceinline__ float batched_dot16(const unsigned short* __restrict__ c16, int4 rec,
-                                               const float* __restrict__ val, const float* __restrict__ x,
-                                               int e, int z) {
-  constexpr int U = 16, nl = 32;
+__device__ __forceinline__ float chunk16_sum(int4 rec, const float4 (&v)[kChunk / 128],
+                                             const uint2 (&o)[kChunk / 128], const float* __restrict__ x, int lane) {
+  const int split = rec.z & 0xffff;
   const float* __restrict__ x0 = x + rec.x;
   const float* __restrict__ x1 = x + rec.y;
-  const int split = rec.z;
-  float s0 = 0.f, s1 = 0.f;
-  for (; e + (U - 1) * nl < z; e += U * nl) {
-    unsigned short c[U];
-    float v[U];
+  float s[2] = {0.f, 0.f};
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      c[u] = ldcs(c16 + e + u * nl);
-      v[u] = ldcs(val + e + u * nl);
-    }
+  for (int u = 0; u < kChunk / 128; u++) {
+    const int i = 128 * u + 4 * lane;
+    const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+    const unsigned cc[4] = {o[u].x & 0xffffu, o[u].x >> 16, o[u].y & 0xffffu, o[u].y >> 16};
 #pragma unroll
-    for (int u = 0; u < U; u += 2) {
-      s0 = fma_t(v[u], ldg((TWO && e + u * nl >= split ? x1 : x0) + c[u]), s0);
-      s1 = fma_t(v[u + 1], ldg((TWO && e + (u + 1) * nl >= split ? x1 : x0) + c[u + 1]), s1);
-    }
+    for (int k = 0; k < 4; k++) s[k & 1] = fma_t(vv[k], ldg((TWO && i + k >= split ? x1 : x0) + cc[k]), s[k & 1]);
   }
-  if (e < z) {
-    unsigned short c[U];
-    float v[U];
+  return s[0] + s[1];
+}
+
+__device__ __forceinline__ float chunk32_sum(const int* __restrict__ col, const float* __restrict__ val,
+                                             const float* __restrict__ x, int2 c, int lane) {
+  float s[2] = {0.f, 0.f};
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int q = e + u * nl;
-      c[u] = q < z ? ldcs(c16 + q) : (unsigned short)0;
-      v[u] = q < z ? ldcs(val + q) : 0.f;
-    }
+  for (int u = 0; u < kChunk / 128; u++)
 #pragma unroll
-    for (int u = 0; u < U; u += 2) {
-      if (e + u * nl < z) s0 = fma_t(v[u], ldg((TWO && e + u * nl >= split ? x1 : x0) + c[u]), s0);
-      if (e + (u + 1) * nl < z)
-        s1 = fma_t(v[u + 1], ldg((TWO && e + (u + 1) * nl >= split ? x1 : x0) + c[u + 1]), s1);
+    for (int k = 0; k < 4; k++) {
+      const int e = c.x + 128 * u + 4 * lane + k;
+      const bool in = e < c.y;
+      s[k & 1] = fma_t(in ? ldcs(val + e) : 0.0f, ldg(x + ldcs(col + (in ? e : c.y - 1))), s[k & 1]);
     }
-  }
-  return s0 + s1;
+  return s[0] + s[1];
 }
 
 // One warp per chunk of a long row (chunk launch): chunk w = blockIdx.x *
-// (kBlock / 32) + warp; lane-strided entries, for FP32 values one predicated
-// batch of 16 per lane (a whole 512-entry chunk; measured faster than two
-// batches of 8), for FP64 batches of 8 into one accumulator (FP64-pipe
-// bound: eight accumulators cost seven combining adds per 16 products, 20%
-// of the dual step); then a fixed warp tree; the sum goes to part.cpart[w]
-// in FP64.
+// (kBlock / 32) + warp; for FP32 values chunk16_sum / chunk32_sum (the whole
+// chunk, 16 entries per lane, in flight at once), for FP64 lane-strided
+// batches of 8 into one accumulator (FP64-pipe bound: eight accumulators
+// cost seven combining adds per 16 products, 20% of the dual step); then a
+// fixed warp tree; the sum goes to part.cpart[w] in FP64.
 // cb: the block's index among the chunk blocks (blockIdx.x unless a launch
 // interleaves them with other work).
 template <typename VT>
@@ -256,15 +264,22 @@ __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT
                                            int cb = -1) {
   const int w = (cb < 0 ? (int)blockIdx.x : cb) * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= part.nchunk) return;
-  const int2 c = part.chunks[w];
   VT s;
   if constexpr (sizeof(VT) == 4) {
-    // 16-bit column offsets once they are filled, unless the chunk is wider
-    const int4 rec = part.c16 ? part.crec[w] : make_int4(-1, 0, 0, 0);
-    if (rec.x < 0) s = batched_dot<VT, 16, 2, true>(col, val, x, c.x + lane, c.y, 32);
-    else if (rec.z >= c.y) s = batched_dot16<false>(part.c16, rec, val, x, c.x + lane, c.y);
-    else s = batched_dot16<true>(part.c16, rec, val, x, c.x + lane, c.y);
+    // the chunk stream once it is filled, unless the chunk needs 32-bit columns
+    if (part.cst) {
+      float4 v[kChunk / 128];
+      uint2 o[kChunk / 128];
+      chunk16_load(part, w, lane, v, o);
+      const int4 rec = part.crec[w];
+      if (rec.x < 0) s = chunk32_sum(col, val, x, part.chunks[w], lane);
+      else if ((rec.z & 0xffff) >= (rec.z >> 16)) s = chunk16_sum<false>(rec, v, o, x, lane);
+      else s = chunk16_sum<true>(rec, v, o, x, lane);
+    } else {
+      s = chunk32_sum(col, val, x, part.chunks[w], lane);
+    }
   } else {
+    const int2 c = part.chunks[w];
     s = batched_dot<VT, 8, 1, false>(col, val, x, c.x + lane, c.y, 32);
   }
   s = warp_sum(s);
