@@ -722,7 +722,8 @@ int Handle::power_round(const scuc_solve_params& p) {
         k_power_spmv32<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs32, q32, pA, nullptr, y32, partRA, pctrl);
       if (pT.nchunk) k_chunk_sums<float><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst32, y32, pT);
       if (pT.nblk && power_sell)
-        k_power_sell32<<<pT.nblk, kBlock, 0, s>>>(sT, pT, y32, wv, xt32, partRT, pctrl);
+        k_power_sell32<<<std::min(pT.nblk, sell_blocks(sT, pT)), kBlock, 0, s>>>(sT, pT, y32, wv, xt32, partRT,
+                                                                                 pctrl);
       else if (pT.nblk)
         k_power_spmv32<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst32, y32, pT, wv, xt32, partRT, pctrl);
     } else {
@@ -834,8 +835,9 @@ int Handle::launch_checks(cudaStream_t s, int check_every) {
   if (pT.nblk) {
     // on the sliced copy of A^T when the solve's primal products use it
     // (the same partial-sum slots as the CSR form)
-    if (use_sell && algo == SCUC_ALGO_PDHG_AVG) k_res_dual_sell<true><<<pT.nblk, kBlock, 0, s>>>(L);
-    else if (use_sell) k_res_dual_sell<false><<<pT.nblk, kBlock, 0, s>>>(L);
+    const int gs = std::min(pT.nblk, sell_blocks(sT, pT));
+    if (use_sell && algo == SCUC_ALGO_PDHG_AVG) k_res_dual_sell<true><<<gs, kBlock, 0, s>>>(L);
+    else if (use_sell) k_res_dual_sell<false><<<gs, kBlock, 0, s>>>(L);
     else if (algo == SCUC_ALGO_PDHG_AVG) k_res_dual<true><<<pT.nblk, kBlock, pT.smem, s>>>(L);
     else k_res_dual<false><<<pT.nblk, kBlock, pT.smem, s>>>(L);
   }

@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(64) k_dual_long(DevLP L, int j) {
   DualEpi<false> epi{L, ctrl->s_step, L.coef[2 * j], L.coef[2 * j + 1], phase64(ctrl, PREC),
                      ctrl->algo == SCUC_ALGO_PDHG_AVG, {0.0, 0.0}, 0.0, 0.0, 0.0, 0.0};
   epi.load(r);
-  const double t = chunk_total(P, li);
+  const double t = chunk_total16(P, li);
   epi.row(r, epi.fp64 ? t : (double)(float)t);
 }
 
@@ -592,12 +592,24 @@ __global__ void __launch_bounds__(kBlock) k_res_dual(DevLP L) {
 
 // A^T v on the sliced copy of A^T with a per-column epilogue, for launches
 // whose block partial sums the host or the decide kernel reads as nslot
-// (= A^T's CSR partition block count) slots: block b takes slice blocks b,
-// b + nslot, ... (8 slices each, one per warp) and long columns b * kBlock +
-// t, (b + nslot) * kBlock + t, ... (their chunk sums already computed, added
-// in chunk order), then stores its Q partial sums in slot b; a block with no
-// work stores zeros.  Deterministic: fixed assignment, fixed orders.  VT:
-// the product's value type (FP32 values: the FP32 form the copy holds).
+// (= A^T's CSR partition block count) slots.  The grid has G = min(nslot,
+// sell_blocks) blocks: block b takes slice blocks b, b + G, ... (8 slices
+// each, one per warp) and long columns b * kBlock + t, (b + G) * kBlock + t,
+// ... (their chunk sums already computed, added in chunk order), stores its
+// Q partial sums in slot b and zeros in slots b + G, b + 2G, ... < nslot.
+// Deterministic: fixed assignment, fixed orders.  VT: the product's value
+// type (FP32 values: the FP32 form the copy holds).
+__host__ __device__ inline int sell_blocks(const Sell& S, const Partition& pT) {
+  return (S.nslice + kBlock / 32 - 1) / (kBlock / 32) + (pT.nlong + kBlock - 1) / kBlock;
+}
+
+template <int Q>
+__device__ __forceinline__ void sell_store(const double (&v)[Q], double* out, int nslot) {
+  block_store_slot<Q>(v, out, nslot, (int)blockIdx.x);
+  for (int z = (int)(blockIdx.x + gridDim.x); z < nslot; z += (int)gridDim.x)
+    if ((int)threadIdx.x < Q) out[threadIdx.x * nslot + z] = 0.0;
+}
+
 template <typename VT, class Epi>
 __device__ __forceinline__ void sell_gridstride(const Sell& S, const Partition& pT, const VT* __restrict__ x,
                                                 Epi& epi) {
@@ -628,7 +640,7 @@ __global__ void __launch_bounds__(kBlock) k_res_dual_sell(DevLP L) {
   if (ctrl->done) return;
   ResDualEpi<AVG> epi{L, ctrl->gamma, {}};
   sell_gridstride<double>(L.sT, L.pT, L.ybar, epi);
-  block_store_slot<AVG ? 2 : 1>(epi.acc, L.partRT, (int)gridDim.x, (int)blockIdx.x);
+  sell_store<AVG ? 2 : 1>(epi.acc, L.partRT, L.pT.nblk);
 }
 
 // ---------------------------------------------------------------------------

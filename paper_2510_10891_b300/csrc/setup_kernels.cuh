@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kBlock) k_power_sell32(Sell S, Partition pT, c
   if (P->done) return;
   StoreEpi32 epi{out, out32, {0.0}};
   sell_gridstride<float>(S, pT, in, epi);
-  block_store_slot<1>(epi.acc, psum, (int)gridDim.x, (int)blockIdx.x);
+  sell_store<1>(epi.acc, psum, pT.nblk);
 }
 
 __global__ void __launch_bounds__(kDecideThreads) k_power_decide(const double* pu, int nA, const double* pw,

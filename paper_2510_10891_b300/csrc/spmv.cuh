@@ -289,6 +289,8 @@ __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT
 // Sum of long row li's chunk sums, in chunk order: loaded eight at a time
 // so a row of many chunks (a 21,000-entry row has 41) waits for one batch,
 // not one load per chunk; the adds keep their order (the same result).
+// One thread per row: B300's FP64 pipe makes a sum that every lane of a
+// warp repeats cost 32 times as much.
 __device__ __forceinline__ double chunk_total(const Partition& part, int li) {
   int c = part.chunk_ptr[li];
   const int ce = part.chunk_ptr[li + 1];
@@ -301,6 +303,23 @@ __device__ __forceinline__ double chunk_total(const Partition& part, int li) {
     for (int u = 0; u < 8; u++) s += v[u];
   }
   for (; c < ce; c++) s += part.cpart[c];
+  return s;
+}
+
+// The same sum in predicated batches of sixteen (three batches for 41
+// chunks), for kernels with registers to spare (the long-row launch).
+__device__ __forceinline__ double chunk_total16(const Partition& part, int li) {
+  int c = part.chunk_ptr[li];
+  const int ce = part.chunk_ptr[li + 1];
+  double s = 0.0;
+  for (; c < ce; c += 16) {
+    double v[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) v[u] = c + u < ce ? part.cpart[c + u] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 16; u++)
+      if (c + u < ce) s += v[u];
+  }
   return s;
 }
 
