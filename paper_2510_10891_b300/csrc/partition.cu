@@ -3,6 +3,7 @@
 // copy.  The plan decides which kernel path every row takes, so the SpMV
 // kernels' traffic depends on this file and the kernel sources only.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "lp.h"
@@ -31,51 +32,83 @@ int palloc(T** p, size_t count) {
 // then the staged blocks, then the long rows.
 void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, bool allow_long, PartPlan* plan,
                     int long_min) {
-  std::vector<int> G[4];  // G[k]: list rows with 32 >> k threads per row
+  // Two passes over the rows: the first gives every row its class (a list
+  // class 0..3, a long row, a short row of a staged run, or a short row in
+  // no list), counting the list rows per class; the second writes the list
+  // rows straight to their class's place, the staged runs and the chunks
+  // in row order.  (Appending to four growing per-class lists and copying
+  // them took three times as long for the 1.5M columns of a 13k-bus A^T.)
+  constexpr unsigned char kLong = 254, kStaged = 255, kNone = 253;
+  static thread_local std::vector<unsigned char> cls;  // per host thread, reused
+  cls.assign(m, kNone);
   *plan = PartPlan{};
   plan->chunk_ptr.assign(1, 0);
-  auto cls = [](int gsz) { return gsz == 32 ? 0 : gsz == 16 ? 1 : gsz == 8 ? 2 : 3; };
-  auto flush_run = [&](int a, int b) {  // short rows [a, b)
-    if (b - a < shape.min_run) {
-      for (int r = a; r < b; r++) G[3].push_back(r);
-      return;
-    }
-    int r = a;
-    while (r < b) {
-      const int start = r;
-      int nz = 0;
-      while (r < b && r - start < kMaxRows && nz + (rp[r + 1] - rp[r]) <= kNnzCap) {
-        nz += rp[r + 1] - rp[r];
-        r++;
-      }
-      const int nr = r - start;
-      int g = 1;
-      while (g < 32 && g * 2 * nr <= kBlock) g *= 2;
-      plan->desc.push_back(make_int4(start, rp[start], rp[r], (nr << 8) | g));
-    }
+  int cnt[4] = {0, 0, 0, 0};
+  auto list_class = [&](int len) {
+    const int g = len > kGroupRowMax ? 32 : group_size_for(len, shape.ept);
+    return g == 32 ? 0 : g == 16 ? 1 : g == 8 ? 2 : 3;
+  };
+  auto mark_run = [&](int a, int b) {  // short rows [a, b): staged, or 4-thread list rows if too few
+    if (b <= a) return;
+    const bool staged = b - a >= shape.min_run;
+    if (!staged) cnt[3] += b - a;
+    memset(cls.data() + a, staged ? kStaged : 3, b - a);
   };
   int run0 = 0;
   for (int r = 0; r < m; r++) {
     const int len = rp[r + 1] - rp[r];
     if (len <= kShortMax) continue;
-    flush_run(run0, r);
+    mark_run(run0, r);
     run0 = r + 1;
     if (len > long_min && allow_long) {
+      cls[r] = kLong;
+    } else {
+      const int k = list_class(len);
+      cls[r] = (unsigned char)k;
+      cnt[k]++;
+    }
+  }
+  mark_run(run0, m);
+  int at[4];
+  for (int k = 0, o = 0; k < 4; k++) {
+    plan->cls_row[k] = at[k] = o;
+    plan->cls_blk[k + 1] = plan->cls_blk[k] + (cnt[k] + (kBlock >> (5 - k)) - 1) / (kBlock >> (5 - k));
+    o += cnt[k];
+  }
+  plan->cls_row[4] = at[3] + cnt[3];
+  plan->listx.resize(plan->cls_row[4]);
+  int4* L = plan->listx.data();
+  for (int r = 0; r < m;) {
+    const unsigned char c = cls[r];
+    if (c < 4) {
+      L[at[c]++] = make_int4(r, rp[r], rp[r + 1], 0);
+      r++;
+    } else if (c == kLong) {
       plan->long_rows.push_back(r);
       for (int e = rp[r]; e < rp[r + 1]; e += kChunk)
         plan->chunks.push_back(make_int2(e, std::min(rp[r + 1], e + kChunk)));
       plan->chunk_ptr.push_back((int)plan->chunks.size());
+      r++;
+    } else if (c == kStaged) {
+      // a run of short rows: blocks of <= kMaxRows rows / <= kNnzCap nonzeros
+      int b = r;
+      while (b < m && cls[b] == kStaged) b++;
+      while (r < b) {
+        const int start = r;
+        int nz = 0;
+        while (r < b && r - start < kMaxRows && nz + (rp[r + 1] - rp[r]) <= kNnzCap) {
+          nz += rp[r + 1] - rp[r];
+          r++;
+        }
+        const int nr = r - start;
+        int g = 1;
+        while (g < 32 && g * 2 * nr <= kBlock) g *= 2;
+        plan->desc.push_back(make_int4(start, rp[start], rp[r], (nr << 8) | g));
+      }
     } else {
-      G[cls(len > kGroupRowMax ? 32 : group_size_for(len, shape.ept))].push_back(r);
+      r++;
     }
   }
-  flush_run(run0, m);
-  for (int k = 0; k < 4; k++) {
-    plan->cls_row[k] = (int)plan->listx.size();
-    for (int r : G[k]) plan->listx.push_back(make_int4(r, rp[r], rp[r + 1], 0));
-    plan->cls_blk[k + 1] = plan->cls_blk[k] + (int)((G[k].size() + (kBlock >> (5 - k)) - 1) / (kBlock >> (5 - k)));
-  }
-  plan->cls_row[4] = (int)plan->listx.size();
 }
 
 // device copies of a planned partition (freed by free_partition)
