@@ -165,14 +165,30 @@ int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vec
   };
   std::vector<int> order(m > 0 ? m : 1);
   std::vector<Slice> slices;
+  // rows of each window ordered by length, longest first, ties by index: a
+  // stable counting sort over the lengths 0..max_len (a comparison sort of
+  // the 1.5M columns of a 13k-bus A^T took 30 ms on the host)
+  std::vector<int> cnt(max_len + 2);
   int kept = 0;
   for (int w0 = 0; w0 < m; w0 += kSellWindow) {
     const int w1 = std::min(m, w0 + kSellWindow);
     const int k0 = kept;
-    for (int r = w0; r < w1; r++)
-      if (rp[r + 1] - rp[r] <= max_len) order[kept++] = r;
-    std::stable_sort(order.begin() + k0, order.begin() + kept,
-                     [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int r = w0; r < w1; r++) {
+      const int len = rp[r + 1] - rp[r];
+      if (len <= max_len) cnt[len]++;
+    }
+    int at = k0;
+    for (int len = max_len; len >= 0; len--) {  // cnt[len] becomes the first place of length len
+      const int c = cnt[len];
+      cnt[len] = at;
+      at += c;
+    }
+    for (int r = w0; r < w1; r++) {
+      const int len = rp[r + 1] - rp[r];
+      if (len <= max_len) order[cnt[len]++] = r;
+    }
+    kept = at;
     for (int q = k0; q < kept; q += 32) slices.push_back(Slice{rp[order[q] + 1] - rp[order[q]], q, kept});
   }
   std::stable_sort(slices.begin(), slices.end(), [](const Slice& a, const Slice& b) { return a.len > b.len; });
