@@ -207,6 +207,7 @@ def cpu_baseline(inst, result=None):
         k = oracle.kkt(oracle.as_lp(inst), *result)
         check = {k2: float(k[k2]) for k2 in ("kkt", "rp", "rd", "gap", "pobj", "dobj")}
     s13 = oracle_13k_sample(inst, threads)
+    s13_1 = oracle_13k_sample(inst, None)   # the same sample, single-threaded build
     full = oracle_to_tolerance(make_preset(SMALL), threads)
     return {"value": s13["value"], "unit": "s", "cores": s13["threads"], "kind": "oracle",
             "sample": "oracle (FP64, OpenMP, %d threads) on the 13k-bus LP: set-up + 8 and + 24 iterations "
@@ -214,7 +215,8 @@ def cpu_baseline(inst, result=None):
                       "count to 1e-4) + %.2f s set-up" % (s13["threads"], s13["sample_s"], s13["s_per_iter"],
                                                           s13["oracle_iters"], s13["oracle_power_iters"],
                                                           s13["setup_s"]),
-            "scuc13k_sample": s13, "measured_to_tolerance": dict(full, workload=SMALL_DESC),
+            "scuc13k_sample": s13, "scuc13k_sample_one_core": s13_1,
+            "measured_to_tolerance": dict(full, workload=SMALL_DESC),
             "oracle_kkt_of_step_result": check}
 
 
