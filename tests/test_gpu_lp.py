@@ -304,6 +304,30 @@ def test_scuc2k_full_size(P):
         assert oracle.kkt(inst, s["x"], s["y"], s["z"])["kkt"] <= 1e-4 * 1.0001
 
 
+def test_scuc13k_full_size(P):
+    """The 13,000-bus relaxation the benchmark solves (1.6M rows, 1.5M
+    columns, 113M nonzeros), in the benchmark's launch configuration: the
+    first 128 FP64 iterations (two check periods) match the oracle (OpenMP
+    build on all host cores) check by check, and a solve to 1e-4 with FP32
+    matvecs from cold start (the sliced copies on 16-bit offsets and the
+    chunk stream) returns a point the oracle certifies."""
+    inst = make_preset("scuc13k")
+    kw = dict(tol=0.0, max_iter=128)
+    o = oracle.hpr_solve(inst, threads=0, **kw)
+    lp = P.LP(inst)
+    g = lp.solve(**kw)
+    _compare_logs(g["log"], o["log"], rtol=1e-6)
+    assert _rel(g["x"], o["x"]) < 1e-7
+    s = lp.solve(tol=1e-4, precision="mixed")
+    assert s["info"]["status"] == 0 and s["info"]["iters_fp32"] == s["info"]["iters"], s["info"]
+    k = oracle.kkt(inst, s["x"], s["y"], s["z"])
+    assert k["kkt"] <= 1e-4 * 1.0001, k
+    assert k["pobj"] == pytest.approx(s["info"]["pobj"], rel=1e-9)
+    lay = lp.layout()
+    assert lay["t_sell_compressed"] == 1 and lay["a_chunk32"] == 0 and lay["a_chunk16"] > 0.9 * inst.nnz
+    lp.close()
+
+
 def test_invalid_inputs_rejected_before_any_kernel(P):
     """Malformed inputs give SCUC_E_INVALID with the first failing row or
     column named (the entries are checked by several host threads while
