@@ -24,6 +24,10 @@ struct PartPlan {
   std::vector<int2> chunks;
   int cls_blk[5] = {0, 0, 0, 0, 0};
   int cls_row[5] = {0, 0, 0, 0, 0};
+  void clear() {  // empty, capacity kept
+    listx.clear(); desc.clear(); long_rows.clear(); chunk_ptr.clear(); slot.clear(); chunks.clear();
+    for (int k = 0; k < 5; k++) cls_blk[k] = cls_row[k] = 0;
+  }
 };
 int build_partition(const std::vector<int>& rp, int m, Partition* P, int long_min = kGroupRowMax);
 // sliced ELL structure of a CSR matrix with row pointers rp (the FP32 value

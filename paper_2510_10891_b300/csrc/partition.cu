@@ -41,7 +41,7 @@ void plan_partition(const std::vector<int>& rp, int m, const PartShape& shape, b
   constexpr unsigned char kLong = 254, kStaged = 255, kNone = 253;
   static thread_local std::vector<unsigned char> cls;  // per host thread, reused
   cls.assign(m, kNone);
-  *plan = PartPlan{};
+  plan->clear();  // keeps the vectors' capacity (see build_partition)
   plan->chunk_ptr.assign(1, 0);
   int cnt[4] = {0, 0, 0, 0};
   auto list_class = [&](int len) {
@@ -224,7 +224,10 @@ int build_sell(const std::vector<int>& rp, int m, int max_len, Sell* S, std::vec
 }
 
 int build_partition(const std::vector<int>& rp, int m, Partition* P, int long_min) {
-  PartPlan plan;
+  // per host thread and reused: a fixing round plans a new LP of a million
+  // rows, whose freshly allocated plan arrays (16 MB) cost more in page
+  // faults than filling them
+  static thread_local PartPlan plan;
   plan_partition(rp, m, PartShape{}, true, &plan, long_min);
   return upload_partition(plan, P);
 }
