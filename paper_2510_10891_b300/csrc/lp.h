@@ -1,5 +1,7 @@
 // Internal declarations of the SCUC LP library (host side).
 #pragma once
+#include <memory>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -17,9 +19,31 @@ struct DevTranspose {
   const std::vector<int>* rpt_h;  // row pointers of A^T (n + 1)
 };
 
+// allocator whose resize leaves new elements default-initialised (for a
+// trivial type: unwritten), for buffers the planner writes in full
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <typename U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+
 // host plan of a Partition
 struct PartPlan {
-  std::vector<int4> listx, desc;
+  std::vector<int4, NoInitAlloc<int4>> listx;  // every list row is written by plan_partition
+  std::vector<int4> desc;
   std::vector<int> long_rows, chunk_ptr, slot;
   std::vector<int2> chunks;
   int cls_blk[5] = {0, 0, 0, 0, 0};
