@@ -717,19 +717,19 @@ int Handle::power_round(const scuc_solve_params& p) {
   float* q32 = f32 ? xt32 : nullptr;
   for (int j = 0; j < 16; j++) {
     if (f32) {
-      if (pA.nchunk) k_chunk_sums<float><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs32, q32, pA);
+      if (pA.nchunk) k_power_chunks<float><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs32, q32, pA, pctrl);
       if (pA.nblk)
         k_power_spmv32<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs32, q32, pA, nullptr, y32, partRA, pctrl);
-      if (pT.nchunk) k_chunk_sums<float><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst32, y32, pT);
+      if (pT.nchunk) k_power_chunks<float><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst32, y32, pT, pctrl);
       if (pT.nblk && power_sell)
         k_power_sell32<<<std::min(pT.nblk, sell_blocks(sT, pT)), kBlock, 0, s>>>(sT, pT, y32, wv, xt32, partRT,
                                                                                  pctrl);
       else if (pT.nblk)
         k_power_spmv32<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst32, y32, pT, wv, xt32, partRT, pctrl);
     } else {
-      if (pA.nchunk) k_chunk_sums<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA);
+      if (pA.nchunk) k_power_chunks<double><<<pA.nchunkblk, kBlock, 0, s>>>(col, vs, qv, pA, pctrl);
       if (pA.nblk) k_power_spmv<<<pA.nblk, kBlock, pA.smem, s>>>(rp, col, vs, qv, pA, uv, partRA, pctrl);
-      if (pT.nchunk) k_chunk_sums<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, uv, pT);
+      if (pT.nchunk) k_power_chunks<double><<<pT.nchunkblk, kBlock, 0, s>>>(colt, vst, uv, pT, pctrl);
       if (pT.nblk) k_power_spmv<<<pT.nblk, kBlock, pT.smem, s>>>(rpt, colt, vst, uv, pT, wv, partRT, pctrl);
     }
     k_power_decide<<<1, kDecideThreads, 0, s>>>(partRA, pA.nblk, partRT, pT.nblk, pctrl);

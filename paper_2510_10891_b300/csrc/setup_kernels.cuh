@@ -482,6 +482,16 @@ __global__ void __launch_bounds__(kBlock) k_power_spmv32(const int* __restrict__
   block_store<1>(epi.acc, psum, part);
 }
 
+// Chunk launch of a power iteration: returns at once when the estimate has
+// converged (a round queues 16 iterations; those after the last do nothing).
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_power_chunks(const int* __restrict__ col, const VT* __restrict__ val,
+                                                         const VT* __restrict__ x, Partition part,
+                                                         const PowerCtrl* __restrict__ P) {
+  if (P->done) return;
+  chunk_warp<VT>(col, val, x, part);
+}
+
 // The A^T product of an FP32 power iteration on the sliced copy of A^T
 // (one LP; its partial sums in A^T's CSR partition slots, as
 // k_power_spmv32 stores them).
