@@ -800,7 +800,8 @@ int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 1], s));
     if (profile) SCUC_CUDA(cudaEventRecord(prof_ev[4 * j + 2], s));
     if (fuse_d) {
-      k_dual_fused<PREC><<<(sA.nslice + kBlock / 32 - 1) / (kBlock / 32) + pA.nchunkblk, kBlock, 0, s>>>(L, j);
+      k_dual_fused<PREC><<<(sA.nslice + kDualWpb - 1) / kDualWpb + (pA.nchunk + kDualWpb - 1) / kDualWpb,
+                           kDualBlock, 0, s>>>(L, j);
       k_dual_long<PREC><<<(pA.nlong + 63) / 64, 64, 0, s>>>(L, j);
     } else {
       if (pA.nchunk) k_chunks_iter<kChunksDual, PREC><<<pA.nchunkblk, kBlock, 0, s>>>(L);

@@ -257,12 +257,12 @@ __device__ __forceinline__ float chunk32_sum(const int* __restrict__ col, const 
 // cost seven combining adds per 16 products, 20% of the dual step); then a
 // fixed warp tree; the sum goes to part.cpart[w] in FP64.
 // cb: the block's index among the chunk blocks (blockIdx.x unless a launch
-// interleaves them with other work).
-template <typename VT>
+// interleaves them with other work); WPB: warps per block of the launch.
+template <typename VT, int WPB = kBlock / 32>
 __device__ __forceinline__ void chunk_warp(const int* __restrict__ col, const VT* __restrict__ val,
                                            const VT* __restrict__ x, const Partition& part,
                                            int cb = -1) {
-  const int w = (cb < 0 ? (int)blockIdx.x : cb) * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int w = (cb < 0 ? (int)blockIdx.x : cb) * WPB + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= part.nchunk) return;
   VT s;
   if constexpr (sizeof(VT) == 4) {
