@@ -789,9 +789,9 @@ int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
     const bool fuse_d = !chk && !split_steps && use_sell_dual;
     if (pT.nchunk) k_chunks_iter<kChunksPrimal, PREC><<<pT.nchunkblk, kBlock, 0, s>>>(L);
     if (use_sell) {
-      const int g = (sT.nslice + kBlock / 32 - 1) / (kBlock / 32) + (pT.nlong + kBlock - 1) / kBlock;
-      if (g && fuse_p) k_primal_sell<PREC, true><<<g, kBlock, 0, s>>>(L, j);
-      else if (g) k_primal_sell<PREC, false><<<g, kBlock, 0, s>>>(L, j);
+      const int g = (sT.nslice + kPrimalWpb - 1) / kPrimalWpb + (pT.nlong + kPrimalBlock - 1) / kPrimalBlock;
+      if (g && fuse_p) k_primal_sell<PREC, true><<<g, kPrimalBlock, 0, s>>>(L, j);
+      else if (g) k_primal_sell<PREC, false><<<g, kPrimalBlock, 0, s>>>(L, j);
     } else if (pT.nblk) {
       k_primal_sum<PREC><<<pT.nblk, kBlock, pT.smem, s>>>(L);
     }

@@ -331,17 +331,20 @@ __device__ __forceinline__ double sell_sum(const Sell& S, const double* __restri
 // iterations): the thread that owns a column runs the primal update on it
 // (operands loaded before the sum) instead of storing g for the elementwise
 // launch; g is rounded as it would have been stored, so the iterates are
-// bit-identical to the two-launch form that check iterations keep.
+// bit-identical to the two-launch form that check iterations keep.  Blocks
+// of two warps (the reason is the fused dual step's; 13k-bus LP: 0.1443 ms
+// per primal step against 0.1461 ms with 256-thread blocks).
+constexpr int kPrimalBlock = 64, kPrimalWpb = kPrimalBlock / 32;
 template <int PREC, bool EPI>
-__global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_primal_sell(DevLP L, int j) {
+__global__ void __launch_bounds__(kPrimalBlock, kDualMinBlocks * kBlock / kPrimalBlock) k_primal_sell(DevLP L, int j) {
   const Ctrl* ctrl = L.ctrl;
   if (ctrl->done) return;
   const bool fp64 = phase64(ctrl, PREC);
   PrimalEpi<false> epi{L, ctrl->sigma, EPI ? L.coef[2 * j] : 0.0, EPI ? L.coef[2 * j + 1] : 0.0, fp64,
                        ctrl->algo == SCUC_ALGO_PDHG_AVG, false, {0.0, 0.0, 0.0, 0.0}, 0.0, 0.0, 0.0, 0.0, 0.0};
-  const int nsb = (L.sT.nslice + kBlock / 32 - 1) / (kBlock / 32);
+  const int nsb = (L.sT.nslice + kPrimalWpb - 1) / kPrimalWpb;
   if ((int)blockIdx.x < nsb) {
-    const int sl = (int)blockIdx.x * (kBlock / 32) + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int sl = (int)blockIdx.x * kPrimalWpb + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (sl >= L.sT.nslice) return;
     if (!fp64) {
       int r;
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(kBlock, kDualMinBlocks) k_primal_sell(DevLP L,
     }
     return;
   }
-  const int i = ((int)blockIdx.x - nsb) * kBlock + (int)threadIdx.x;
+  const int i = ((int)blockIdx.x - nsb) * kPrimalBlock + (int)threadIdx.x;
   if (i >= L.pT.nlong) return;
   const int r = L.pT.long_rows[i];
   if (EPI) epi.load(r);
