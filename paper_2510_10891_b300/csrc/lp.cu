@@ -819,7 +819,7 @@ int Handle::launch_iterations(cudaStream_t s, int check_every, bool profile) {
 // kernels of one period: anchor, iterations, residual SpMVs, decide
 int64_t Handle::period_kernels(int check_every) const {
   const int la = (pA.nblk ? 1 : 0) + (pA.nchunk ? 1 : 0), lt = (pT.nblk ? 1 : 0) + (pT.nchunk ? 1 : 0);
-  const int gt = (sT.nslice + kBlock / 32 - 1) / (kBlock / 32) + (pT.nlong + kBlock - 1) / kBlock;
+  const bool gt = sT.nslice > 0 || pT.nlong > 0;  // k_primal_sell has blocks
   const int lt_iter = use_sell ? (pT.nchunk ? 1 : 0) + (gt ? 1 : 0) : lt;
   // a plain iteration: primal product (+ update unless fused), dual step
   const int plain_p = lt_iter + (!split_steps && use_sell ? 0 : 1);
