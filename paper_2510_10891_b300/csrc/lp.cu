@@ -399,8 +399,9 @@ int Handle::init_device(int32_t m_, int32_t n_, int64_t nnz_, int* d_rp, int* d_
   return setup_device(rp32);
 }
 
-// transpose, partitions and solver buffers (data already on the device)
-int Handle::setup_device(const std::vector<int>& rp32) {
+// transpose, partitions and solver buffers (data already on the device);
+// rp32 is moved from
+int Handle::setup_device(std::vector<int>& rp32) {
   std::vector<int> rpt_h;
   SCUC_TRY(build_transpose(&rpt_h));
   return setup_solver(rp32, rpt_h);
@@ -453,8 +454,9 @@ int Handle::build_transpose(std::vector<int>* rpt_out) {
   return SCUC_OK;
 }
 
-// partitions and solver buffers; rp32 / rpt_h: row pointers of A and A^T
-int Handle::setup_solver(const std::vector<int>& rp32, const std::vector<int>& rpt_h) {
+// partitions and solver buffers; rp32 / rpt_h: row pointers of A and A^T,
+// moved from (kept for the sliced copies of the first solve)
+int Handle::setup_solver(std::vector<int>& rp32, std::vector<int>& rpt_h) {
   cudaStream_t s = work;
   // rows above kSellMaxLen are chunked (warp per 512 entries); the sliced
   // ELL copies below hold the rest for the iteration products
@@ -466,8 +468,8 @@ int Handle::setup_solver(const std::vector<int>& rp32, const std::vector<int>& r
   // on the CSR partition: its short rows are staged runs, its long rows
   // chunks (measured faster than a sliced copy of A's short rows plus an
   // elementwise update on the 13k-bus LP: 0.199 vs 0.210 ms).
-  rpt_plan = rpt_h;
-  if (pA.nchunk) rp_plan = rp32;
+  rpt_plan = std::move(rpt_h);
+  if (pA.nchunk) rp_plan = std::move(rp32);
   for (Partition* P : {&pA, &pT})
     for (void* q : {(void*)P->listx, (void*)P->desc, (void*)P->chunks, (void*)P->long_rows, (void*)P->chunk_ptr,
                     (void*)P->cpart, (void*)P->slot})

@@ -11,12 +11,13 @@ namespace scuc {
 struct DevLP;      // device view of a handle (lp_kernels.cuh)
 struct Validator;  // input checks of scuc_lp_create, run while the arrays are copied (lp.cu)
 
-// A^T of a matrix built elsewhere (Handle::init_device adopts the arrays)
+// A^T of a matrix built elsewhere (Handle::init_device adopts the arrays,
+// and the two host row-pointer arrays: they are moved from)
 struct DevTranspose {
   int *rpt, *colt, *permt;
   double* valt;
-  const std::vector<int>* rp_h;   // row pointers of A (m + 1)
-  const std::vector<int>* rpt_h;  // row pointers of A^T (n + 1)
+  std::vector<int>* rp_h;   // row pointers of A (m + 1)
+  std::vector<int>* rpt_h;  // row pointers of A^T (n + 1)
 };
 
 // allocator whose resize leaves new elements default-initialised (for a
@@ -124,9 +125,9 @@ struct Handle {
   int init_device(int32_t m, int32_t n, int64_t nnz, int* d_rp, int* d_col, double* d_val, double* d_c,
                   double* d_xl, double* d_xu, double* d_lo, double* d_hi, cudaStream_t user,
                   const DevTranspose* t = nullptr);
-  int setup_device(const std::vector<int>& rp32);
+  int setup_device(std::vector<int>& rp32);
   int build_transpose(std::vector<int>* rpt_h);
-  int setup_solver(const std::vector<int>& rp32, const std::vector<int>& rpt_h);
+  int setup_solver(std::vector<int>& rp32, std::vector<int>& rpt_h);
   // FP32 value form of a sliced ELL copy built by build_sell (compressed
   // when asked and every row allows it, else the 32-bit form)
   int sell_values(Sell* S, const int* rp_d, const int* col_d, bool compress);
